@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of batched IPv6 longest-prefix-match on GB300 (PlanB linearized B+-tree).
+
+Workload (default): a 200,000-prefix synthetic backbone FIB (BGP-like length mix, ~30 % nested,
+1 % /128, next hops in [1, 4095], ::/0 -> 0) and 2^28 lookup addresses per GPU (70 % uniform inside
+a random prefix, 30 % uniform over the 128-bit space). One step = one planb_lookup over all 2^28
+device-resident addresses: key ingest, tree descent, next-hop gather and result store (hot-path
+steps a5-a10). The 4 GiB key stream is larger than L2, so no flush is needed between steps.
+
+Prints ONE JSON line on rank 0. ``--impl reference`` times the CPU oracle (binary trie) instead.
+Multi-GPU (torchrun, one rank per GPU): each rank looks up its own 2^28 addresses against a replica
+of the table (weak scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "B lookups/s on 200k-prefix FIB, learned vs plain tree; p99 batch latency"
+UNIT = "B lookups/s"
+HBM_BYTES_PER_LOOKUP = 18          # 16-byte address in, 2-byte next hop out
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="planb", choices=["planb", "reference"])
+    ap.add_argument("--prefixes", type=int, default=200_000)
+    ap.add_argument("--lookups", type=int, default=1 << 28)
+    ap.add_argument("--format", default="f8x128", choices=["f8x128", "f16hi"])
+    ap.add_argument("--smem-levels", type=int, default=-1)
+    ap.add_argument("--traffic", default="uniform", choices=["uniform", "zipf"])
+    ap.add_argument("--seed", type=int, default=2604)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--latency-batches", type=int, default=1000)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, use_cuda):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value, use_cuda):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if use_cuda else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.uuid = uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd[1:1] = ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                mx.append(float(row[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from an ncu capture committed under profiles/, if the kernel source
+    has not changed since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2604_14650_gb300", "csrc", "lookup.cu")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    e = rec.get(kernel)
+    if not e:
+        return None
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if e.get("source_sha256") != sha:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------- workload
+
+def workload(args, rank):
+    import synth
+    fib = synth.gen_fib(args.prefixes, seed=args.seed, nh_max=4095)
+    n = args.lookups
+    if args.traffic == "zipf":
+        xh, xl = synth.gen_trace_zipf(fib, n, seed=args.seed + 1 + rank)
+    else:
+        xh, xl = synth.gen_trace(fib, n, seed=args.seed + 1, start=rank * n)
+    return fib, xh, xl
+
+
+def workload_name(args):
+    t = "70% covered / 30% uniform" if args.traffic == "uniform" else "Zipf(1.1) over 1e5 hot /64s"
+    return (f"{args.prefixes}-prefix synthetic BGP-like IPv6 FIB, {args.lookups} lookups per GPU "
+            f"({t})")
+
+
+def cpu_oracle_rate(fib, xh, xl, seconds):
+    """The oracle (O2 binary trie, as it stands) on all host cores over a bounded sample."""
+    import oracle
+    trie = oracle.Trie(fib.hi, fib.lo, fib.len, fib.nh)
+    threads = os.cpu_count() or 1
+    probe = min(xh.size, 1 << 20)
+    t0 = time.perf_counter()
+    trie.lookup(xh[:probe], xl[:probe], threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    sample = int(min(xh.size, max(probe, probe * seconds / dt)))
+    out = np.empty(sample, np.uint16)
+    t0 = time.perf_counter()
+    trie.lookup(xh[:sample], xl[:sample], threads=threads, out=out)
+    dt = time.perf_counter() - t0
+    return sample / dt, trie.last_threads, sample, dt
+
+
+def host_info():
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count()}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    fib = synth.gen_fib(args.prefixes, seed=args.seed, nh_max=4095)
+    sample = 1 << 22
+    xh, xl = synth.gen_trace(fib, sample, seed=args.seed + 1)
+    trie = oracle.Trie(fib.hi, fib.lo, fib.len, fib.nh)
+    threads = os.cpu_count() or 1
+    out = np.empty(sample, np.uint16)
+    for _ in range(args.warmup):
+        trie.lookup(xh, xl, threads=threads, out=out)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        trie.lookup(xh, xl, threads=threads, out=out)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sample * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": workload_name(args), "sample_per_step": sample,
+                   "prefixes": args.prefixes, "lookups": args.lookups},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": trie.last_threads,
+                         "kind": "oracle",
+                         "sample": f"{sample} addresses of the same trace per step, binary trie",
+                         "host": host_info()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_planb(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, True)
+    import paper_2604_14650_gb300 as pb
+    fib_in, xh, xl = workload(args, rank)
+    fib = pb.Fib(fib_in.hi, fib_in.lo, fib_in.len, fib_in.nh, format=args.format,
+                 smem_levels=args.smem_levels, device=local)
+    st = fib.stats()
+    n = xh.size
+    d_hi = torch.from_numpy(xh.view(np.int64)).cuda()
+    d_lo = torch.from_numpy(xl.view(np.int64)).cuda()
+    d_out = torch.empty(n, dtype=torch.int16, device="cuda")
+    stream = torch.cuda.Stream()
+    hp, lp, op = d_hi.data_ptr(), d_lo.data_ptr(), d_out.data_ptr()
+
+    # parity spot check of this very launch configuration against the oracle (sampled)
+    with torch.cuda.stream(stream):
+        fib.lookup_ptr(hp, lp, n, op, stream)
+    stream.synchronize()
+    import oracle
+    idx = np.random.default_rng(args.seed).integers(0, n, 1 << 16)
+    want = oracle.Trie(fib_in.hi, fib_in.lo, fib_in.len, fib_in.nh).lookup(xh[idx], xl[idx])
+    got = d_out.cpu().numpy().view(np.uint16)[idx]
+    if not np.array_equal(got, want):
+        raise SystemExit(f"parity failure: {int(np.count_nonzero(got != want))} of {idx.size}")
+
+    for _ in range(args.warmup):
+        fib.lookup_ptr(hp, lp, n, op, stream)
+    stream.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier(dist, local)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        fib.lookup_ptr(hp, lp, n, op, stream)
+        ev[i + 1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier(dist, local)
+    clk = clocks.stop()
+    per_launch = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    total_ms = max_over_ranks(dist, total_ms, True)
+    value = n * world * args.steps / (total_ms / 1e3) / 1e9
+    avg_launch_s = statistics.mean(per_launch) / 1e3
+
+    # e2e through the public API with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        ph = torch.from_numpy(xh.view(np.int64)).pin_memory()
+        pl = torch.from_numpy(xl.view(np.int64)).pin_memory()
+        po = torch.empty(n, dtype=torch.int16).pin_memory()
+        fib.lookup_host(ph, pl, out=po)
+        barrier(dist, local)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            fib.lookup_host(ph, pl, out=po)
+        torch.cuda.synchronize()
+        barrier(dist, local)
+        dt = max_over_ranks(dist, time.perf_counter() - t0, True)
+        e2e = {"value": n * world * args.e2e_steps / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 2 * n,
+               "api": "planb_lookup_host (pinned host buffers, chunked H2D/kernel/D2H pipeline)"}
+        if not np.array_equal(po.numpy().view(np.uint16)[idx], want):
+            raise SystemExit("e2e parity failure")
+        del ph, pl, po
+
+    # p50/p99 latency of 2^16-address batches, each launch event-timed
+    lat = None
+    if args.latency_batches > 0:
+        bs = 1 << 16
+        nb = args.latency_batches
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(nb)]
+        for i in range(nb):
+            off = (i * bs) % max(n - bs, 1)
+            a, b = evs[i]
+            a.record(stream)
+            fib.lookup_ptr(hp + 8 * off, lp + 8 * off, bs, op + 2 * off, stream)
+            b.record(stream)
+        stream.synchronize()
+        us = sorted(1e3 * a.elapsed_time(b) for a, b in evs)
+        lat = {"batch": bs, "batches": nb, "p50_us": us[len(us) // 2],
+               "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))], "max_us": us[-1]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, sample, secs = cpu_oracle_rate(fib_in, xh, xl, args.cpu_seconds)
+        cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {sample} addresses of the same trace, binary trie, {secs:.1f} s",
+               "host": host_info()}
+
+    peak, peak_kind = measured_peaks()
+    kernel = f"lookup_{args.format}<{st['depth']}>"
+    achieved = HBM_BYTES_PER_LOOKUP * n / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(kernel),
+                "kernel": kernel, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": HBM_BYTES_PER_LOOKUP * n}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded)",
+        "config": {"workload": workload_name(args), "prefixes": args.prefixes,
+                   "lookups_per_gpu": n, "traffic": args.traffic, "format": args.format,
+                   "depth": st["depth"], "smem_levels": st["smem_levels"],
+                   "intervals": st["n_intervals"], "table_bytes": st["node_bytes"] + st["value_bytes"],
+                   "build_ms": st["build_ms"], "upload_ms": st["upload_ms"],
+                   "l2": "inputs (16 B x lookups) larger than L2; no flush", "seed": args.seed,
+                   "parallelism": f"dp{world} (table replicated, addresses sharded)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "latency": lat,
+        "clocks": clk,
+        "gpu_launches": args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    fib.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_planb(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * planb.h — C ABI of libplanb.so: batched IPv6 longest-prefix-match (LPM) on a GB300 (sm_103a) GPU,
+ * by the PlanB method (arXiv 2604.14650): prefixes are turned into sorted elementary intervals
+ * (Section 3.1) and stored as a flat-array linearized B+-tree (Section 3.2) that a CUDA kernel
+ * descends once per 128-bit destination address (Algorithm 1) to that interval's next hop.
+ *
+ * Conventions shared by every call
+ *   - Addresses and prefixes are 128-bit numbers held as two uint64_t halves: `hi` is the first
+ *     8 bytes of the address in network order read as a big-endian integer, `lo` the last 8
+ *     (Section 3.1's example: 2001:db8:: is hi = 0x20010db800000000, lo = 0).
+ *   - A prefix is (hi, lo, len) with len in 0..128; host bits beyond len are ignored (masked).
+ *     When the same (prefix, len) is given more than once, the last one wins.
+ *   - An address that no prefix covers gets the ::/0 next hop when the table has one, else 0
+ *     (Section 3.1: uncovered intervals take the default route).
+ *   - Return value: 0 (PLANB_OK) on success, a negative PLANB_E* code on failure; planb_strerror()
+ *     names it. A failed call changes nothing the caller can observe, except where stated.
+ *   - `stream` is a cudaStream_t (0 = the legacy default stream). Calls that take one are
+ *     asynchronous with respect to the host: results are ready when the stream has completed.
+ *   - Host pointers are read during the call only; the library keeps no reference to them.
+ *     Device pointers (the d_ arguments) are caller-owned device memory on the fib's device.
+ */
+#ifndef PLANB_H
+#define PLANB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
+
+/* ----------------------------------------------------------------------------- status codes */
+#define PLANB_OK 0
+#define PLANB_EINVAL (-1)   /* null pointer, len > 128, size too large, bad option            */
+#define PLANB_ENOMEM (-2)   /* host or device allocation failed                               */
+#define PLANB_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed                     */
+#define PLANB_EDEVICE (-4)  /* a kernel reported an error through the fib's device status word */
+#define PLANB_ENODEV (-5)   /* no CUDA device, or the device is not sm_103                      */
+#define PLANB_ETIMEOUT (-6) /* a bounded device-side wait ran out                               */
+
+/* ----------------------------------------------------------------------------- node formats */
+/* F8x128: 8 full 128-bit keys per 128-byte node, 9-ary (the paper's k = 8, b = 9 of Section 3.2,
+ * with 128-bit keys instead of the 64-bit key halves the paper uses). */
+#define PLANB_FMT_F8X128 0
+/* F16HI: 16 key high halves per 128-byte node, 17-ary (Section 3.2: 128-byte lines give 16-key,
+ * 17-ary nodes); a parallel array holds the low halves, read only when a high half ties. */
+#define PLANB_FMT_F16HI 1
+
+typedef struct planb_fib planb_fib; /* opaque; owns all host and device memory of one table */
+
+typedef struct {
+    uint32_t struct_size;   /* sizeof(planb_opts); lets the library accept older callers        */
+    int32_t format;         /* PLANB_FMT_*; default PLANB_FMT_F8X128                            */
+    int32_t merge_equal_nh; /* 1: merge neighbouring intervals with equal next hops (Section 3
+                               intro allows compressing routes that share a next hop); results
+                               are unchanged. Default 0.                                        */
+    int32_t smem_levels;    /* tree levels staged in shared memory per CTA; -1 = automatic       */
+    int32_t device;         /* CUDA device ordinal; -1 = the current device                      */
+    int32_t block_threads;  /* threads per CTA of the lookup kernel; 0 = automatic               */
+    int32_t ctas_per_sm;    /* persistent CTAs per SM; 0 = as many as fit                        */
+    int32_t reserved[8];    /* zero                                                              */
+} planb_opts;
+
+/* Fills *o with the defaults. */
+void planb_opts_default(planb_opts *o);
+
+typedef struct {
+    uint64_t n_input;          /* prefixes given to the last (re)build                           */
+    uint64_t n_prefixes;       /* distinct canonical prefixes in the table                       */
+    uint64_t n_intervals;      /* elementary intervals m (Section 3.1: at most 2N + 1)            */
+    uint32_t depth;            /* levels D including the leaf level (Algorithm 1 visits D nodes)  */
+    uint32_t keys_per_node;    /* k                                                              */
+    uint32_t fanout;           /* b = k + 1                                                      */
+    uint32_t smem_levels;      /* levels staged in shared memory by the lookup kernel            */
+    uint32_t format;           /* PLANB_FMT_*                                                    */
+    uint32_t device;           /* device ordinal                                                 */
+    uint64_t internal_nodes;   /* nodes of the internal levels (complete levels, Section 3.2)     */
+    uint64_t leaf_nodes;       /* leaf nodes allocated (trailing all-padding leaves are not)      */
+    uint64_t node_bytes;       /* bytes of the node array(s) on the device                       */
+    uint64_t value_bytes;      /* bytes of the next-hop array on the device                      */
+    uint64_t version;          /* table generation: 1 after build, +1 per applied update         */
+    uint64_t withdraw_absent;  /* withdraws of prefixes that were not in the table (no-ops)       */
+    double build_ms;           /* host time of the last build (canonicalise .. layout)           */
+    double upload_ms;          /* host time to allocate and upload the last table                */
+} planb_stats_t;
+
+/*
+ * planb_build — builds a table from n prefixes and uploads it to the device.
+ *   prefix_hi, prefix_lo, len, nexthop: host arrays of n entries (n may be 0: every address then
+ *     gets next hop 0). opts may be NULL for the defaults.
+ *   *out receives the new table; the caller frees it with planb_destroy.
+ * Steps (Section 3.1 "Range Conversion" and "Interval Partitioning"; Section 3.6, Algorithm 2):
+ * each prefix P/L becomes the range [P, P + 2^(128-L)), the range ends become sorted boundaries,
+ * a sweep assigns each elementary interval the next hop of its longest covering prefix, and the
+ * interval bounds are laid out as a linearized B+-tree (Section 3.2).
+ * Errors: PLANB_EINVAL (null pointer with n > 0, len > 128, bad option), PLANB_ENOMEM,
+ *   PLANB_ENODEV, PLANB_ECUDA.
+ */
+int planb_build(const uint64_t *prefix_hi, const uint64_t *prefix_lo, const uint8_t *len,
+                const uint16_t *nexthop, size_t n, const planb_opts *opts, planb_fib **out);
+
+/*
+ * planb_lookup — next hop of n addresses (Algorithm 1, Section 3.2; value fetch of "Separation of
+ * Keys and Values", Section 3.2).
+ *   d_addr_hi, d_addr_lo: device arrays of n uint64_t (8-byte aligned); d_out: device array of n
+ *   uint16_t (2-byte aligned). n = 0 is a no-op. Enqueued on `stream`; returns before it runs.
+ *   It uses the table that is current when the call is made (see planb_update).
+ * Errors: PLANB_EINVAL (null pointer with n > 0, misaligned pointer), PLANB_ECUDA (launch failed).
+ */
+int planb_lookup(const planb_fib *fib, const uint64_t *d_addr_hi, const uint64_t *d_addr_lo,
+                 size_t n, uint16_t *d_out, planb_stream_t stream);
+
+/*
+ * planb_lookup_host — the same lookup for addresses and results in HOST memory: the library
+ * copies the addresses to the device in chunks, runs the lookup kernel on each chunk and copies
+ * the next hops back, overlapping the copies of one chunk with the lookup of another on its own
+ * streams. It returns when every result is in `out` (synchronous). Page-locked (pinned) host
+ * buffers give full copy bandwidth; pageable ones work but are slower.
+ *   addr_hi, addr_lo: host arrays of n uint64_t; out: host array of n uint16_t.
+ *   The device staging buffers are owned by the fib and reused by later calls.
+ * Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ECUDA.
+ */
+int planb_lookup_host(planb_fib *fib, const uint64_t *addr_hi, const uint64_t *addr_lo, size_t n,
+                      uint16_t *out);
+
+typedef struct {
+    uint64_t hi, lo;
+    uint8_t len;
+    uint16_t nexthop;
+} planb_route; /* an insert, or a modify when (prefix, len) is already present (Section 3.6) */
+
+typedef struct {
+    uint64_t hi, lo;
+    uint8_t len;
+} planb_prefix; /* a withdraw; a prefix that is not present is a counted no-op */
+
+/*
+ * planb_update — applies a batch of route changes by rebuild-and-swap (Section 3.6, "Dynamic FIB
+ * Update"): the changes are merged into the table's canonical prefix list (withdraws first, then
+ * inserts, each batch in order), a complete new table is built and uploaded, and the fib is
+ * switched to it with one pointer swap. Lookups enqueued before the call keep using the old
+ * table; lookups enqueued after it return use the new one. The old table is freed only after the
+ * work already enqueued on every stream this fib's lookups have used (and on `stream`) is done.
+ *   inserts: host array of n_ins routes; withdraws: host array of n_wd prefixes (either may be
+ *   NULL when its count is 0).
+ * On any failure the previous table stays current and unchanged.
+ * Errors: PLANB_EINVAL (len > 128, null pointer with a count > 0), PLANB_ENOMEM, PLANB_ECUDA.
+ */
+int planb_update(planb_fib *fib, const planb_route *inserts, size_t n_ins,
+                 const planb_prefix *withdraws, size_t n_wd, planb_stream_t stream);
+
+/* planb_stats — copies the table's statistics into *out. Errors: PLANB_EINVAL. */
+int planb_stats(const planb_fib *fib, planb_stats_t *out);
+
+/*
+ * planb_device_status — waits for the device, then reads and clears the fib's device status word,
+ * which kernels set when a bounds check fails (builds with PLANB_BOUNDS_CHECK) or a bounded wait
+ * runs out. Returns PLANB_OK, PLANB_EDEVICE or PLANB_ETIMEOUT; *detail (nullable) receives the
+ * raw word.
+ */
+int planb_device_status(planb_fib *fib, uint32_t *detail);
+
+/* planb_destroy — waits for the fib's outstanding work and frees it. NULL is a no-op. */
+void planb_destroy(planb_fib *fib);
+
+/* planb_strerror — a static string naming a PLANB_* code. */
+const char *planb_strerror(int code);
+
+/* ------------------------------------------------------------------ host-only entry points */
+/* These run on the host alone and need no GPU; they expose the build steps for inspection.  */
+
+/*
+ * planb_intervals — the elementary intervals of a prefix table (Section 3.1; Algorithm 2's event
+ * sort and stack sweep, with the readings stated in the project's design notes): out_start_hi/lo
+ * receive the first address of each interval, strictly increasing from 0, and out_nh its next hop.
+ * `cap` is the room in the output arrays; *out_m receives the interval count m (<= 2N + 1). When
+ * cap < m nothing is written, *out_m is set and PLANB_EINVAL is returned.
+ * merge_equal_nh as in planb_opts.
+ */
+int planb_intervals(const uint64_t *prefix_hi, const uint64_t *prefix_lo, const uint8_t *len,
+                    const uint16_t *nexthop, size_t n, int merge_equal_nh, uint64_t *out_start_hi,
+                    uint64_t *out_start_lo, uint16_t *out_nh, size_t cap, size_t *out_m);
+
+typedef struct {
+    uint32_t keys_per_node;  /* k */
+    uint32_t fanout;         /* b = k + 1 */
+    uint32_t depth;          /* D: levels including the leaf level */
+    uint32_t reserved;
+    uint64_t n_keys;         /* keys to index */
+    uint64_t internal_nodes; /* sum over the D - 1 internal levels of b^l */
+    uint64_t leaf_capacity;  /* b^(D - 1) leaf nodes */
+    uint64_t key_capacity;   /* k * b^(D - 1) */
+    uint64_t level_start[16];/* level_start(l) = k (b^l - 1) / (b - 1), in keys (Section 3.2) */
+} planb_layout_t;
+
+/*
+ * planb_layout_info — the linearized B+-tree arithmetic of Section 3.2 for k keys per node and
+ * n_keys keys: the smallest depth whose leaf level holds n_keys keys, the level starts and the
+ * capacities. depth_override > 0 forces that depth instead (for checking the capacity figures).
+ * Errors: PLANB_EINVAL (k < 1, or a depth beyond 16 levels).
+ */
+int planb_layout_info(uint32_t keys_per_node, uint64_t n_keys, uint32_t depth_override,
+                      planb_layout_t *out);
+
+/*
+ * planb_child_index — key index of the first key of child c of the j-th node on level d
+ * (Section 3.2: child_start(d, j, c) = level_start(d + 1) + (j * b + c) * k). Host-only helper
+ * exposed for checking the index arithmetic.
+ */
+uint64_t planb_child_index(uint32_t keys_per_node, uint32_t d, uint64_t j, uint32_t c);
+
+/*
+ * planb_debug_inject — test hook (the paper has no counterpart): makes the next table build fail
+ * as if memory ran out, on the host (point = 1) or at device allocation (point = 2); 0 clears it.
+ * It lets a test check that a failed planb_update leaves the previous table current and correct.
+ * Errors: PLANB_EINVAL for another point.
+ */
+int planb_debug_inject(int point);
+
+/* planb_version — library version, (major << 16) | minor. */
+uint32_t planb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PLANB_H */

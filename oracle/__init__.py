@@ -19,13 +19,14 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "planb_oracle.c")
-_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT = os.path.join(_HERE, "_build", platform.machine(), "liboracle.so")
 _lib = None
 
 _u64p = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")

@@ -1,0 +1,290 @@
+"""Python binding of libplanb.so (include/planb.h): argument marshalling only.
+
+Every step of a lookup runs in the library's CUDA kernels; the table build runs in its C++ host
+code. PyTorch supplies device memory and streams: device arrays are CUDA tensors (addresses as
+int64 holding the u64 bits, next hops as int16 holding the u16 bits) and a stream is a
+``torch.cuda.Stream``. If the compiled library is missing, every call raises — there is no Python
+or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import platform
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_DIR = os.path.join(HERE, "_build", platform.machine())
+
+PLANB_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EDEVICE", -5: "ENODEV", -6: "ETIMEOUT"}
+FORMATS = {"f8x128": 0, "f16hi": 1}
+
+
+class PlanbError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_strerror(code)})")
+
+
+class Opts(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("format", C.c_int32), ("merge_equal_nh", C.c_int32),
+                ("smem_levels", C.c_int32), ("device", C.c_int32), ("block_threads", C.c_int32),
+                ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32 * 8)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_input", C.c_uint64), ("n_prefixes", C.c_uint64), ("n_intervals", C.c_uint64),
+                ("depth", C.c_uint32), ("keys_per_node", C.c_uint32), ("fanout", C.c_uint32),
+                ("smem_levels", C.c_uint32), ("format", C.c_uint32), ("device", C.c_uint32),
+                ("internal_nodes", C.c_uint64), ("leaf_nodes", C.c_uint64),
+                ("node_bytes", C.c_uint64), ("value_bytes", C.c_uint64), ("version", C.c_uint64),
+                ("withdraw_absent", C.c_uint64), ("build_ms", C.c_double),
+                ("upload_ms", C.c_double)]
+
+
+class LayoutT(C.Structure):
+    _fields_ = [("keys_per_node", C.c_uint32), ("fanout", C.c_uint32), ("depth", C.c_uint32),
+                ("reserved", C.c_uint32), ("n_keys", C.c_uint64), ("internal_nodes", C.c_uint64),
+                ("leaf_capacity", C.c_uint64), ("key_capacity", C.c_uint64),
+                ("level_start", C.c_uint64 * 16)]
+
+
+# planb_route {u64 hi, lo; u8 len; u16 nexthop} and planb_prefix {u64 hi, lo; u8 len} in C layout
+ROUTE_DTYPE = np.dtype({"names": ["hi", "lo", "len", "nexthop"],
+                        "formats": [np.uint64, np.uint64, np.uint8, np.uint16],
+                        "offsets": [0, 8, 16, 18], "itemsize": 24})
+PREFIX_DTYPE = np.dtype({"names": ["hi", "lo", "len"], "formats": [np.uint64, np.uint64, np.uint8],
+                         "offsets": [0, 8, 16], "itemsize": 24})
+
+_libs: dict = {}
+
+_vp = C.c_void_p
+_sz = C.c_size_t
+_SIGS = {
+    "planb_opts_default": (None, [_vp]),
+    "planb_strerror": (C.c_char_p, [C.c_int]),
+    "planb_version": (C.c_uint32, []),
+    "planb_build": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, C.POINTER(_vp)]),
+    "planb_lookup": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
+    "planb_lookup_host": (C.c_int, [_vp, _vp, _vp, _sz, _vp]),
+    "planb_update": (C.c_int, [_vp, _vp, _sz, _vp, _sz, _vp]),
+    "planb_stats": (C.c_int, [_vp, _vp]),
+    "planb_device_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
+    "planb_destroy": (None, [_vp]),
+    "planb_intervals": (C.c_int, [_vp, _vp, _vp, _vp, _sz, C.c_int, _vp, _vp, _vp, _sz,
+                                  C.POINTER(_sz)]),
+    "planb_layout_info": (C.c_int, [C.c_uint32, C.c_uint64, C.c_uint32, _vp]),
+    "planb_child_index": (C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32]),
+    "planb_debug_inject": (C.c_int, [C.c_int]),
+}
+
+
+def library_path(variant: str = "libplanb.so") -> str:
+    return os.path.join(LIB_DIR, variant)
+
+
+def load(variant: str = "libplanb.so"):
+    """Loads (once) and returns the ctypes handle of a compiled library variant."""
+    if variant in _libs:
+        return _libs[variant]
+    path = library_path(variant)
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2604_14650_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _libs[variant] = lib
+    return lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load().planb_strerror(code).decode()
+    except Exception:
+        return "?"
+
+
+def _check(rc: int, where: str):
+    if rc != PLANB_OK:
+        raise PlanbError(rc, where)
+
+
+def _np(a, dtype):
+    a = np.ascontiguousarray(a)
+    if a.dtype != dtype:
+        if a.dtype.itemsize == np.dtype(dtype).itemsize and a.dtype.kind in "iu":
+            a = a.view(dtype)
+        else:
+            a = a.astype(dtype)
+    return a
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p) if a.size else None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def version() -> int:
+    return int(load().planb_version())
+
+
+def intervals(hi, lo, ln, nh, merge: bool = False, variant: str = "libplanb.so"):
+    """Elementary intervals of a prefix table (host only): (start_hi, start_lo, nh) arrays."""
+    lib = load(variant)
+    hi, lo, ln, nh = _np(hi, np.uint64), _np(lo, np.uint64), _np(ln, np.uint8), _np(nh, np.uint16)
+    n = hi.size
+    m = _sz(0)
+    cap = 2 * n + 1
+    sh = np.empty(cap, np.uint64)
+    sl = np.empty(cap, np.uint64)
+    snh = np.empty(cap, np.uint16)
+    _check(lib.planb_intervals(_ptr(hi), _ptr(lo), _ptr(ln), _ptr(nh), n, int(merge), _ptr(sh),
+                               _ptr(sl), _ptr(snh), cap, C.byref(m)), "planb_intervals")
+    k = m.value
+    return sh[:k].copy(), sl[:k].copy(), snh[:k].copy()
+
+
+def layout_info(keys_per_node: int, n_keys: int, depth: int = 0) -> dict:
+    t = LayoutT()
+    _check(load().planb_layout_info(keys_per_node, n_keys, depth, C.byref(t)), "planb_layout_info")
+    d = {f: getattr(t, f) for f, _ in LayoutT._fields_ if f not in ("reserved", "level_start")}
+    d["level_start"] = list(t.level_start)[: t.depth]
+    return d
+
+
+def child_index(keys_per_node: int, d: int, j: int, c: int) -> int:
+    return int(load().planb_child_index(keys_per_node, d, j, c))
+
+
+def debug_inject(point: int):
+    _check(load().planb_debug_inject(point), "planb_debug_inject")
+
+
+class Fib:
+    """One lookup table on a GPU (a planb_fib)."""
+
+    def __init__(self, hi, lo, ln, nh, *, format: str = "f8x128", merge: bool = False,
+                 smem_levels: int = -1, device: int | None = None, block_threads: int = 0,
+                 ctas_per_sm: int = 0, variant: str = "libplanb.so"):
+        self._lib = load(variant)
+        self._h = None
+        hi, lo, ln, nh = _np(hi, np.uint64), _np(lo, np.uint64), _np(ln, np.uint8), _np(nh, np.uint16)
+        if not (hi.shape == lo.shape == ln.shape == nh.shape):
+            raise ValueError("prefix arrays differ in length")
+        o = Opts()
+        self._lib.planb_opts_default(C.byref(o))
+        o.format = FORMATS[format]
+        o.merge_equal_nh = int(merge)
+        o.smem_levels = smem_levels
+        o.device = -1 if device is None else device
+        o.block_threads = block_threads
+        o.ctas_per_sm = ctas_per_sm
+        h = C.c_void_p()
+        _check(self._lib.planb_build(_ptr(hi), _ptr(lo), _ptr(ln), _ptr(nh), hi.size, C.byref(o),
+                                     C.byref(h)), "planb_build")
+        self._h = h
+        self.device = self.stats()["device"]
+
+    # -- lookups ---------------------------------------------------------------------------
+    def lookup(self, addr_hi, addr_lo, out=None, stream=None):
+        """Next hops of CUDA tensors of addresses (int64 bits of u64); returns an int16 tensor."""
+        import torch
+        if not (addr_hi.is_cuda and addr_lo.is_cuda):
+            raise ValueError("addresses must be CUDA tensors (use lookup_host for host arrays)")
+        if addr_hi.dtype not in (torch.int64, torch.uint64) or addr_lo.dtype != addr_hi.dtype:
+            raise ValueError("addresses must be int64 (u64 bits)")
+        if not (addr_hi.is_contiguous() and addr_lo.is_contiguous()):
+            raise ValueError("addresses must be contiguous")
+        n = addr_hi.numel()
+        if addr_lo.numel() != n:
+            raise ValueError("hi and lo differ in length")
+        if out is None:
+            out = torch.empty(n, dtype=torch.int16, device=addr_hi.device)
+        elif out.numel() != n or out.element_size() != 2 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous 2-byte tensor of n elements")
+        _check(self._lib.planb_lookup(self._h, C.c_void_p(addr_hi.data_ptr()),
+                                      C.c_void_p(addr_lo.data_ptr()), n,
+                                      C.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "planb_lookup")
+        return out
+
+    def lookup_ptr(self, hi_ptr: int, lo_ptr: int, n: int, out_ptr: int, stream=None):
+        """Same as lookup on raw device pointers (for timing loops)."""
+        _check(self._lib.planb_lookup(self._h, C.c_void_p(hi_ptr), C.c_void_p(lo_ptr), n,
+                                      C.c_void_p(out_ptr), _stream_handle(stream)), "planb_lookup")
+
+    def lookup_host(self, addr_hi, addr_lo, out=None):
+        """Next hops of host arrays (numpy, or CPU tensors — pinned for full speed); synchronous."""
+        hp, lp, n, keep = _host_ptrs(addr_hi, addr_lo)
+        if out is None:
+            out = np.empty(n, dtype=np.uint16)
+        op = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        _check(self._lib.planb_lookup_host(self._h, C.c_void_p(hp), C.c_void_p(lp), n,
+                                           C.c_void_p(op)), "planb_lookup_host")
+        del keep
+        return out
+
+    # -- updates ---------------------------------------------------------------------------
+    def update(self, ins_hi=(), ins_lo=(), ins_len=(), ins_nh=(), wd_hi=(), wd_lo=(), wd_len=(),
+               stream=None):
+        """Rebuild-and-swap with a batch of inserts (or modifies) and withdraws."""
+        ins = np.zeros(len(ins_hi), dtype=ROUTE_DTYPE)
+        ins["hi"], ins["lo"], ins["len"], ins["nexthop"] = ins_hi, ins_lo, ins_len, ins_nh
+        wd = np.zeros(len(wd_hi), dtype=PREFIX_DTYPE)
+        wd["hi"], wd["lo"], wd["len"] = wd_hi, wd_lo, wd_len
+        st = _stream_handle(stream) if stream is not None else C.c_void_p(0)
+        _check(self._lib.planb_update(self._h, _ptr(ins), ins.size, _ptr(wd), wd.size, st),
+               "planb_update")
+
+    # -- introspection ---------------------------------------------------------------------
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.planb_stats(self._h, C.byref(s)), "planb_stats")
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def device_status(self):
+        w = C.c_uint32(0)
+        rc = self._lib.planb_device_status(self._h, C.byref(w))
+        return rc, w.value
+
+    def close(self):
+        if self._h:
+            self._lib.planb_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _host_ptrs(hi, lo):
+    if hasattr(hi, "data_ptr"):
+        if hi.is_cuda or lo.is_cuda:
+            raise ValueError("lookup_host takes host arrays")
+        if not (hi.is_contiguous() and lo.is_contiguous()) or hi.element_size() != 8:
+            raise ValueError("host tensors must be contiguous 8-byte integers")
+        return hi.data_ptr(), lo.data_ptr(), hi.numel(), (hi, lo)
+    hi, lo = _np(hi, np.uint64), _np(lo, np.uint64)
+    if hi.size != lo.size:
+        raise ValueError("hi and lo differ in length")
+    return hi.ctypes.data, lo.ctypes.data, hi.size, (hi, lo)

@@ -1,0 +1,586 @@
+// C ABI of libplanb (declared in include/planb.h): table objects, build and upload, lookups, and
+// the rebuild-and-swap update of Section 3.6.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "planb_internal.h"
+
+using planb::u128;
+
+namespace {
+
+std::atomic<int> g_inject{0};  // test hook: 1 = fail the next build on the host, 2 = on the device
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Makes `dev` current for the lifetime of the guard.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (ok && prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// One built, uploaded, immutable table.
+struct Table {
+  int device = 0;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  planb::Layout L;
+  planb::DevTable dt{};
+  planb::LaunchCfg cfg;
+  uint64_t n_input = 0, n_prefixes = 0;
+  double build_ms = 0, upload_ms = 0;
+  ~Table() {
+    if (mem) {
+      DeviceGuard g(device);
+      cudaFree(mem);
+    }
+  }
+};
+
+struct Retired {
+  std::shared_ptr<Table> t;
+  std::vector<cudaEvent_t> events;
+  bool fenced = false;
+};
+
+constexpr size_t kHostChunk = size_t(1) << 21;  // keys per chunk of planb_lookup_host
+constexpr int kHostSlots = 3;
+
+}  // namespace
+
+struct planb_fib {
+  planb_opts opts{};
+  int device = 0;
+  std::vector<planb::Prefix> rib;  // canonical prefix list, sorted by (prefix, len)
+  std::mutex cur_mu;               // guards cur and streams
+  std::shared_ptr<Table> cur;
+  std::vector<cudaStream_t> streams;
+  bool streams_overflow = false;
+  std::mutex upd_mu;               // serialises updates, retirement and the host pipeline
+  std::vector<Retired> retired;
+  uint64_t version = 0;
+  uint64_t withdraw_absent = 0;
+  uint32_t* d_status = nullptr;
+  // planb_lookup_host resources
+  cudaStream_t hs[kHostSlots] = {};
+  cudaEvent_t he[kHostSlots] = {};
+  void* hbuf = nullptr;
+};
+
+namespace {
+
+int check_device(int dev) {
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) return PLANB_ENODEV;
+  if (dev < 0 || dev >= count) return PLANB_EINVAL;
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+    return PLANB_ECUDA;
+  if (major != 10 || minor != 3) return PLANB_ENODEV;  // built for sm_103a only
+  return PLANB_OK;
+}
+
+uint32_t auto_smem_levels(const planb::Layout& L, uint32_t format) {
+  // whole tree when it is small, else the deepest prefix of levels within 64 KiB
+  if (planb::smem_bytes_for(L, format, L.D) <= 96 * 1024) return L.D;
+  uint32_t s = 0;
+  while (s + 1 < L.D && planb::smem_bytes_for(L, format, s + 1) <= 64 * 1024) s++;
+  return s;
+}
+
+// Builds and uploads a table from a canonical prefix list.
+int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const planb_opts& o,
+               int device, std::shared_ptr<Table>& out) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (g_inject.load() == 1) {
+    g_inject.store(0);
+    return PLANB_ENOMEM;
+  }
+  planb::Intervals iv;
+  planb::sweep(canon, o.merge_equal_nh != 0, iv);
+  const uint32_t format = static_cast<uint32_t>(o.format);
+  const uint32_t k = format == PLANB_FMT_F16HI ? 16 : 8;
+  const uint64_t m = iv.size();
+  auto t = std::make_shared<Table>();
+  t->device = device;
+  t->n_input = n_input;
+  t->n_prefixes = canon.size();
+  int rc = planb::make_layout(k, m - 1, 0, t->L);
+  if (rc) return rc;
+  const uint64_t total = t->L.total_nodes();
+  if (t->L.D > 10 || total >= (uint64_t(1) << 32)) return PLANB_EINVAL;
+  const size_t node_bytes = static_cast<size_t>(total) * 128;
+  const size_t lo_bytes = format == PLANB_FMT_F16HI ? node_bytes : 0;
+  const size_t val_bytes = ((static_cast<size_t>(m) * 2 + 255) / 256) * 256;
+  std::vector<uint64_t> host((node_bytes + lo_bytes) / 8);
+  if (format == PLANB_FMT_F16HI)
+    planb::fill_f16hi(iv, t->L, host.data(), host.data() + node_bytes / 8);
+  else
+    planb::fill_f8x128(iv, t->L, host.data());
+  t->build_ms = ms_since(t0);
+
+  auto t1 = std::chrono::steady_clock::now();
+  DeviceGuard g(device);
+  if (!g.ok) return PLANB_ECUDA;
+  t->bytes = node_bytes + lo_bytes + val_bytes;
+  if (g_inject.load() == 2) {
+    g_inject.store(0);
+    return PLANB_ENOMEM;
+  }
+  if (cudaMalloc(&t->mem, t->bytes) != cudaSuccess) {
+    t->mem = nullptr;
+    cudaGetLastError();
+    return PLANB_ENOMEM;
+  }
+  char* base = static_cast<char*>(t->mem);
+  if (cudaMemcpy(base, host.data(), node_bytes + lo_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + node_bytes + lo_bytes, iv.nh.data(), m * 2, cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return PLANB_ECUDA;
+  t->dt.nodes = base;
+  t->dt.nodes_lo = lo_bytes ? reinterpret_cast<const uint64_t*>(base + node_bytes) : nullptr;
+  t->dt.values = reinterpret_cast<const uint16_t*>(base + node_bytes + lo_bytes);
+  t->dt.n_intervals = m;
+  t->dt.total_nodes = total;
+  t->dt.internal_nodes = t->L.internal_nodes;
+  t->dt.depth = t->L.D;
+  t->dt.format = format;
+  uint32_t s = o.smem_levels < 0 ? auto_smem_levels(t->L, format)
+                                 : std::min<uint32_t>(o.smem_levels, t->L.D);
+  while (s > 0 && planb::smem_bytes_for(t->L, format, s) > 200 * 1024) s--;
+  t->dt.smem_levels = s;
+  t->dt.smem_nodes = static_cast<uint32_t>(planb::smem_bytes_for(t->L, format, s) / 128);
+  rc = planb::plan_launch(t->dt, device, o.block_threads, o.ctas_per_sm, t->cfg);
+  if (rc) return rc;
+  t->upload_ms = ms_since(t1);
+  out = std::move(t);
+  return PLANB_OK;
+}
+
+// Frees retired tables whose grace period is over (see planb_update).
+void reclaim(planb_fib* f, bool wait) {
+  DeviceGuard g(f->device);
+  for (auto it = f->retired.begin(); it != f->retired.end();) {
+    Retired& r = *it;
+    if (!r.fenced) {
+      if (r.t.use_count() > 1 && !wait) { ++it; continue; }
+      std::vector<cudaStream_t> ss;
+      bool overflow;
+      {
+        std::lock_guard<std::mutex> lk(f->cur_mu);
+        ss = f->streams;
+        overflow = f->streams_overflow;
+      }
+      if (overflow || wait) {
+        cudaDeviceSynchronize();
+        r.events.clear();
+      } else {
+        for (cudaStream_t s : ss) {
+          cudaEvent_t e;
+          if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaDeviceSynchronize();
+            break;
+          }
+          cudaEventRecord(e, s);
+          r.events.push_back(e);
+        }
+      }
+      r.fenced = true;
+    }
+    bool done = true;
+    for (cudaEvent_t e : r.events) {
+      cudaError_t q = wait ? cudaEventSynchronize(e) : cudaEventQuery(e);
+      if (q == cudaErrorNotReady) { done = false; break; }
+    }
+    if (!done) { ++it; continue; }
+    for (cudaEvent_t e : r.events) cudaEventDestroy(e);
+    cudaGetLastError();
+    it = f->retired.erase(it);
+  }
+}
+
+void note_stream(planb_fib* f, cudaStream_t s) {
+  for (cudaStream_t x : f->streams)
+    if (x == s) return;
+  if (f->streams.size() < 64) f->streams.push_back(s);
+  else f->streams_overflow = true;
+}
+
+int canon_routes(const planb_route* r, size_t n, std::vector<planb::Prefix>& out) {
+  std::vector<uint64_t> hi(n), lo(n);
+  std::vector<uint8_t> len(n);
+  std::vector<uint16_t> nh(n);
+  for (size_t i = 0; i < n; i++) {
+    hi[i] = r[i].hi; lo[i] = r[i].lo; len[i] = r[i].len; nh[i] = r[i].nexthop;
+  }
+  return planb::canonicalise(hi.data(), lo.data(), len.data(), nh.data(), n, out);
+}
+
+}  // namespace
+
+extern "C" {
+
+void planb_opts_default(planb_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->struct_size = sizeof(planb_opts);
+  o->format = PLANB_FMT_F8X128;
+  o->merge_equal_nh = 0;
+  o->smem_levels = -1;
+  o->device = -1;
+  o->block_threads = 0;
+  o->ctas_per_sm = 0;
+}
+
+const char* planb_strerror(int code) {
+  switch (code) {
+    case PLANB_OK: return "success";
+    case PLANB_EINVAL: return "invalid argument";
+    case PLANB_ENOMEM: return "out of memory";
+    case PLANB_ECUDA: return "CUDA runtime error";
+    case PLANB_EDEVICE: return "device-side check failed";
+    case PLANB_ENODEV: return "no sm_103 CUDA device";
+    case PLANB_ETIMEOUT: return "device-side wait timed out";
+    default: return "unknown error";
+  }
+}
+
+uint32_t planb_version(void) { return (1u << 16) | 0u; }
+
+int planb_build(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint8_t* len,
+                const uint16_t* nexthop, size_t n, const planb_opts* opts, planb_fib** out) {
+  if (!out) return PLANB_EINVAL;
+  *out = nullptr;
+  planb_opts o;
+  planb_opts_default(&o);
+  if (opts) {
+    if (opts->struct_size < offsetof(planb_opts, reserved)) return PLANB_EINVAL;
+    std::memcpy(&o, opts, std::min<size_t>(opts->struct_size, sizeof(o)));
+    o.struct_size = sizeof(o);
+  }
+  if (o.format != PLANB_FMT_F8X128 && o.format != PLANB_FMT_F16HI) return PLANB_EINVAL;
+  if (o.block_threads < 0 || o.block_threads > 256 || o.block_threads % 32) return PLANB_EINVAL;
+  try {
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return PLANB_ENODEV;
+    int rc = check_device(dev);
+    if (rc) return rc;
+    auto t0 = std::chrono::steady_clock::now();
+    std::unique_ptr<planb_fib> f(new planb_fib());
+    f->opts = o;
+    f->device = dev;
+    rc = planb::canonicalise(prefix_hi, prefix_lo, len, nexthop, n, f->rib);
+    if (rc) return rc;
+    double canon_ms = ms_since(t0);
+    std::shared_ptr<Table> t;
+    rc = make_table(f->rib, n, o, dev, t);
+    if (rc) return rc;
+    t->build_ms += canon_ms;
+    DeviceGuard g(dev);
+    if (cudaMalloc(&f->d_status, sizeof(uint32_t)) != cudaSuccess) return PLANB_ENOMEM;
+    if (cudaMemset(f->d_status, 0, sizeof(uint32_t)) != cudaSuccess) return PLANB_ECUDA;
+    f->cur = std::move(t);
+    f->version = 1;
+    *out = f.release();
+    return PLANB_OK;
+  } catch (const std::bad_alloc&) {
+    return PLANB_ENOMEM;
+  } catch (...) {
+    return PLANB_EINVAL;
+  }
+}
+
+int planb_lookup(const planb_fib* fib_c, const uint64_t* d_addr_hi, const uint64_t* d_addr_lo,
+                 size_t n, uint16_t* d_out, planb_stream_t stream) {
+  if (!fib_c) return PLANB_EINVAL;
+  if (n == 0) return PLANB_OK;
+  if (!d_addr_hi || !d_addr_lo || !d_out) return PLANB_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_addr_hi) | reinterpret_cast<uintptr_t>(d_addr_lo)) & 7u ||
+      reinterpret_cast<uintptr_t>(d_out) & 1u)
+    return PLANB_EINVAL;
+  planb_fib* f = const_cast<planb_fib*>(fib_c);
+  std::shared_ptr<Table> t;
+  {
+    std::lock_guard<std::mutex> lk(f->cur_mu);
+    t = f->cur;
+    note_stream(f, reinterpret_cast<cudaStream_t>(stream));
+  }
+  DeviceGuard g(f->device);
+  if (!g.ok) return PLANB_ECUDA;
+  return planb::launch_lookup(t->dt, t->cfg, d_addr_hi, d_addr_lo, n, d_out, f->d_status, stream);
+}
+
+int planb_lookup_host(planb_fib* f, const uint64_t* addr_hi, const uint64_t* addr_lo, size_t n,
+                      uint16_t* out) {
+  if (!f) return PLANB_EINVAL;
+  if (n == 0) return PLANB_OK;
+  if (!addr_hi || !addr_lo || !out) return PLANB_EINVAL;
+  std::lock_guard<std::mutex> ul(f->upd_mu);
+  DeviceGuard g(f->device);
+  if (!g.ok) return PLANB_ECUDA;
+  const size_t slot_bytes = kHostChunk * (8 + 8 + 2);
+  if (!f->hbuf) {
+    if (cudaMalloc(&f->hbuf, slot_bytes * kHostSlots) != cudaSuccess) {
+      f->hbuf = nullptr;
+      cudaGetLastError();
+      return PLANB_ENOMEM;
+    }
+    for (int s = 0; s < kHostSlots; s++) {
+      if (cudaStreamCreateWithFlags(&f->hs[s], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&f->he[s], cudaEventDisableTiming) != cudaSuccess)
+        return PLANB_ECUDA;
+    }
+  }
+  std::shared_ptr<Table> t;
+  {
+    std::lock_guard<std::mutex> lk(f->cur_mu);
+    t = f->cur;
+    for (int s = 0; s < kHostSlots; s++) note_stream(f, f->hs[s]);
+  }
+  int rc = PLANB_OK;
+  size_t chunk_id = 0;
+  for (size_t off = 0; off < n; off += kHostChunk, chunk_id++) {
+    const size_t c = std::min(kHostChunk, n - off);
+    const int s = static_cast<int>(chunk_id % kHostSlots);
+    char* base = static_cast<char*>(f->hbuf) + slot_bytes * s;
+    uint64_t* dh = reinterpret_cast<uint64_t*>(base);
+    uint64_t* dl = dh + kHostChunk;
+    uint16_t* dout = reinterpret_cast<uint16_t*>(dl + kHostChunk);
+    cudaStream_t st = f->hs[s];
+    if (cudaMemcpyAsync(dh, addr_hi + off, c * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dl, addr_lo + off, c * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = PLANB_ECUDA;
+      break;
+    }
+    rc = planb::launch_lookup(t->dt, t->cfg, dh, dl, c, dout, f->d_status, st);
+    if (rc) break;
+    if (cudaMemcpyAsync(out + off, dout, c * 2, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+      rc = PLANB_ECUDA;
+      break;
+    }
+  }
+  for (int s = 0; s < kHostSlots; s++)
+    if (cudaStreamSynchronize(f->hs[s]) != cudaSuccess) rc = PLANB_ECUDA;
+  return rc;
+}
+
+int planb_update(planb_fib* f, const planb_route* inserts, size_t n_ins,
+                 const planb_prefix* withdraws, size_t n_wd, planb_stream_t stream) {
+  if (!f) return PLANB_EINVAL;
+  if ((n_ins && !inserts) || (n_wd && !withdraws)) return PLANB_EINVAL;
+  try {
+    std::lock_guard<std::mutex> ul(f->upd_mu);
+    auto t0 = std::chrono::steady_clock::now();
+    // canonical batches
+    std::vector<planb::Prefix> ins;
+    int rc = canon_routes(inserts, n_ins, ins);
+    if (rc) return rc;
+    std::vector<planb::Prefix> wd(n_wd);
+    for (size_t i = 0; i < n_wd; i++) {
+      if (withdraws[i].len > 128) return PLANB_EINVAL;
+      wd[i].p = planb::mk128(withdraws[i].hi, withdraws[i].lo) & planb::top_bits(withdraws[i].len);
+      wd[i].len = withdraws[i].len;
+      wd[i].nh = 0;
+    }
+    std::sort(wd.begin(), wd.end(), planb::prefix_less);
+    wd.erase(std::unique(wd.begin(), wd.end(),
+                         [](const planb::Prefix& a, const planb::Prefix& b) {
+                           return a.p == b.p && a.len == b.len;
+                         }),
+             wd.end());
+    // merge: rib minus withdraws, then union inserts (an insert of a present prefix modifies it)
+    std::vector<planb::Prefix> mid;
+    mid.reserve(f->rib.size());
+    uint64_t absent = 0;
+    {
+      size_t i = 0, j = 0;
+      const auto& R = f->rib;
+      while (i < R.size() || j < wd.size()) {
+        if (j == wd.size() || (i < R.size() && planb::prefix_less(R[i], wd[j]))) {
+          mid.push_back(R[i++]);
+        } else if (i == R.size() || planb::prefix_less(wd[j], R[i])) {
+          absent++;
+          j++;
+        } else {
+          i++;
+          j++;
+        }
+      }
+    }
+    std::vector<planb::Prefix> next;
+    next.reserve(mid.size() + ins.size());
+    {
+      size_t i = 0, j = 0;
+      while (i < mid.size() || j < ins.size()) {
+        if (j == ins.size() || (i < mid.size() && planb::prefix_less(mid[i], ins[j]))) {
+          next.push_back(mid[i++]);
+        } else if (i == mid.size() || planb::prefix_less(ins[j], mid[i])) {
+          next.push_back(ins[j++]);
+        } else {
+          next.push_back(ins[j++]);
+          i++;
+        }
+      }
+    }
+    const double merge_ms = ms_since(t0);
+    std::shared_ptr<Table> t;
+    rc = make_table(next, next.size(), f->opts, f->device, t);
+    if (rc) return rc;  // the current table is untouched
+    t->build_ms += merge_ms;
+    std::shared_ptr<Table> old;
+    {
+      std::lock_guard<std::mutex> lk(f->cur_mu);
+      old = std::move(f->cur);
+      f->cur = std::move(t);
+      note_stream(f, reinterpret_cast<cudaStream_t>(stream));
+    }
+    f->rib.swap(next);
+    f->version++;
+    f->withdraw_absent += absent;
+    f->retired.push_back(Retired{std::move(old), {}, false});
+    reclaim(f, false);
+    return PLANB_OK;
+  } catch (const std::bad_alloc&) {
+    return PLANB_ENOMEM;
+  } catch (...) {
+    return PLANB_EINVAL;
+  }
+}
+
+int planb_stats(const planb_fib* fib_c, planb_stats_t* out) {
+  if (!fib_c || !out) return PLANB_EINVAL;
+  planb_fib* f = const_cast<planb_fib*>(fib_c);
+  std::shared_ptr<Table> t;
+  {
+    std::lock_guard<std::mutex> lk(f->cur_mu);
+    t = f->cur;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->n_input = t->n_input;
+  out->n_prefixes = t->n_prefixes;
+  out->n_intervals = t->dt.n_intervals;
+  out->depth = t->L.D;
+  out->keys_per_node = t->L.k;
+  out->fanout = t->L.b;
+  out->smem_levels = t->dt.smem_levels;
+  out->format = t->dt.format;
+  out->device = static_cast<uint32_t>(f->device);
+  out->internal_nodes = t->L.internal_nodes;
+  out->leaf_nodes = t->L.leaf_nodes;
+  out->node_bytes = t->L.total_nodes() * 128 * (t->dt.format == PLANB_FMT_F16HI ? 2 : 1);
+  out->value_bytes = t->dt.n_intervals * 2;
+  out->version = f->version;
+  out->withdraw_absent = f->withdraw_absent;
+  out->build_ms = t->build_ms;
+  out->upload_ms = t->upload_ms;
+  return PLANB_OK;
+}
+
+int planb_device_status(planb_fib* f, uint32_t* detail) {
+  if (!f) return PLANB_EINVAL;
+  DeviceGuard g(f->device);
+  if (!g.ok) return PLANB_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PLANB_ECUDA;
+  uint32_t w = 0;
+  if (cudaMemcpy(&w, f->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PLANB_ECUDA;
+  if (cudaMemset(f->d_status, 0, 4) != cudaSuccess) return PLANB_ECUDA;
+  if (detail) *detail = w;
+  if (w == 0) return PLANB_OK;
+  return (w & 0x80000000u) ? PLANB_ETIMEOUT : PLANB_EDEVICE;
+}
+
+void planb_destroy(planb_fib* f) {
+  if (!f) return;
+  {
+    std::lock_guard<std::mutex> ul(f->upd_mu);
+    reclaim(f, true);
+  }
+  DeviceGuard g(f->device);
+  cudaDeviceSynchronize();
+  for (int s = 0; s < kHostSlots; s++) {
+    if (f->hs[s]) cudaStreamDestroy(f->hs[s]);
+    if (f->he[s]) cudaEventDestroy(f->he[s]);
+  }
+  if (f->hbuf) cudaFree(f->hbuf);
+  if (f->d_status) cudaFree(f->d_status);
+  f->cur.reset();
+  delete f;
+}
+
+int planb_intervals(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint8_t* len,
+                    const uint16_t* nexthop, size_t n, int merge_equal_nh, uint64_t* out_start_hi,
+                    uint64_t* out_start_lo, uint16_t* out_nh, size_t cap, size_t* out_m) {
+  if (!out_m) return PLANB_EINVAL;
+  try {
+    std::vector<planb::Prefix> canon;
+    int rc = planb::canonicalise(prefix_hi, prefix_lo, len, nexthop, n, canon);
+    if (rc) return rc;
+    planb::Intervals iv;
+    planb::sweep(canon, merge_equal_nh != 0, iv);
+    *out_m = iv.size();
+    if (cap < iv.size() || !out_start_hi || !out_start_lo || !out_nh) return PLANB_EINVAL;
+    for (size_t i = 0; i < iv.size(); i++) {
+      out_start_hi[i] = planb::hi64(iv.start[i]);
+      out_start_lo[i] = planb::lo64(iv.start[i]);
+      out_nh[i] = iv.nh[i];
+    }
+    return PLANB_OK;
+  } catch (const std::bad_alloc&) {
+    return PLANB_ENOMEM;
+  }
+}
+
+int planb_layout_info(uint32_t keys_per_node, uint64_t n_keys, uint32_t depth_override,
+                      planb_layout_t* out) {
+  if (!out) return PLANB_EINVAL;
+  planb::Layout L;
+  int rc = planb::make_layout(keys_per_node, n_keys, depth_override, L);
+  if (rc) return rc;
+  std::memset(out, 0, sizeof(*out));
+  out->keys_per_node = L.k;
+  out->fanout = L.b;
+  out->depth = L.D;
+  out->n_keys = n_keys;
+  out->internal_nodes = L.internal_nodes;
+  out->leaf_capacity = L.leaf_capacity;
+  out->key_capacity = L.leaf_capacity * L.k;
+  for (uint32_t l = 0; l < L.D && l < 16; l++) out->level_start[l] = L.level_node[l] * L.k;
+  return PLANB_OK;
+}
+
+uint64_t planb_child_index(uint32_t keys_per_node, uint32_t d, uint64_t j, uint32_t c) {
+  // in nodes: child c of node j on level d is node level_node(d+1) + j*b + c
+  const uint64_t k = keys_per_node, b = k + 1;
+  uint64_t level = 0, pw = 1;
+  for (uint32_t l = 0; l <= d; l++) {
+    level += pw;  // after the loop: level_node(d+1) = sum_{l<=d} b^l
+    pw *= b;
+  }
+  return (level + j * b + c) * k;
+}
+
+int planb_debug_inject(int point) {
+  if (point < 0 || point > 2) return PLANB_EINVAL;
+  g_inject.store(point);
+  return PLANB_OK;
+}
+
+}  // extern "C"

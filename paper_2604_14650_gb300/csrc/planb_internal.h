@@ -1,0 +1,108 @@
+// Internal declarations of libplanb: host builder (canonicalise, event sweep, tree layout) and the
+// device-side table description shared by the kernels and the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "planb.h"
+
+namespace planb {
+
+typedef unsigned __int128 u128;
+
+inline u128 mk128(uint64_t hi, uint64_t lo) { return (static_cast<u128>(hi) << 64) | lo; }
+inline uint64_t hi64(u128 v) { return static_cast<uint64_t>(v >> 64); }
+inline uint64_t lo64(u128 v) { return static_cast<uint64_t>(v); }
+
+// top `len` bits set, len in 0..128
+inline u128 top_bits(int len) {
+  if (len <= 0) return 0;
+  if (len >= 128) return ~static_cast<u128>(0);
+  return ~static_cast<u128>(0) << (128 - len);
+}
+
+// One canonical prefix: host bits cleared; (p, len) unique in a table.
+struct Prefix {
+  u128 p;
+  uint16_t nh;
+  uint8_t len;
+};
+
+inline bool prefix_less(const Prefix& a, const Prefix& b) {
+  return a.p < b.p || (a.p == b.p && a.len < b.len);
+}
+
+// Elementary intervals: start[i] is the first address of interval i (start[0] == 0, strictly
+// increasing), nh[i] its next hop.
+struct Intervals {
+  std::vector<u128> start;
+  std::vector<uint16_t> nh;
+  size_t size() const { return start.size(); }
+};
+
+// Step a1 (Section 3.1): mask host bits, drop earlier duplicates of a (prefix, len), sort by
+// (prefix, len). Returns PLANB_EINVAL for len > 128.
+int canonicalise(const uint64_t* hi, const uint64_t* lo, const uint8_t* len, const uint16_t* nh,
+                 size_t n, std::vector<Prefix>& out);
+
+// Steps a2-a3 (Section 3.1 "Interval Partitioning"; Algorithm 2's event list, sort and stack
+// sweep) on a canonical, sorted prefix list.
+void sweep(const std::vector<Prefix>& canon, bool merge_equal_nh, Intervals& out);
+
+// Linearized B+-tree arithmetic (Section 3.2).
+struct Layout {
+  uint32_t k = 0, b = 0, D = 0;        // keys per node, fanout, levels incl. leaves
+  uint64_t n_keys = 0;                 // real keys (m - 1 inclusive interval ends)
+  uint64_t internal_nodes = 0;         // complete internal levels: sum_{l<D-1} b^l
+  uint64_t leaf_capacity = 0;          // b^(D-1)
+  uint64_t leaf_nodes = 0;             // allocated leaves
+  uint64_t level_node[17] = {0};       // first node index of level l (leaf level = internal_nodes)
+  uint64_t total_nodes() const { return internal_nodes + leaf_nodes; }
+};
+
+// Smallest D with k * b^(D-1) >= n_keys (or depth_override). Returns PLANB_EINVAL when D > 16.
+int make_layout(uint32_t k, uint64_t n_keys, uint32_t depth_override, Layout& L);
+
+// Step a4 for PLANB_FMT_F8X128: node-major array of (hi, lo) key pairs, k = 8 per node.
+// keys are the inclusive interval ends start[i+1] - 1; padding is all-ones.
+void fill_f8x128(const Intervals& iv, const Layout& L, uint64_t* nodes /* 2*8*total_nodes */);
+
+// Step a4 for PLANB_FMT_F16HI: node-major hi halves (16 per node) and the parallel lo halves.
+void fill_f16hi(const Intervals& iv, const Layout& L, uint64_t* node_hi, uint64_t* node_lo);
+
+// ------------------------------------------------------------------------- device side
+
+// Everything a lookup kernel needs about one table (device pointers).
+struct DevTable {
+  const void* nodes;        // F8X128: ulonglong2[total_nodes * 8]; F16HI: uint64_t[total * 16]
+  const uint64_t* nodes_lo; // F16HI: low halves, same shape; else null
+  const uint16_t* values;   // next hop per interval, n_intervals entries
+  uint64_t n_intervals;
+  uint64_t total_nodes;
+  uint64_t internal_nodes;
+  uint32_t depth;
+  uint32_t format;
+  uint32_t smem_levels;     // levels staged in shared memory
+  uint32_t smem_nodes;      // nodes staged (the first smem_nodes of the array)
+};
+
+struct LaunchCfg {
+  int threads = 256;
+  int blocks = 0;           // persistent grid size cap
+  size_t smem_bytes = 0;
+};
+
+// Launches the lookup kernel for one table on `stream`. d_status may be null.
+int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
+                  const uint64_t* d_lo, size_t n, uint16_t* d_out, uint32_t* d_status,
+                  void* stream);
+
+// Occupancy-derived launch configuration for a table on a device.
+int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, LaunchCfg& cfg);
+
+// Staged shared-memory bytes for `levels` levels of a table layout/format.
+size_t smem_bytes_for(const Layout& L, uint32_t format, uint32_t levels);
+
+}  // namespace planb

@@ -1,0 +1,178 @@
+"""GPU parity: libplanb's lookup kernels against the CPU oracle, bit-exact, through the C ABI.
+
+Expected next hops always come from ``oracle`` (O2 trie, cross-checked with O1 brute force on
+samples); inputs come from ``synth``. Boundary probes are derived from the oracle-independent
+product intervals only as *addresses* to look up, never as expected values.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2604_14650_gb300 as pb  # noqa: E402
+
+M64 = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pb.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def gpu_lookup(fib, xh, xl, stream=None):
+    out = fib.lookup(dev(xh), dev(xl), stream=stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().view(np.uint16)
+
+
+def expected(f, xh, xl):
+    return oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl)
+
+
+def boundary_probes(f):
+    """Every interval start, start - 1, start + 1, plus 0 and all-ones."""
+    sh, sl, _ = pb.intervals(f.hi, f.lo, f.len, f.nh)
+    s = [(int(h) << 64) | int(l) for h, l in zip(sh, sl)]
+    vals = set()
+    for v in s:
+        for d in (-1, 0, 1):
+            vals.add((v + d) % (1 << 128))
+    vals |= {0, (1 << 128) - 1}
+    vals = sorted(vals)
+    return (np.array([v >> 64 for v in vals], np.uint64),
+            np.array([v & M64 for v in vals], np.uint64))
+
+
+FORMATS = ["f8x128", "f16hi"]
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("smem", [-1, 0, 1, 99])
+def test_config_small_parity(fmt, smem):
+    """1,000 prefixes (+ ::/0), 10^6 addresses (70 % covered), every smem staging depth."""
+    f = synth.gen_fib(1000, seed=101, nh_max=255)
+    xh, xl = synth.gen_trace(f, 1_000_000, seed=102)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, smem_levels=smem) as fib:
+        got = gpu_lookup(fib, xh, xl)
+        want = expected(f, xh, xl)
+        assert np.array_equal(got, want)
+        sub = slice(0, 20_000)
+        assert np.array_equal(want[sub], oracle.brute_lookup(f.hi, f.lo, f.len, f.nh, xh[sub], xl[sub]))
+        bh, bl = boundary_probes(f)
+        assert np.array_equal(gpu_lookup(fib, bh, bl), expected(f, bh, bl))
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("n", [0, 1, 5, 31, 32, 33, 1000, 123_457])
+def test_ragged_batches_and_tables(fmt, n):
+    f = synth.gen_fib(max(n, 1) if n < 1000 else 3000, seed=200 + n, nh_max=4095)
+    xh, xl = synth.gen_trace(f, n, seed=7)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as fib:
+        got = gpu_lookup(fib, xh, xl) if n else np.zeros(0, np.uint16)
+        assert np.array_equal(got, expected(f, xh, xl))
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_degenerate_tables(fmt):
+    probes_h = np.array([0, M64, 0x2001_0DB8 << 32, 0xFFFF << 48, 1], np.uint64)
+    probes_l = np.array([0, M64, 0, 5, M64], np.uint64)
+    tables = {
+        "empty": ([], [], [], []),
+        "default_only": ([0], [0], [0], [77]),
+        "host_routes_at_ends": ([0, M64], [0, M64], [128, 128], [5, 6]),
+        "top_of_space": ([0xFFFF << 48], [0], [16], [9]),
+        "chain": ([0x2001_0DB8_1234_5678] * 129, [0x9ABC_DEF0_1234_5678] * 129, list(range(129)),
+                  [L + 1 for L in range(129)]),
+        "duplicates": ([0x2001_0DB8 << 32] * 3, [0, 1, 2], [32, 32, 32], [1, 2, 3]),
+    }
+    for name, (h, l, L, nh) in tables.items():
+        f = synth.Fib(np.array(h, np.uint64), np.array(l, np.uint64), np.array(L, np.uint8),
+                      np.array(nh, np.uint16), 0)
+        with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as fib:
+            bh, bl = boundary_probes(f)
+            xh = np.concatenate([probes_h, bh])
+            xl = np.concatenate([probes_l, bl])
+            assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl)), name
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_merge_flag_keeps_results(fmt):
+    f = synth.gen_fib(20_000, seed=31, nh_max=3)   # few next hops: many equal neighbours
+    xh, xl = synth.gen_trace(f, 300_000, seed=32)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, merge=True) as a, \
+            pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as b:
+        assert a.stats()["n_intervals"] < b.stats()["n_intervals"]
+        want = expected(f, xh, xl)
+        assert np.array_equal(gpu_lookup(a, xh, xl), want)
+        assert np.array_equal(gpu_lookup(b, xh, xl), want)
+
+
+def test_bounds_checked_build_reports_clean():
+    f = synth.gen_fib(5000, seed=41, nh_max=4095)
+    xh, xl = synth.gen_trace(f, 200_000, seed=42)
+    for fmt in FORMATS:
+        with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, variant="libplanb_checked.so") as fib:
+            assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl))
+            assert fib.device_status() == (0, 0)
+
+
+def test_zipf_trace_parity():
+    f = synth.gen_fib(20_000, seed=51, nh_max=4095)
+    xh, xl = synth.gen_trace_zipf(f, 500_000, seed=52, hot=10_000)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh) as fib:
+        assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl))
+
+
+def test_lookup_host_matches_device_path():
+    f = synth.gen_fib(5000, seed=61, nh_max=4095)
+    n = (1 << 21) * 2 + 12345                 # more than two host-pipeline chunks, ragged
+    xh, xl = synth.gen_trace(f, n, seed=62)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh) as fib:
+        got = fib.lookup_host(xh, xl)
+        assert np.array_equal(got, expected(f, xh, xl))
+        pin_h = torch.from_numpy(xh.view(np.int64)).pin_memory()
+        pin_l = torch.from_numpy(xl.view(np.int64)).pin_memory()
+        out = torch.empty(n, dtype=torch.int16).pin_memory()
+        fib.lookup_host(pin_h, pin_l, out=out)
+        assert np.array_equal(out.numpy().view(np.uint16), got)
+
+
+def test_api_errors():
+    f = synth.gen_fib(100, seed=71)
+    with pytest.raises(pb.PlanbError):
+        pb.Fib(f.hi, f.lo, np.full(f.n, 129, np.uint8), f.nh)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh) as fib:
+        x = dev(np.zeros(8, np.uint64))
+        with pytest.raises(pb.PlanbError):      # misaligned device pointer
+            fib.lookup_ptr(x.data_ptr() + 4, x.data_ptr(), 1, x.data_ptr())
+        fib.lookup_ptr(x.data_ptr(), x.data_ptr(), 0, x.data_ptr())   # n = 0 is a no-op
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_backbone_full_size_parity(fmt):
+    """200,000 prefixes (next hops in [1, 4095]) and 2^28 addresses, the benchmark's workload and
+    launch configuration: every one of the 2^28 next hops equals the oracle trie's."""
+    import os
+    f = synth.gen_fib(200_000, seed=2604, nh_max=4095)
+    n = 1 << 28
+    xh, xl = synth.gen_trace(f, n, seed=2605)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as fib:
+        dh, dl = dev(xh), dev(xl)
+        out = fib.lookup(dh, dl)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint16)
+        del dh, dl, out
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl, threads=os.cpu_count())
+    bad = np.count_nonzero(got != want)
+    assert bad == 0, f"{bad} of {n} differ"
