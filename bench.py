@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--prefixes", type=int, default=200_000)
     ap.add_argument("--lookups", type=int, default=1 << 28)
     ap.add_argument("--format", default="f8x128", choices=["f8x128", "f16hi"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "hybrid", "coop", "flat"])
+    ap.add_argument("--ablation-steps", type=int, default=5,
+                    help="timed steps per kernel variant in the ablation block (0 = skip)")
     ap.add_argument("--smem-levels", type=int, default=-1)
     ap.add_argument("--traffic", default="uniform", choices=["uniform", "zipf"])
     ap.add_argument("--seed", type=int, default=2604)
@@ -265,7 +268,7 @@ def run_planb(args):
     import paper_2604_14650_gb300 as pb
     fib_in, xh, xl = workload(args, rank)
     fib = pb.Fib(fib_in.hi, fib_in.lo, fib_in.len, fib_in.nh, format=args.format,
-                 smem_levels=args.smem_levels, device=local)
+                 smem_levels=args.smem_levels, device=local, kernel=args.kernel)
     st = fib.stats()
     n = xh.size
     d_hi = torch.from_numpy(xh.view(np.int64)).cuda()
@@ -352,6 +355,31 @@ def run_planb(args):
         lat = {"batch": bs, "batches": nb, "p50_us": us[len(us) // 2],
                "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))], "max_us": us[-1]}
 
+    # ablation (the GPU analogue of the paper's Section 4.5 study): every lookup kernel on the same
+    # device-resident addresses
+    ablation = None
+    if args.ablation_steps > 0:
+        ablation = {}
+        for name, fmt, kern in (("flat binary search (std::lower_bound analogue)", "f8x128", "flat"),
+                                ("linearized tree, coop 8-lane, 128-bit keys", "f8x128", "coop"),
+                                ("linearized tree, coop 16-lane, 64-bit key halves", "f16hi", "coop"),
+                                ("linearized tree, hybrid smem index + coop L2", "f8x128", "hybrid")):
+            with pb.Fib(fib_in.hi, fib_in.lo, fib_in.len, fib_in.nh, format=fmt, kernel=kern,
+                        device=local) as v:
+                for _ in range(2):
+                    v.lookup_ptr(hp, lp, n, op, stream)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for _ in range(args.ablation_steps):
+                    v.lookup_ptr(hp, lp, n, op, stream)
+                b.record(stream)
+                stream.synchronize()
+                vs = v.stats()
+                ablation[f"{fmt}/{kern}"] = {
+                    "what": name, "B_lookups_per_s": n * args.ablation_steps / a.elapsed_time(b) / 1e6,
+                    "depth": vs["depth"], "smem_levels": vs["smem_levels"],
+                    "smem_bytes": vs["smem_bytes"], "threads": vs["threads"], "ctas": vs["ctas"]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, sample, secs = cpu_oracle_rate(fib_in, xh, xl, args.cpu_seconds)
@@ -360,7 +388,9 @@ def run_planb(args):
                "host": host_info()}
 
     peak, peak_kind = measured_peaks()
-    kernel = f"lookup_{args.format}<{st['depth']}>"
+    kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
+    kernel = {"hybrid": f"lookup_hybrid<{st['depth'] - st['smem_levels']}>",
+              "flat": "lookup_flat"}.get(kname, f"lookup_coop_{'f16' if args.format == 'f16hi' else 'f8'}<{st['depth']}>")
     achieved = HBM_BYTES_PER_LOOKUP * n / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(kernel),
@@ -372,7 +402,8 @@ def run_planb(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded)",
         "config": {"workload": workload_name(args), "prefixes": args.prefixes,
                    "lookups_per_gpu": n, "traffic": args.traffic, "format": args.format,
-                   "depth": st["depth"], "smem_levels": st["smem_levels"],
+                   "kernel": kname, "depth": st["depth"], "smem_levels": st["smem_levels"],
+                   "threads": st["threads"], "ctas": st["ctas"], "smem_bytes": st["smem_bytes"],
                    "intervals": st["n_intervals"], "table_bytes": st["node_bytes"] + st["value_bytes"],
                    "build_ms": st["build_ms"], "upload_ms": st["upload_ms"],
                    "l2": "inputs (16 B x lookups) larger than L2; no flush", "seed": args.seed,
@@ -381,6 +412,7 @@ def run_planb(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "latency": lat,
+        "ablation": ablation,
         "clocks": clk,
         "gpu_launches": args.steps,
     }

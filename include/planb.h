@@ -48,6 +48,19 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
  * 17-ary nodes); a parallel array holds the low halves, read only when a high half ties. */
 #define PLANB_FMT_F16HI 1
 
+/* ----------------------------------------------------------------------------- lookup kernels */
+#define PLANB_KERNEL_AUTO 0   /* hybrid for F8X128, coop for F16HI                                */
+/* coop: every level by 8-lane (16-lane for F16HI) groups, one coalesced 128-byte node line per
+ * level (Listing 1's node search as a warp ballot + popcount), top levels staged in shared memory */
+#define PLANB_KERNEL_COOP 1
+/* hybrid (F8X128 only): the top S levels are replaced by a per-thread lower bound over the level-S
+ * subtree maxima held in shared memory (the same count, so the same node); the remaining levels
+ * are descended cooperatively from L2 with several addresses per lane group in flight */
+#define PLANB_KERNEL_HYBRID 2
+/* flat (F8X128 only): per-thread binary search over the sorted interval keys in global memory;
+ * the GPU analogue of the paper's ablation baseline (Section 4.5, std::lower_bound) */
+#define PLANB_KERNEL_FLAT 3
+
 typedef struct planb_fib planb_fib; /* opaque; owns all host and device memory of one table */
 
 typedef struct {
@@ -56,11 +69,13 @@ typedef struct {
     int32_t merge_equal_nh; /* 1: merge neighbouring intervals with equal next hops (Section 3
                                intro allows compressing routes that share a next hop); results
                                are unchanged. Default 0.                                        */
-    int32_t smem_levels;    /* tree levels staged in shared memory per CTA; -1 = automatic       */
+    int32_t smem_levels;    /* tree levels resolved in shared memory per CTA (coop: levels staged;
+                               hybrid: levels replaced by the index); -1 = automatic            */
     int32_t device;         /* CUDA device ordinal; -1 = the current device                      */
     int32_t block_threads;  /* threads per CTA of the lookup kernel; 0 = automatic               */
     int32_t ctas_per_sm;    /* persistent CTAs per SM; 0 = as many as fit                        */
-    int32_t reserved[8];    /* zero                                                              */
+    int32_t kernel;         /* PLANB_KERNEL_*; default PLANB_KERNEL_AUTO                          */
+    int32_t reserved[7];    /* zero                                                              */
 } planb_opts;
 
 /* Fills *o with the defaults. */
@@ -84,6 +99,10 @@ typedef struct {
     uint64_t withdraw_absent;  /* withdraws of prefixes that were not in the table (no-ops)       */
     double build_ms;           /* host time of the last build (canonicalise .. layout)           */
     double upload_ms;          /* host time to allocate and upload the last table                */
+    uint32_t kernel;           /* PLANB_KERNEL_* in use (never AUTO)                             */
+    uint32_t threads;          /* threads per CTA of the lookup kernel                           */
+    uint32_t ctas;             /* persistent grid size (CTAs)                                    */
+    uint32_t smem_bytes;       /* dynamic shared memory per CTA                                  */
 } planb_stats_t;
 
 /*

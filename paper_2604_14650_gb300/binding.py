@@ -20,6 +20,7 @@ LIB_DIR = os.path.join(HERE, "_build", platform.machine())
 PLANB_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EDEVICE", -5: "ENODEV", -6: "ETIMEOUT"}
 FORMATS = {"f8x128": 0, "f16hi": 1}
+KERNELS = {"auto": 0, "coop": 1, "hybrid": 2, "flat": 3}
 
 
 class PlanbError(RuntimeError):
@@ -31,7 +32,7 @@ class PlanbError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("format", C.c_int32), ("merge_equal_nh", C.c_int32),
                 ("smem_levels", C.c_int32), ("device", C.c_int32), ("block_threads", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("ctas_per_sm", C.c_int32), ("kernel", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class Stats(C.Structure):
@@ -41,7 +42,8 @@ class Stats(C.Structure):
                 ("internal_nodes", C.c_uint64), ("leaf_nodes", C.c_uint64),
                 ("node_bytes", C.c_uint64), ("value_bytes", C.c_uint64), ("version", C.c_uint64),
                 ("withdraw_absent", C.c_uint64), ("build_ms", C.c_double),
-                ("upload_ms", C.c_double)]
+                ("upload_ms", C.c_double), ("kernel", C.c_uint32), ("threads", C.c_uint32),
+                ("ctas", C.c_uint32), ("smem_bytes", C.c_uint32)]
 
 
 class LayoutT(C.Structure):
@@ -91,7 +93,7 @@ def load(variant: str = "libplanb.so"):
         return _libs[variant]
     path = library_path(variant)
     if not os.path.exists(path):
-        raise RuntimeError(f"{path} is missing: build it with paper_2604_14650_gb300.build.build()")
+        raise RuntimeError(f"{path} is missing: build it with paper_2604_14650_gb300.build()")
     lib = C.CDLL(path)
     for name, (res, args) in _SIGS.items():
         fn = getattr(lib, name)
@@ -177,7 +179,7 @@ class Fib:
 
     def __init__(self, hi, lo, ln, nh, *, format: str = "f8x128", merge: bool = False,
                  smem_levels: int = -1, device: int | None = None, block_threads: int = 0,
-                 ctas_per_sm: int = 0, variant: str = "libplanb.so"):
+                 ctas_per_sm: int = 0, kernel: str = "auto", variant: str = "libplanb.so"):
         self._lib = load(variant)
         self._h = None
         hi, lo, ln, nh = _np(hi, np.uint64), _np(lo, np.uint64), _np(ln, np.uint8), _np(nh, np.uint16)
@@ -191,6 +193,7 @@ class Fib:
         o.device = -1 if device is None else device
         o.block_threads = block_threads
         o.ctas_per_sm = ctas_per_sm
+        o.kernel = KERNELS[kernel]
         h = C.c_void_p()
         _check(self._lib.planb_build(_ptr(hi), _ptr(lo), _ptr(ln), _ptr(nh), hi.size, C.byref(o),
                                      C.byref(h)), "planb_build")

@@ -249,4 +249,28 @@ void fill_f16hi(const Intervals& iv, const Layout& L, uint64_t* node_hi, uint64_
   });
 }
 
+uint64_t sidx_entries(const Layout& L, uint32_t S) {
+  if (S >= L.D) return L.n_keys;
+  u128 span = L.k;                     // keys under one level-S node: k * b^(D-1-S)
+  for (uint32_t l = S; l + 1 < L.D; l++) span *= L.b;
+  u128 cap = 1;
+  for (uint32_t l = 0; l < S; l++) cap *= L.b;
+  const u128 full = static_cast<u128>(L.n_keys) / span;  // entries (q+1)*span-1 < n_keys
+  return static_cast<uint64_t>(std::min<u128>(cap - 1, full));
+}
+
+void fill_sidx(const Intervals& iv, const Layout& L, uint32_t S, uint64_t* out) {
+  const uint64_t n = sidx_entries(L, S);
+  u128 span = 1;
+  if (S < L.D) {
+    span = L.k;
+    for (uint32_t l = S; l + 1 < L.D; l++) span *= L.b;
+  }
+  for (uint64_t q = 0; q < n; q++) {
+    const u128 key = key_at(iv, L.n_keys, (static_cast<u128>(q) + 1) * span - 1);
+    out[2 * q] = hi64(key);
+    out[2 * q + 1] = lo64(key);
+  }
+}
+
 }  // namespace planb

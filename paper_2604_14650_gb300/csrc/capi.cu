@@ -98,11 +98,22 @@ int check_device(int dev) {
   return PLANB_OK;
 }
 
+constexpr size_t kSmemBudget = 96 * 1024;   // per CTA; two hybrid CTAs fit one SM
+
 uint32_t auto_smem_levels(const planb::Layout& L, uint32_t format) {
   // whole tree when it is small, else the deepest prefix of levels within 64 KiB
-  if (planb::smem_bytes_for(L, format, L.D) <= 96 * 1024) return L.D;
+  if (planb::smem_bytes_for(L, format, L.D) <= kSmemBudget) return L.D;
   uint32_t s = 0;
   while (s + 1 < L.D && planb::smem_bytes_for(L, format, s + 1) <= 64 * 1024) s++;
+  return s;
+}
+
+// levels resolved by the hybrid kernel's shared-memory index: every key when they fit, else the
+// deepest level whose subtree maxima fit
+uint32_t auto_index_levels(const planb::Layout& L, size_t budget) {
+  if (planb::sidx_entries(L, L.D) * 16 <= budget) return L.D;
+  uint32_t s = 0;
+  while (s + 1 < L.D && planb::sidx_entries(L, s + 1) * 16 <= budget) s++;
   return s;
 }
 
@@ -118,6 +129,9 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   planb::sweep(canon, o.merge_equal_nh != 0, iv);
   const uint32_t format = static_cast<uint32_t>(o.format);
   const uint32_t k = format == PLANB_FMT_F16HI ? 16 : 8;
+  uint32_t kernel = static_cast<uint32_t>(o.kernel);
+  if (format == PLANB_FMT_F16HI) kernel = planb::kCoop;
+  else if (kernel == PLANB_KERNEL_AUTO) kernel = planb::kHybrid;
   const uint64_t m = iv.size();
   auto t = std::make_shared<Table>();
   t->device = device;
@@ -127,20 +141,36 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   if (rc) return rc;
   const uint64_t total = t->L.total_nodes();
   if (t->L.D > 10 || total >= (uint64_t(1) << 32)) return PLANB_EINVAL;
+  // levels resolved in shared memory
+  uint32_t s;
+  if (kernel == planb::kHybrid) {
+    s = o.smem_levels < 0 ? auto_index_levels(t->L, kSmemBudget)
+                          : std::min<uint32_t>(o.smem_levels, t->L.D);
+    while (s > 0 && planb::sidx_entries(t->L, s) * 16 > 200 * 1024) s--;
+  } else if (kernel == planb::kFlat) {
+    s = 0;
+  } else {
+    s = o.smem_levels < 0 ? auto_smem_levels(t->L, format)
+                          : std::min<uint32_t>(o.smem_levels, t->L.D);
+    while (s > 0 && planb::smem_bytes_for(t->L, format, s) > 200 * 1024) s--;
+  }
+  const uint64_t sidx_n = kernel == planb::kHybrid ? planb::sidx_entries(t->L, s) : 0;
   const size_t node_bytes = static_cast<size_t>(total) * 128;
   const size_t lo_bytes = format == PLANB_FMT_F16HI ? node_bytes : 0;
+  const size_t sidx_bytes = ((sidx_n * 16 + 127) / 128) * 128;
   const size_t val_bytes = ((static_cast<size_t>(m) * 2 + 255) / 256) * 256;
-  std::vector<uint64_t> host((node_bytes + lo_bytes) / 8);
+  std::vector<uint64_t> host((node_bytes + lo_bytes + sidx_bytes) / 8);
   if (format == PLANB_FMT_F16HI)
     planb::fill_f16hi(iv, t->L, host.data(), host.data() + node_bytes / 8);
   else
     planb::fill_f8x128(iv, t->L, host.data());
+  if (sidx_n) planb::fill_sidx(iv, t->L, s, host.data() + (node_bytes + lo_bytes) / 8);
   t->build_ms = ms_since(t0);
 
   auto t1 = std::chrono::steady_clock::now();
   DeviceGuard g(device);
   if (!g.ok) return PLANB_ECUDA;
-  t->bytes = node_bytes + lo_bytes + val_bytes;
+  t->bytes = node_bytes + lo_bytes + sidx_bytes + val_bytes;
   if (g_inject.load() == 2) {
     g_inject.store(0);
     return PLANB_ENOMEM;
@@ -151,23 +181,26 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
     return PLANB_ENOMEM;
   }
   char* base = static_cast<char*>(t->mem);
-  if (cudaMemcpy(base, host.data(), node_bytes + lo_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(base + node_bytes + lo_bytes, iv.nh.data(), m * 2, cudaMemcpyHostToDevice) !=
-          cudaSuccess)
+  const size_t head = node_bytes + lo_bytes + sidx_bytes;
+  if (cudaMemcpy(base, host.data(), head, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(base + head, iv.nh.data(), m * 2, cudaMemcpyHostToDevice) != cudaSuccess)
     return PLANB_ECUDA;
   t->dt.nodes = base;
   t->dt.nodes_lo = lo_bytes ? reinterpret_cast<const uint64_t*>(base + node_bytes) : nullptr;
-  t->dt.values = reinterpret_cast<const uint16_t*>(base + node_bytes + lo_bytes);
+  t->dt.sidx = sidx_n ? reinterpret_cast<const uint64_t*>(base + node_bytes + lo_bytes) : nullptr;
+  t->dt.sidx_n = sidx_n;
+  t->dt.sidx_node = s < t->L.D ? t->L.level_node[s] : 0;
+  t->dt.kernel = kernel;
+  t->dt.values = reinterpret_cast<const uint16_t*>(base + head);
   t->dt.n_intervals = m;
   t->dt.total_nodes = total;
   t->dt.internal_nodes = t->L.internal_nodes;
   t->dt.depth = t->L.D;
   t->dt.format = format;
-  uint32_t s = o.smem_levels < 0 ? auto_smem_levels(t->L, format)
-                                 : std::min<uint32_t>(o.smem_levels, t->L.D);
-  while (s > 0 && planb::smem_bytes_for(t->L, format, s) > 200 * 1024) s--;
   t->dt.smem_levels = s;
-  t->dt.smem_nodes = static_cast<uint32_t>(planb::smem_bytes_for(t->L, format, s) / 128);
+  t->dt.smem_nodes = kernel == planb::kCoop
+                         ? static_cast<uint32_t>(planb::smem_bytes_for(t->L, format, s) / 128)
+                         : 0;
   rc = planb::plan_launch(t->dt, device, o.block_threads, o.ctas_per_sm, t->cfg);
   if (rc) return rc;
   t->upload_ms = ms_since(t1);
@@ -248,6 +281,7 @@ void planb_opts_default(planb_opts* o) {
   o->device = -1;
   o->block_threads = 0;
   o->ctas_per_sm = 0;
+  o->kernel = PLANB_KERNEL_AUTO;
 }
 
 const char* planb_strerror(int code) {
@@ -277,7 +311,9 @@ int planb_build(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint
     o.struct_size = sizeof(o);
   }
   if (o.format != PLANB_FMT_F8X128 && o.format != PLANB_FMT_F16HI) return PLANB_EINVAL;
-  if (o.block_threads < 0 || o.block_threads > 256 || o.block_threads % 32) return PLANB_EINVAL;
+  if (o.block_threads < 0 || o.block_threads > 512 || o.block_threads % 32) return PLANB_EINVAL;
+  if (o.kernel < PLANB_KERNEL_AUTO || o.kernel > PLANB_KERNEL_FLAT) return PLANB_EINVAL;
+  if (o.format == PLANB_FMT_F16HI && o.kernel > PLANB_KERNEL_COOP) return PLANB_EINVAL;
   try {
     int dev = o.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return PLANB_ENODEV;
@@ -491,6 +527,10 @@ int planb_stats(const planb_fib* fib_c, planb_stats_t* out) {
   out->withdraw_absent = f->withdraw_absent;
   out->build_ms = t->build_ms;
   out->upload_ms = t->upload_ms;
+  out->kernel = t->dt.kernel;
+  out->threads = static_cast<uint32_t>(t->cfg.threads);
+  out->ctas = static_cast<uint32_t>(t->cfg.blocks);
+  out->smem_bytes = static_cast<uint32_t>(t->cfg.smem_bytes);
   return PLANB_OK;
 }
 

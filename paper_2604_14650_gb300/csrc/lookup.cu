@@ -1,26 +1,33 @@
 // Lookup kernels: descent of the linearized B+-tree for a batch of 128-bit addresses
 // (hot-path steps a5-a10).
 //
-// The paper's search (Algorithm 1, Listing 1, Section 3.2-3.5) runs one address per core through
+// The paper's search (Algorithm 1, Listing 1, Sections 3.2-3.5) runs one address per core through
 // D node visits, each an 8-wide SIMD compare, a popcount and the child arithmetic
-// i = (k+1) i + (c+1) k. Here a node visit is spread over a lane group: lane j of an 8-lane group
-// holds key j of the node (one 16-byte load; the group's 8 loads are one coalesced 128-byte line),
-// compares it with the address as a 128-bit number, and the warp's ballot plus a popcount of the
-// group's byte give every lane the child index c. The child of node i is node b*i + 1 + c
-// (Section 3.2's child_start formula counted in nodes). Four groups serve four addresses per warp
-// step; each lane owns one address of a 32-address tile, so key loads (hi, lo as 8-byte words) and
-// result stores (u16) are coalesced and the query is broadcast to its group by shuffles.
+// i = (k+1) i + (c+1) k. On the GPU a node visit is spread over a lane group: lane j of an 8-lane
+// group holds key j of the node (one 16-byte load; the group's 8 loads are one coalesced 128-byte
+// line), compares it with the address as a 128-bit number, and the warp's ballot plus a popcount
+// of the group's byte give every lane the child index c. The child of node i is node b*i + 1 + c
+// (Section 3.2's child_start formula counted in nodes).
 //
-// The first `smem_levels` levels are copied once per CTA into shared memory; deeper levels are
-// read through the read-only path from L2, where the whole table stays resident (Section 2.1's
-// cache-residency argument, with GB300's L2 in place of a CPU's L3). The kernel is persistent: a
-// grid of a few CTAs per SM strides over the tiles.
+// Keys are the inclusive interval ends and every count is of keys strictly below the address, so
+// the popcount at the leaf is the interval index r itself and the next hop is values[r] (the
+// separate value array of Section 3.2).
 //
-// Keys are the inclusive interval ends and the count is of keys strictly below the address, so the
-// popcount at the leaf is the interval index r itself and the next hop is values[r].
+// Three kernels:
+//   coop    every level by 8-lane groups (16-lane groups for the F16HI format); the first
+//           smem_levels levels are staged in shared memory per CTA. Four addresses per warp step.
+//   hybrid  (default) levels 0 .. S-1 are replaced by a per-thread branchless lower bound over the
+//           level-S subtree maxima staged in shared memory (the same count a descent of those
+//           levels yields, at one 16-byte entry per level-S node instead of a 128-byte node per
+//           internal node); the remaining D - S levels, read from L2, are descended by 8-lane
+//           groups with four addresses per group in flight, so a warp keeps 16 node fetches
+//           outstanding.
+//   flat    per-thread lower bound over the whole sorted key array in global memory: the GPU
+//           analogue of the paper's ablation baseline (Section 4.5, std::lower_bound).
+// All are persistent: a grid of a few CTAs per SM strides over 32-address tiles; each lane owns
+// one address of a tile, so address loads (8-byte hi and lo words) and next-hop stores (u16) are
+// coalesced.
 #include <cuda_runtime.h>
-
-#include <cstdio>
 
 #include "planb_internal.h"
 
@@ -34,6 +41,7 @@ struct KParams {
   const ulonglong2* nodes;    // F8X128 nodes (key j of node i at nodes[i*8 + j])
   const uint64_t* nodes_hi;   // F16HI high halves (key j of node i at [i*16 + j])
   const uint64_t* nodes_lo;   // F16HI low halves
+  const ulonglong2* sidx;     // hybrid top-of-tree index
   const uint16_t* values;
   const uint64_t* xhi;
   const uint64_t* xlo;
@@ -44,12 +52,14 @@ struct KParams {
   uint32_t internal_nodes;
   uint32_t smem_levels;
   uint32_t smem_nodes;
+  uint32_t sidx_n;
+  uint32_t sidx_node;
   uint32_t* status;
 };
 
-// 128-bit unsigned a < x, with a = (ah, al), x = (xh, xl)
-__device__ __forceinline__ bool less128(uint64_t ah, uint64_t al, uint64_t xh, uint64_t xl) {
-  return (ah < xh) | ((ah == xh) & (al < xl));
+// 128-bit unsigned k < x
+__device__ __forceinline__ bool less128(uint64_t kh, uint64_t kl, uint64_t xh, uint64_t xl) {
+  return (kh < xh) | ((kh == xh) & (kl < xl));
 }
 
 #ifdef PLANB_BOUNDS_CHECK
@@ -58,9 +68,24 @@ __device__ __forceinline__ void report(uint32_t* status, uint32_t code) {
 }
 #endif
 
-// ------------------------------------------------------------------------------- F8X128
+// Number of entries of the sorted array a[0..n) that are below x (n >= 1), branch-free with a
+// trip count that depends on n only (Khuong and Morin's branchless binary search).
+template <class Load>
+__device__ __forceinline__ uint32_t count_below(Load load, uint32_t n, uint64_t xh, uint64_t xl) {
+  uint32_t b = 0;
+  while (n > 1) {
+    const uint32_t half = n >> 1;
+    const ulonglong2 u = load(b + half);
+    b = less128(u.x, u.y, xh, xl) ? b + half : b;
+    n -= half;
+  }
+  const ulonglong2 u = load(b);
+  return b + (less128(u.x, u.y, xh, xl) ? 1u : 0u);
+}
+
+// ------------------------------------------------------------------------------- coop F8X128
 template <int D>
-__global__ void __launch_bounds__(256, 4) lookup_f8x128(const KParams p) {
+__global__ void __launch_bounds__(256, 4) lookup_coop_f8(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ulonglong2* sm = reinterpret_cast<ulonglong2*>(smem_raw);
   const uint32_t staged = p.smem_nodes * 8u;
@@ -110,12 +135,12 @@ __global__ void __launch_bounds__(256, 4) lookup_f8x128(const KParams p) {
   }
 }
 
-// ------------------------------------------------------------------------------- F16HI
+// ------------------------------------------------------------------------------- coop F16HI
 // 16-lane groups, two addresses per warp step; a node is 16 high halves (one 128-byte line). A
 // lane whose high half equals the address's reads the matching low half from the parallel array;
 // the warp takes that branch only when some lane has such a tie.
 template <int D>
-__global__ void __launch_bounds__(256, 4) lookup_f16hi(const KParams p) {
+__global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw);
   const uint32_t staged = p.smem_nodes * 16u;
@@ -168,21 +193,135 @@ __global__ void __launch_bounds__(256, 4) lookup_f16hi(const KParams p) {
   }
 }
 
+// ------------------------------------------------------------------------------- hybrid
+// DB = levels left after the shared-memory index (D - S); 0 when the index holds every key.
+constexpr int kRounds = 4;  // addresses per group in flight during the L2 levels
+
+template <int DB>
+__global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* U = reinterpret_cast<ulonglong2*>(smem_raw);
+  const uint32_t N = p.sidx_n;
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) U[i] = __ldg(p.sidx + i);
+  __syncthreads();
+
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t g = lane >> 3;
+  const uint32_t j = lane & 7u;
+  const uint32_t gshift = g * 8u;
+  const uint32_t gmask = 0xFFu << gshift;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  auto sload = [U](uint32_t i) { return U[i]; };
+
+  for (uint64_t base = warp * 32; base < p.n; base += nwarps * 32) {
+    const uint64_t mine = base + lane;
+    const bool ok = mine < p.n;
+    const uint64_t my_hi = ok ? p.xhi[mine] : 0ull;
+    const uint64_t my_lo = ok ? p.xlo[mine] : 0ull;
+    // phase A: per-thread count over the level-S subtree maxima in shared memory
+    const uint32_t cnt = N ? count_below(sload, N, my_hi, my_lo) : 0u;
+    if constexpr (DB == 0) {
+      uint32_t rank = cnt;
+#ifdef PLANB_BOUNDS_CHECK
+      if (rank >= p.n_intervals) {
+        report(p.status, 2u);
+        rank = 0;
+      }
+#endif
+      const uint16_t v = __ldg(p.values + rank);
+      if (ok) p.out[mine] = v;
+    } else {
+      const uint32_t my_node = p.sidx_node + cnt;
+      uint32_t result = 0;
+      // phase B: the last DB levels from L2, 8-lane groups, kRounds addresses per group at once
+#pragma unroll
+      for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
+        uint64_t qh[kRounds], ql[kRounds];
+        uint32_t nd[kRounds], c[kRounds];
+#pragma unroll
+        for (int i = 0; i < kRounds; i++) {
+          const uint32_t src = gshift + r0 + i;
+          qh[i] = __shfl_sync(kFull, my_hi, src);
+          ql[i] = __shfl_sync(kFull, my_lo, src);
+          nd[i] = __shfl_sync(kFull, my_node, src);
+        }
+#pragma unroll
+        for (int l = 0; l < DB; l++) {
+          ulonglong2 key[kRounds];
+#pragma unroll
+          for (int i = 0; i < kRounds; i++)
+            key[i] = __ldg(p.nodes + static_cast<uint64_t>(nd[i]) * 8u + j);
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            const uint32_t m = __ballot_sync(kFull, less128(key[i].x, key[i].y, qh[i], ql[i]));
+            c[i] = __popc(m & gmask);
+            if (l + 1 < DB) nd[i] = nd[i] * 9u + 1u + c[i];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < kRounds; i++) {
+          uint64_t rank = static_cast<uint64_t>(nd[i] - p.internal_nodes) * 8u + c[i];
+#ifdef PLANB_BOUNDS_CHECK
+          if (rank >= p.n_intervals || nd[i] >= p.total_nodes) {
+            report(p.status, 4u);
+            rank = 0;
+          }
+#endif
+          const uint32_t v = __ldg(p.values + rank);
+          if (j == r0 + i) result = v;
+        }
+      }
+      if (ok) p.out[mine] = static_cast<uint16_t>(result);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------- flat
+__global__ void __launch_bounds__(256) lookup_flat(const KParams p) {
+  const ulonglong2* keys = p.nodes + static_cast<uint64_t>(p.internal_nodes) * 8u;
+  const uint32_t nk = static_cast<uint32_t>(p.n_intervals - 1);
+  auto gload = [keys](uint32_t i) { return __ldg(keys + i); };
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.n;
+       i += stride) {
+    const uint64_t xh = p.xhi[i], xl = p.xlo[i];
+    uint32_t rank = nk ? count_below(gload, nk, xh, xl) : 0u;
+#ifdef PLANB_BOUNDS_CHECK
+    if (rank >= p.n_intervals) {
+      report(p.status, 8u);
+      rank = 0;
+    }
+#endif
+    p.out[i] = __ldg(p.values + rank);
+  }
+}
+
 typedef void (*KernelFn)(const KParams);
 
 constexpr int kMaxDepth = 10;
 
-KernelFn kernel_for(uint32_t format, uint32_t D) {
+KernelFn kernel_for(const DevTable& t) {
   static const KernelFn f8[kMaxDepth + 1] = {
-      nullptr,           lookup_f8x128<1>, lookup_f8x128<2>, lookup_f8x128<3>,
-      lookup_f8x128<4>,  lookup_f8x128<5>, lookup_f8x128<6>, lookup_f8x128<7>,
-      lookup_f8x128<8>,  lookup_f8x128<9>, lookup_f8x128<10>};
+      nullptr,            lookup_coop_f8<1>, lookup_coop_f8<2>, lookup_coop_f8<3>,
+      lookup_coop_f8<4>,  lookup_coop_f8<5>, lookup_coop_f8<6>, lookup_coop_f8<7>,
+      lookup_coop_f8<8>,  lookup_coop_f8<9>, lookup_coop_f8<10>};
   static const KernelFn f16[kMaxDepth + 1] = {
-      nullptr,          lookup_f16hi<1>, lookup_f16hi<2>, lookup_f16hi<3>,
-      lookup_f16hi<4>,  lookup_f16hi<5>, lookup_f16hi<6>, lookup_f16hi<7>,
-      lookup_f16hi<8>,  lookup_f16hi<9>, lookup_f16hi<10>};
-  if (D < 1 || D > kMaxDepth) return nullptr;
-  return format == PLANB_FMT_F16HI ? f16[D] : f8[D];
+      nullptr,             lookup_coop_f16<1>, lookup_coop_f16<2>, lookup_coop_f16<3>,
+      lookup_coop_f16<4>,  lookup_coop_f16<5>, lookup_coop_f16<6>, lookup_coop_f16<7>,
+      lookup_coop_f16<8>,  lookup_coop_f16<9>, lookup_coop_f16<10>};
+  static const KernelFn hyb[kMaxDepth + 1] = {
+      lookup_hybrid<0>, lookup_hybrid<1>, lookup_hybrid<2>, lookup_hybrid<3>,
+      lookup_hybrid<4>, lookup_hybrid<5>, lookup_hybrid<6>, lookup_hybrid<7>,
+      lookup_hybrid<8>, lookup_hybrid<9>, lookup_hybrid<10>};
+  const uint32_t D = t.depth;
+  if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
+  if (t.format == PLANB_FMT_F16HI) return f16[D];
+  switch (t.kernel) {
+    case kHybrid: return t.smem_levels <= D ? hyb[D - t.smem_levels] : nullptr;
+    case kFlat: return lookup_flat;
+    default: return f8[D];
+  }
 }
 
 }  // namespace
@@ -195,12 +334,19 @@ size_t smem_bytes_for(const Layout& L, uint32_t format, uint32_t levels) {
 }
 
 int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, LaunchCfg& cfg) {
-  KernelFn fn = kernel_for(t.format, t.depth);
+  KernelFn fn = kernel_for(t);
   if (!fn) return PLANB_EINVAL;
-  if (threads <= 0) threads = 256;
-  if (threads % 32 || threads > 256) return PLANB_EINVAL;
+  const bool f8 = t.format == PLANB_FMT_F8X128;
+  const int max_threads = (t.kernel == kHybrid && f8) ? 512 : 256;
+  if (threads <= 0) threads = max_threads;
+  if (threads % 32 || threads > max_threads) return PLANB_EINVAL;
   cfg.threads = threads;
-  cfg.smem_bytes = static_cast<size_t>(t.smem_nodes) * 128u;
+  if (t.kernel == kHybrid && f8)
+    cfg.smem_bytes = static_cast<size_t>(t.sidx_n) * 16u;
+  else if (t.kernel == kFlat && f8)
+    cfg.smem_bytes = 0;
+  else
+    cfg.smem_bytes = static_cast<size_t>(t.smem_nodes) * 128u;
   if (cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(cfg.smem_bytes)) != cudaSuccess)
@@ -221,12 +367,13 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   const uint64_t* d_lo, size_t n, uint16_t* d_out, uint32_t* d_status,
                   void* stream) {
   if (n == 0) return PLANB_OK;
-  KernelFn fn = kernel_for(t.format, t.depth);
+  KernelFn fn = kernel_for(t);
   if (!fn) return PLANB_EINVAL;
   KParams p;
   p.nodes = static_cast<const ulonglong2*>(t.nodes);
   p.nodes_hi = static_cast<const uint64_t*>(t.nodes);
   p.nodes_lo = t.nodes_lo;
+  p.sidx = reinterpret_cast<const ulonglong2*>(t.sidx);
   p.values = t.values;
   p.xhi = d_hi;
   p.xlo = d_lo;
@@ -237,10 +384,17 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   p.internal_nodes = static_cast<uint32_t>(t.internal_nodes);
   p.smem_levels = t.smem_levels;
   p.smem_nodes = t.smem_nodes;
+  p.sidx_n = static_cast<uint32_t>(t.sidx_n);
+  p.sidx_node = static_cast<uint32_t>(t.sidx_node);
   p.status = d_status;
-  const uint64_t tiles = (n + 31) / 32;
-  const uint64_t warps_per_block = cfg.threads / 32;
-  uint64_t blocks = (tiles + warps_per_block - 1) / warps_per_block;
+  uint64_t blocks;
+  if (t.kernel == kFlat && t.format == PLANB_FMT_F8X128) {
+    blocks = (n + cfg.threads - 1) / cfg.threads;
+  } else {
+    const uint64_t tiles = (n + 31) / 32;
+    const uint64_t warps_per_block = cfg.threads / 32;
+    blocks = (tiles + warps_per_block - 1) / warps_per_block;
+  }
   if (cfg.blocks > 0 && blocks > static_cast<uint64_t>(cfg.blocks)) blocks = cfg.blocks;
   fn<<<static_cast<unsigned>(blocks), cfg.threads, cfg.smem_bytes,
        static_cast<cudaStream_t>(stream)>>>(p);

@@ -72,11 +72,25 @@ void fill_f8x128(const Intervals& iv, const Layout& L, uint64_t* nodes /* 2*8*to
 // Step a4 for PLANB_FMT_F16HI: node-major hi halves (16 per node) and the parallel lo halves.
 void fill_f16hi(const Intervals& iv, const Layout& L, uint64_t* node_hi, uint64_t* node_lo);
 
+// Top-of-tree index for the hybrid kernel: entry q is the largest key of the subtree of the q-th
+// node on level S (the key at leaf position (q + 1) * k * b^(D-1-S) - 1), for every q whose entry
+// is a real key; trailing all-padding entries are left out. Counting the entries below an address
+// gives the level-S node that a descent of levels 0 .. S-1 would reach (for S = D: the keys
+// themselves, and the count is the interval index). Returns the entry count.
+uint64_t sidx_entries(const Layout& L, uint32_t S);
+void fill_sidx(const Intervals& iv, const Layout& L, uint32_t S, uint64_t* out /* 2 per entry */);
+
 // ------------------------------------------------------------------------- device side
 
 // Everything a lookup kernel needs about one table (device pointers).
+enum Kernel : uint32_t { kCoop = 1, kHybrid = 2, kFlat = 3 };
+
 struct DevTable {
   const void* nodes;        // F8X128: ulonglong2[total_nodes * 8]; F16HI: uint64_t[total * 16]
+  const uint64_t* sidx;     // hybrid: top-of-tree index, (hi, lo) per entry
+  uint64_t sidx_n;          // entries in sidx
+  uint64_t sidx_node;       // first node of level S (where the hybrid's per-group phase starts)
+  uint32_t kernel;          // Kernel
   const uint64_t* nodes_lo; // F16HI: low halves, same shape; else null
   const uint16_t* values;   // next hop per interval, n_intervals entries
   uint64_t n_intervals;

@@ -55,15 +55,23 @@ def boundary_probes(f):
 
 
 FORMATS = ["f8x128", "f16hi"]
+# (node format, kernel) pairs: every lookup kernel of the library
+VARIANTS = [("f8x128", "hybrid"), ("f8x128", "coop"), ("f8x128", "flat"), ("f16hi", "coop")]
+VIDS = [f"{f}-{k}" for f, k in VARIANTS]
 
 
-@pytest.mark.parametrize("fmt", FORMATS)
-@pytest.mark.parametrize("smem", [-1, 0, 1, 99])
-def test_config_small_parity(fmt, smem):
-    """1,000 prefixes (+ ::/0), 10^6 addresses (70 % covered), every smem staging depth."""
+def make(f, variant, **kw):
+    fmt, kernel = variant
+    return pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel, **kw)
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+@pytest.mark.parametrize("smem", [-1, 0, 1, 2, 3, 99])
+def test_config_small_parity(variant, smem):
+    """1,000 prefixes (+ ::/0), 10^6 addresses (70 % covered), every shared-memory depth."""
     f = synth.gen_fib(1000, seed=101, nh_max=255)
     xh, xl = synth.gen_trace(f, 1_000_000, seed=102)
-    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, smem_levels=smem) as fib:
+    with make(f, variant, smem_levels=smem) as fib:
         got = gpu_lookup(fib, xh, xl)
         want = expected(f, xh, xl)
         assert np.array_equal(got, want)
@@ -73,18 +81,18 @@ def test_config_small_parity(fmt, smem):
         assert np.array_equal(gpu_lookup(fib, bh, bl), expected(f, bh, bl))
 
 
-@pytest.mark.parametrize("fmt", FORMATS)
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
 @pytest.mark.parametrize("n", [0, 1, 5, 31, 32, 33, 1000, 123_457])
-def test_ragged_batches_and_tables(fmt, n):
+def test_ragged_batches_and_tables(variant, n):
     f = synth.gen_fib(max(n, 1) if n < 1000 else 3000, seed=200 + n, nh_max=4095)
     xh, xl = synth.gen_trace(f, n, seed=7)
-    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as fib:
+    with make(f, variant) as fib:
         got = gpu_lookup(fib, xh, xl) if n else np.zeros(0, np.uint16)
         assert np.array_equal(got, expected(f, xh, xl))
 
 
-@pytest.mark.parametrize("fmt", FORMATS)
-def test_degenerate_tables(fmt):
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_degenerate_tables(variant):
     probes_h = np.array([0, M64, 0x2001_0DB8 << 32, 0xFFFF << 48, 1], np.uint64)
     probes_l = np.array([0, M64, 0, 5, M64], np.uint64)
     tables = {
@@ -99,19 +107,18 @@ def test_degenerate_tables(fmt):
     for name, (h, l, L, nh) in tables.items():
         f = synth.Fib(np.array(h, np.uint64), np.array(l, np.uint64), np.array(L, np.uint8),
                       np.array(nh, np.uint16), 0)
-        with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as fib:
+        with make(f, variant) as fib:
             bh, bl = boundary_probes(f)
             xh = np.concatenate([probes_h, bh])
             xl = np.concatenate([probes_l, bl])
             assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl)), name
 
 
-@pytest.mark.parametrize("fmt", FORMATS)
-def test_merge_flag_keeps_results(fmt):
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_merge_flag_keeps_results(variant):
     f = synth.gen_fib(20_000, seed=31, nh_max=3)   # few next hops: many equal neighbours
     xh, xl = synth.gen_trace(f, 300_000, seed=32)
-    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, merge=True) as a, \
-            pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as b:
+    with make(f, variant, merge=True) as a, make(f, variant) as b:
         assert a.stats()["n_intervals"] < b.stats()["n_intervals"]
         want = expected(f, xh, xl)
         assert np.array_equal(gpu_lookup(a, xh, xl), want)
@@ -121,8 +128,8 @@ def test_merge_flag_keeps_results(fmt):
 def test_bounds_checked_build_reports_clean():
     f = synth.gen_fib(5000, seed=41, nh_max=4095)
     xh, xl = synth.gen_trace(f, 200_000, seed=42)
-    for fmt in FORMATS:
-        with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, variant="libplanb_checked.so") as fib:
+    for v in VARIANTS:
+        with make(f, v, variant="libplanb_checked.so") as fib:
             assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl))
             assert fib.device_status() == (0, 0)
 
@@ -130,8 +137,10 @@ def test_bounds_checked_build_reports_clean():
 def test_zipf_trace_parity():
     f = synth.gen_fib(20_000, seed=51, nh_max=4095)
     xh, xl = synth.gen_trace_zipf(f, 500_000, seed=52, hot=10_000)
-    with pb.Fib(f.hi, f.lo, f.len, f.nh) as fib:
-        assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl))
+    want = expected(f, xh, xl)
+    for v in VARIANTS:
+        with make(f, v) as fib:
+            assert np.array_equal(gpu_lookup(fib, xh, xl), want), v
 
 
 def test_lookup_host_matches_device_path():
@@ -159,20 +168,28 @@ def test_api_errors():
         fib.lookup_ptr(x.data_ptr(), x.data_ptr(), 0, x.data_ptr())   # n = 0 is a no-op
 
 
-@pytest.mark.parametrize("fmt", FORMATS)
-def test_backbone_full_size_parity(fmt):
-    """200,000 prefixes (next hops in [1, 4095]) and 2^28 addresses, the benchmark's workload and
-    launch configuration: every one of the 2^28 next hops equals the oracle trie's."""
+@pytest.fixture(scope="module")
+def backbone():
+    """200,000 prefixes (next hops in [1, 4095]) and 2^28 addresses: the benchmark's workload;
+    the oracle's answer for all 2^28 addresses is computed once."""
     import os
     f = synth.gen_fib(200_000, seed=2604, nh_max=4095)
     n = 1 << 28
     xh, xl = synth.gen_trace(f, n, seed=2605)
-    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as fib:
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl, threads=os.cpu_count())
+    return f, xh, xl, want
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_backbone_full_size_parity(backbone, variant):
+    """Every one of the 2^28 next hops equals the oracle's, in the launch configuration the
+    benchmark times (default grid, block and shared-memory depth)."""
+    f, xh, xl, want = backbone
+    with make(f, variant) as fib:
         dh, dl = dev(xh), dev(xl)
         out = fib.lookup(dh, dl)
         torch.cuda.synchronize()
         got = out.cpu().numpy().view(np.uint16)
         del dh, dl, out
-    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl, threads=os.cpu_count())
     bad = np.count_nonzero(got != want)
-    assert bad == 0, f"{bad} of {n} differ"
+    assert bad == 0, f"{bad} of {want.size} differ"

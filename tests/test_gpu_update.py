@@ -62,13 +62,14 @@ def oracle_answer(ref, xh, xl):
     return oracle.Trie(h, l, L, n).lookup(xh, xl)
 
 
-@pytest.mark.parametrize("fmt", ["f8x128", "f16hi"])
-def test_update_batches_match_oracle_rebuild(fmt):
+@pytest.mark.parametrize("fmt,kernel", [("f8x128", "hybrid"), ("f8x128", "coop"),
+                                        ("f16hi", "coop")])
+def test_update_batches_match_oracle_rebuild(fmt, kernel):
     f = synth.gen_fib(20_000, seed=81, nh_max=4095)
     xh, xl = synth.gen_trace(f, 400_000, seed=82)
     ref = RefTable(f)
     absent_total = 0
-    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as fib:
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel) as fib:
         dh, dl = dev(xh), dev(xl)
         for batch in range(6):
             upd = synth.gen_updates(f, 500 * (batch + 1), seed=83, start=batch * 10_000)
