@@ -21,7 +21,8 @@
 //           levels yields, at one 16-byte entry per level-S node instead of a 128-byte node per
 //           internal node); the remaining D - S levels, read from L2, are descended by 8-lane
 //           groups with four addresses per group in flight, so a warp keeps 16 node fetches
-//           outstanding.
+//           outstanding. The address-to-group broadcast of the paper's vector broadcast (Listing
+//           1's set1) is a warp shuffle.
 //   flat    per-thread lower bound over the whole sorted key array in global memory: the GPU
 //           analogue of the paper's ablation baseline (Section 4.5, std::lower_bound).
 // All are persistent: a grid of a few CTAs per SM strides over 32-address tiles; each lane owns
@@ -195,14 +196,30 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
 
 // ------------------------------------------------------------------------------- hybrid
 // DB = levels left after the shared-memory index (D - S); 0 when the index holds every key.
+//
+// The index sits in shared memory as two arrays, high halves then low halves. The binary search
+// reads only the 8-byte high halves (half the shared-memory wavefronts of 16-byte entries); it
+// counts the entries whose high half is below the address's, and the entries whose high half
+// equals it — contiguous and sorted by low half right after that count — are then added one by one
+// while their low half is below the address's (a /65+ boundary shares its high half with the
+// address; rare, and a short loop when it happens).
+//
+// In the L2 levels a group needs the address of the lane it serves: only the high half and the node
+// index are broadcast; the low half is broadcast only when some lane of the warp finds a key whose
+// high half equals the address's.
 constexpr int kRounds = 4;  // addresses per group in flight during the L2 levels
 
 template <int DB>
 __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ulonglong2* U = reinterpret_cast<ulonglong2*>(smem_raw);
   const uint32_t N = p.sidx_n;
-  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) U[i] = __ldg(p.sidx + i);
+  uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* Ul = Uh + N;
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+    const ulonglong2 e = __ldg(p.sidx + i);
+    Uh[i] = e.x;
+    Ul[i] = e.y;
+  }
   __syncthreads();
 
   const uint32_t lane = threadIdx.x & 31u;
@@ -212,7 +229,6 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   const uint32_t gmask = 0xFFu << gshift;
   const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-  auto sload = [U](uint32_t i) { return U[i]; };
 
   for (uint64_t base = warp * 32; base < p.n; base += nwarps * 32) {
     const uint64_t mine = base + lane;
@@ -220,7 +236,17 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
     const uint64_t my_hi = ok ? p.xhi[mine] : 0ull;
     const uint64_t my_lo = ok ? p.xlo[mine] : 0ull;
     // phase A: per-thread count over the level-S subtree maxima in shared memory
-    const uint32_t cnt = N ? count_below(sload, N, my_hi, my_lo) : 0u;
+    uint32_t cnt = 0;
+    if (N) {
+      uint32_t b = 0, n = N;
+      while (n > 1) {
+        const uint32_t half = n >> 1;
+        b = Uh[b + half] < my_hi ? b + half : b;
+        n -= half;
+      }
+      cnt = b + (Uh[b] < my_hi ? 1u : 0u);
+      while (cnt < N && Uh[cnt] == my_hi && Ul[cnt] < my_lo) cnt++;
+    }
     if constexpr (DB == 0) {
       uint32_t rank = cnt;
 #ifdef PLANB_BOUNDS_CHECK
@@ -237,13 +263,12 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
       // phase B: the last DB levels from L2, 8-lane groups, kRounds addresses per group at once
 #pragma unroll
       for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
-        uint64_t qh[kRounds], ql[kRounds];
+        uint64_t qh[kRounds];
         uint32_t nd[kRounds], c[kRounds];
 #pragma unroll
         for (int i = 0; i < kRounds; i++) {
           const uint32_t src = gshift + r0 + i;
           qh[i] = __shfl_sync(kFull, my_hi, src);
-          ql[i] = __shfl_sync(kFull, my_lo, src);
           nd[i] = __shfl_sync(kFull, my_node, src);
         }
 #pragma unroll
@@ -252,9 +277,24 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
 #pragma unroll
           for (int i = 0; i < kRounds; i++)
             key[i] = __ldg(p.nodes + static_cast<uint64_t>(nd[i]) * 8u + j);
+          bool lt[kRounds], eq[kRounds];
+          bool anyeq = false;
 #pragma unroll
           for (int i = 0; i < kRounds; i++) {
-            const uint32_t m = __ballot_sync(kFull, less128(key[i].x, key[i].y, qh[i], ql[i]));
+            lt[i] = key[i].x < qh[i];
+            eq[i] = key[i].x == qh[i];
+            anyeq |= eq[i];
+          }
+          if (__any_sync(kFull, anyeq)) {
+#pragma unroll
+            for (int i = 0; i < kRounds; i++) {
+              const uint64_t ql = __shfl_sync(kFull, my_lo, gshift + r0 + i);
+              lt[i] = lt[i] | (eq[i] & (key[i].y < ql));
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            const uint32_t m = __ballot_sync(kFull, lt[i]);
             c[i] = __popc(m & gmask);
             if (l + 1 < DB) nd[i] = nd[i] * 9u + 1u + c[i];
           }

@@ -60,8 +60,8 @@ VARIANTS = [("f8x128", "hybrid"), ("f8x128", "coop"), ("f8x128", "flat"), ("f16h
 VIDS = [f"{f}-{k}" for f, k in VARIANTS]
 
 
-def make(f, variant, **kw):
-    fmt, kernel = variant
+def make(f, which, **kw):
+    fmt, kernel = which
     return pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel, **kw)
 
 
@@ -193,3 +193,30 @@ def test_backbone_full_size_parity(backbone, variant):
         del dh, dl, out
     bad = np.count_nonzero(got != want)
     assert bad == 0, f"{bad} of {want.size} differ"
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_shared_high_halves(variant):
+    """Many boundaries that differ only in their low 64 bits (clusters of /128 and /65../127 routes
+    inside single /64s): exercises every high-half tie path of the kernels."""
+    f = synth.gen_fib(20_000, seed=301, nh_max=4095)
+    rng = np.random.default_rng(302)
+    base = rng.choice(np.nonzero(f.len == 48)[0], 400, replace=False)
+    eh, el, eL, en = [], [], [], []
+    for i, b in enumerate(base):
+        h = np.uint64(f.hi[b] | np.uint64(i))                 # a /64 inside the /48
+        for k in range(6):
+            eh.append(h)
+            el.append(np.uint64(rng.integers(0, 2 ** 63)) * np.uint64(2))
+            eL.append(128 if k < 4 else int(rng.integers(65, 128)))
+            en.append(int(rng.integers(1, 4096)))
+    g = synth.Fib(np.concatenate([f.hi, np.array(eh, np.uint64)]),
+                  np.concatenate([f.lo, np.array(el, np.uint64)]),
+                  np.concatenate([f.len, np.array(eL, np.uint8)]),
+                  np.concatenate([f.nh, np.array(en, np.uint16)]), 0)
+    bh, bl = boundary_probes(g)
+    xh, xl = synth.gen_trace(g, 200_000, seed=303)
+    xh = np.concatenate([bh, xh, np.array(eh, np.uint64)])
+    xl = np.concatenate([bl, xl, np.array(el, np.uint64)])
+    with make(g, variant) as fib:
+        assert np.array_equal(gpu_lookup(fib, xh, xl), expected(g, xh, xl))
