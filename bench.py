@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="planb", choices=["planb", "reference"])
     ap.add_argument("--prefixes", type=int, default=200_000)
     ap.add_argument("--lookups", type=int, default=1 << 28)
-    ap.add_argument("--format", default="f8x128", choices=["f8x128", "f16hi"])
+    ap.add_argument("--format", default="f8v7", choices=["f8v7", "f8x128", "f16hi"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "hybrid", "coop", "flat"])
     ap.add_argument("--ablation-steps", type=int, default=5,
                     help="timed steps per kernel variant in the ablation block (0 = skip)")
@@ -363,7 +363,8 @@ def run_planb(args):
         for name, fmt, kern in (("flat binary search (std::lower_bound analogue)", "f8x128", "flat"),
                                 ("linearized tree, coop 8-lane, 128-bit keys", "f8x128", "coop"),
                                 ("linearized tree, coop 16-lane, 64-bit key halves", "f16hi", "coop"),
-                                ("linearized tree, hybrid smem index + coop L2", "f8x128", "hybrid")):
+                                ("linearized tree, hybrid smem index + coop L2", "f8x128", "hybrid"),
+                                ("hybrid + next hops packed in the leaf line", "f8v7", "hybrid")):
             with pb.Fib(fib_in.hi, fib_in.lo, fib_in.len, fib_in.nh, format=fmt, kernel=kern,
                         device=local) as v:
                 for _ in range(2):
@@ -391,6 +392,8 @@ def run_planb(args):
     kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
     kernel = {"hybrid": f"lookup_hybrid<{st['depth'] - st['smem_levels']}>",
               "flat": "lookup_flat"}.get(kname, f"lookup_coop_{'f16' if args.format == 'f16hi' else 'f8'}<{st['depth']}>")
+    if kname == "hybrid":
+        kernel = f"lookup_hybrid<{st['depth'] - st['smem_levels']},{'true' if args.format == 'f8v7' else 'false'}>"
     achieved = HBM_BYTES_PER_LOOKUP * n / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(kernel),

@@ -47,6 +47,12 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
 /* F16HI: 16 key high halves per 128-byte node, 17-ary (Section 3.2: 128-byte lines give 16-key,
  * 17-ary nodes); a parallel array holds the low halves, read only when a high half ties. */
 #define PLANB_FMT_F16HI 1
+/* F8V7 (default): internal nodes as F8X128; each 128-byte leaf line holds 7 keys and, in its last
+ * 16 bytes, the 7 next hops of those keys. The paper keeps values in a separate array (Section 3.2,
+ * "Separation of Keys and Values") and fetches one after the descent; packing them into the leaf
+ * line removes that dependent memory access. The last interval gets an explicit all-ones key, so the
+ * count at a leaf is always 0..6 and names a slot of that same line. Hybrid kernel only. */
+#define PLANB_FMT_F8V7 2
 
 /* ----------------------------------------------------------------------------- lookup kernels */
 #define PLANB_KERNEL_AUTO 0   /* hybrid for F8X128, coop for F16HI                                */
@@ -65,7 +71,7 @@ typedef struct planb_fib planb_fib; /* opaque; owns all host and device memory o
 
 typedef struct {
     uint32_t struct_size;   /* sizeof(planb_opts); lets the library accept older callers        */
-    int32_t format;         /* PLANB_FMT_*; default PLANB_FMT_F8X128                            */
+    int32_t format;         /* PLANB_FMT_*; default PLANB_FMT_F8V7                              */
     int32_t merge_equal_nh; /* 1: merge neighbouring intervals with equal next hops (Section 3
                                intro allows compressing routes that share a next hop); results
                                are unchanged. Default 0.                                        */
@@ -153,7 +159,8 @@ typedef struct {
 typedef struct {
     uint64_t hi, lo;
     uint8_t len;
-} planb_prefix; /* a withdraw; a prefix that is not present is a counted no-op */
+} planb_prefix; /* a withdraw; a prefix that is not present (including one already withdrawn
+                   earlier in the same batch) is a counted no-op */
 
 /*
  * planb_update — applies a batch of route changes by rebuild-and-swap (Section 3.6, "Dynamic FIB

@@ -19,7 +19,7 @@ LIB_DIR = os.path.join(HERE, "_build", platform.machine())
 
 PLANB_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EDEVICE", -5: "ENODEV", -6: "ETIMEOUT"}
-FORMATS = {"f8x128": 0, "f16hi": 1}
+FORMATS = {"f8x128": 0, "f16hi": 1, "f8v7": 2}
 KERNELS = {"auto": 0, "coop": 1, "hybrid": 2, "flat": 3}
 
 
@@ -177,7 +177,7 @@ def debug_inject(point: int):
 class Fib:
     """One lookup table on a GPU (a planb_fib)."""
 
-    def __init__(self, hi, lo, ln, nh, *, format: str = "f8x128", merge: bool = False,
+    def __init__(self, hi, lo, ln, nh, *, format: str = "f8v7", merge: bool = False,
                  smem_levels: int = -1, device: int | None = None, block_threads: int = 0,
                  ctas_per_sm: int = 0, kernel: str = "auto", variant: str = "libplanb.so"):
         self._lib = load(variant)

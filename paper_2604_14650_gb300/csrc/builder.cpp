@@ -153,17 +153,20 @@ void sweep(const std::vector<Prefix>& canon, bool merge_equal_nh, Intervals& out
   }
 }
 
-int make_layout(uint32_t k, uint64_t n_keys, uint32_t depth_override, Layout& L) {
+int make_layout(uint32_t k, uint64_t n_keys, uint32_t depth_override, Layout& L, uint32_t kl) {
   if (k < 1) return PLANB_EINVAL;
+  if (kl == 0) kl = k;
+  if (kl > k) return PLANB_EINVAL;
   L = Layout();
   L.k = k;
+  L.kl = kl;
   L.b = k + 1;
   L.n_keys = n_keys;
   uint32_t D = 1;
   if (depth_override) {
     D = depth_override;
   } else {
-    u128 cap = k;
+    u128 cap = kl;
     while (cap < n_keys) {
       cap *= L.b;
       D++;
@@ -185,24 +188,25 @@ int make_layout(uint32_t k, uint64_t n_keys, uint32_t depth_override, Layout& L)
   for (uint32_t l = 0; l + 1 < D; l++) lc *= L.b;
   L.leaf_capacity = static_cast<uint64_t>(lc);
   // positions 0 .. n_keys must exist (the count can reach n_keys); leaves beyond are never visited
-  const uint64_t need = (n_keys + 1 + k - 1) / k;
+  const uint64_t need = (n_keys + 1 + kl - 1) / kl;
   L.leaf_nodes = std::min<uint64_t>(L.leaf_capacity, std::max<uint64_t>(need, 1));
   return PLANB_OK;
 }
 
 namespace {
 
-// inclusive end of interval i (the tree key at leaf position i), or all-ones padding
+// inclusive end of interval i (the tree key at leaf position i), or all-ones: for padding
+// (pos >= n_keys) and for the last interval, which ends at 2^128 - 1
 inline u128 key_at(const Intervals& iv, uint64_t n_keys, u128 pos) {
-  if (pos >= n_keys) return ~static_cast<u128>(0);
+  if (pos >= n_keys || pos + 1 >= iv.size()) return ~static_cast<u128>(0);
   return iv.start[static_cast<size_t>(pos) + 1] - 1;
 }
 
 template <class Store>
 void fill_generic(const Intervals& iv, const Layout& L, Store store) {
-  const uint32_t k = L.k, b = L.b, D = L.D;
+  const uint32_t k = L.k, kl = L.kl, b = L.b, D = L.D;
   // internal level l, node p, separator c: the largest key of child c's subtree, i.e. the key at
-  // leaf position (p*b + c + 1) * b^(D-2-l) * k - 1 (padding beyond the real keys)
+  // leaf position (p*b + c + 1) * b^(D-2-l) * kl - 1 (padding beyond the real keys)
   u128 span = 1;  // b^(D-2-l), leaves under one child of a level-l node
   for (uint32_t l = 0; l + 2 < D; l++) span *= b;
   for (uint32_t l = 0; l + 1 < D; l++) {
@@ -210,7 +214,7 @@ void fill_generic(const Intervals& iv, const Layout& L, Store store) {
     for (uint64_t p = 0; p < nodes; p++) {
       const uint64_t node = L.level_node[l] + p;
       for (uint32_t c = 0; c < k; c++) {
-        const u128 pos = (static_cast<u128>(p) * b + c + 1) * span * k - 1;
+        const u128 pos = (static_cast<u128>(p) * b + c + 1) * span * kl - 1;
         store(node, c, key_at(iv, L.n_keys, pos));
       }
     }
@@ -218,8 +222,8 @@ void fill_generic(const Intervals& iv, const Layout& L, Store store) {
   }
   auto leaf_range = [&](uint64_t j0, uint64_t j1) {
     for (uint64_t j = j0; j < j1; j++)
-      for (uint32_t s = 0; s < k; s++)
-        store(L.internal_nodes + j, s, key_at(iv, L.n_keys, static_cast<u128>(j) * k + s));
+      for (uint32_t s = 0; s < kl; s++)
+        store(L.internal_nodes + j, s, key_at(iv, L.n_keys, static_cast<u128>(j) * kl + s));
   };
   const uint64_t leaves = L.leaf_nodes;
   const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
@@ -242,6 +246,26 @@ void fill_f8x128(const Intervals& iv, const Layout& L, uint64_t* nodes) {
   });
 }
 
+void fill_f8v7(const Intervals& iv, const Layout& L, uint64_t* nodes) {
+  fill_generic(iv, L, [nodes, k = L.k](uint64_t node, uint32_t slot, u128 key) {
+    nodes[(node * k + slot) * 2 + 0] = hi64(key);
+    nodes[(node * k + slot) * 2 + 1] = lo64(key);
+  });
+  // slot 7 of every leaf: the next hops of its 7 keys
+  const uint32_t kl = L.kl;
+  for (uint64_t j = 0; j < L.leaf_nodes; j++) {
+    uint64_t w[2] = {0, 0};
+    for (uint32_t s = 0; s < kl; s++) {
+      const uint64_t pos = j * kl + s;
+      const uint64_t h = pos < iv.size() ? iv.nh[pos] : 0;
+      w[s / 4] |= h << (16 * (s % 4));
+    }
+    const uint64_t node = L.internal_nodes + j;
+    nodes[(node * L.k + kl) * 2 + 0] = w[0];
+    nodes[(node * L.k + kl) * 2 + 1] = w[1];
+  }
+}
+
 void fill_f16hi(const Intervals& iv, const Layout& L, uint64_t* node_hi, uint64_t* node_lo) {
   fill_generic(iv, L, [node_hi, node_lo, k = L.k](uint64_t node, uint32_t slot, u128 key) {
     node_hi[node * k + slot] = hi64(key);
@@ -251,7 +275,7 @@ void fill_f16hi(const Intervals& iv, const Layout& L, uint64_t* node_hi, uint64_
 
 uint64_t sidx_entries(const Layout& L, uint32_t S) {
   if (S >= L.D) return L.n_keys;
-  u128 span = L.k;                     // keys under one level-S node: k * b^(D-1-S)
+  u128 span = L.kl;                    // keys under one level-S node: kl * b^(D-1-S)
   for (uint32_t l = S; l + 1 < L.D; l++) span *= L.b;
   u128 cap = 1;
   for (uint32_t l = 0; l < S; l++) cap *= L.b;
@@ -263,7 +287,7 @@ void fill_sidx(const Intervals& iv, const Layout& L, uint32_t S, uint64_t* out) 
   const uint64_t n = sidx_entries(L, S);
   u128 span = 1;
   if (S < L.D) {
-    span = L.k;
+    span = L.kl;
     for (uint32_t l = S; l + 1 < L.D; l++) span *= L.b;
   }
   for (uint64_t q = 0; q < n; q++) {

@@ -137,7 +137,9 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   t->device = device;
   t->n_input = n_input;
   t->n_prefixes = canon.size();
-  int rc = planb::make_layout(k, m - 1, 0, t->L);
+  // F8V7 indexes all m inclusive ends (the last is all-ones); the others the m - 1 finite ones
+  int rc = format == PLANB_FMT_F8V7 ? planb::make_layout(8, m, 0, t->L, 7)
+                                    : planb::make_layout(k, m - 1, 0, t->L);
   if (rc) return rc;
   const uint64_t total = t->L.total_nodes();
   if (t->L.D > 10 || total >= (uint64_t(1) << 32)) return PLANB_EINVAL;
@@ -162,6 +164,8 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   std::vector<uint64_t> host((node_bytes + lo_bytes + sidx_bytes) / 8);
   if (format == PLANB_FMT_F16HI)
     planb::fill_f16hi(iv, t->L, host.data(), host.data() + node_bytes / 8);
+  else if (format == PLANB_FMT_F8V7)
+    planb::fill_f8v7(iv, t->L, host.data());
   else
     planb::fill_f8x128(iv, t->L, host.data());
   if (sidx_n) planb::fill_sidx(iv, t->L, s, host.data() + (node_bytes + lo_bytes) / 8);
@@ -275,7 +279,7 @@ void planb_opts_default(planb_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->struct_size = sizeof(planb_opts);
-  o->format = PLANB_FMT_F8X128;
+  o->format = PLANB_FMT_F8V7;
   o->merge_equal_nh = 0;
   o->smem_levels = -1;
   o->device = -1;
@@ -310,7 +314,10 @@ int planb_build(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint
     std::memcpy(&o, opts, std::min<size_t>(opts->struct_size, sizeof(o)));
     o.struct_size = sizeof(o);
   }
-  if (o.format != PLANB_FMT_F8X128 && o.format != PLANB_FMT_F16HI) return PLANB_EINVAL;
+  if (o.format != PLANB_FMT_F8X128 && o.format != PLANB_FMT_F16HI && o.format != PLANB_FMT_F8V7)
+    return PLANB_EINVAL;
+  if (o.format == PLANB_FMT_F8V7 && o.kernel != PLANB_KERNEL_AUTO && o.kernel != PLANB_KERNEL_HYBRID)
+    return PLANB_EINVAL;
   if (o.block_threads < 0 || o.block_threads > 512 || o.block_threads % 32) return PLANB_EINVAL;
   if (o.kernel < PLANB_KERNEL_AUTO || o.kernel > PLANB_KERNEL_FLAT) return PLANB_EINVAL;
   if (o.format == PLANB_FMT_F16HI && o.kernel > PLANB_KERNEL_COOP) return PLANB_EINVAL;
@@ -437,15 +444,17 @@ int planb_update(planb_fib* f, const planb_route* inserts, size_t n_ins,
       wd[i].nh = 0;
     }
     std::sort(wd.begin(), wd.end(), planb::prefix_less);
+    // withdraws apply one after another: a repeat of a prefix in the same batch finds it gone
+    const size_t n_wd_all = wd.size();
     wd.erase(std::unique(wd.begin(), wd.end(),
                          [](const planb::Prefix& a, const planb::Prefix& b) {
                            return a.p == b.p && a.len == b.len;
                          }),
              wd.end());
+    uint64_t absent = n_wd_all - wd.size();
     // merge: rib minus withdraws, then union inserts (an insert of a present prefix modifies it)
     std::vector<planb::Prefix> mid;
     mid.reserve(f->rib.size());
-    uint64_t absent = 0;
     {
       size_t i = 0, j = 0;
       const auto& R = f->rib;

@@ -13,6 +13,10 @@
 // the popcount at the leaf is the interval index r itself and the next hop is values[r] (the
 // separate value array of Section 3.2).
 //
+// Node formats: F8X128 (8 keys per node, next hops in a separate array), F8V7 (internal nodes as
+// F8X128; a leaf line holds 7 keys and their 7 next hops, so the descent's last load also brings
+// the result), F16HI (16 high halves per node plus a low-half array).
+//
 // Three kernels:
 //   coop    every level by 8-lane groups (16-lane groups for the F16HI format); the first
 //           smem_levels levels are staged in shared memory per CTA. Four addresses per warp step.
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
 // high half equals the address's.
 constexpr int kRounds = 4;  // addresses per group in flight during the L2 levels
 
-template <int DB>
+template <int DB, bool PACKED>
 __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
@@ -277,12 +281,14 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
 #pragma unroll
           for (int i = 0; i < kRounds; i++)
             key[i] = __ldg(p.nodes + static_cast<uint64_t>(nd[i]) * 8u + j);
+          // in a packed leaf, slot 7 holds next hops, not a key
+          const bool keylane = !PACKED || (l + 1 < DB) || (j < 7u);
           bool lt[kRounds], eq[kRounds];
           bool anyeq = false;
 #pragma unroll
           for (int i = 0; i < kRounds; i++) {
-            lt[i] = key[i].x < qh[i];
-            eq[i] = key[i].x == qh[i];
+            lt[i] = keylane & (key[i].x < qh[i]);
+            eq[i] = keylane & (key[i].x == qh[i]);
             anyeq |= eq[i];
           }
           if (__any_sync(kFull, anyeq)) {
@@ -298,18 +304,35 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
             c[i] = __popc(m & gmask);
             if (l + 1 < DB) nd[i] = nd[i] * 9u + 1u + c[i];
           }
-        }
+          if (PACKED && l + 1 == DB) {
+            // the next hop of slot c sits in slot 7 of the same leaf line: lane 7 of the group
+            // picks its 16-bit field and broadcasts it
 #pragma unroll
-        for (int i = 0; i < kRounds; i++) {
-          uint64_t rank = static_cast<uint64_t>(nd[i] - p.internal_nodes) * 8u + c[i];
+            for (int i = 0; i < kRounds; i++) {
 #ifdef PLANB_BOUNDS_CHECK
-          if (rank >= p.n_intervals || nd[i] >= p.total_nodes) {
-            report(p.status, 4u);
-            rank = 0;
-          }
+              if (c[i] > 6u || nd[i] >= p.total_nodes) report(p.status, 4u);
 #endif
-          const uint32_t v = __ldg(p.values + rank);
-          if (j == r0 + i) result = v;
+              const uint32_t ci = c[i] & 7u;
+              const uint64_t w = ci < 4u ? key[i].x : key[i].y;
+              const uint32_t f = static_cast<uint32_t>(w >> (16u * (ci & 3u))) & 0xFFFFu;
+              const uint32_t v = __shfl_sync(kFull, f, gshift + 7u);
+              if (j == r0 + i) result = v;
+            }
+          }
+        }
+        if (!PACKED) {
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            uint64_t rank = static_cast<uint64_t>(nd[i] - p.internal_nodes) * 8u + c[i];
+#ifdef PLANB_BOUNDS_CHECK
+            if (rank >= p.n_intervals || nd[i] >= p.total_nodes) {
+              report(p.status, 4u);
+              rank = 0;
+            }
+#endif
+            const uint32_t v = __ldg(p.values + rank);
+            if (j == r0 + i) result = v;
+          }
         }
       }
       if (ok) p.out[mine] = static_cast<uint16_t>(result);
@@ -351,12 +374,20 @@ KernelFn kernel_for(const DevTable& t) {
       lookup_coop_f16<4>,  lookup_coop_f16<5>, lookup_coop_f16<6>, lookup_coop_f16<7>,
       lookup_coop_f16<8>,  lookup_coop_f16<9>, lookup_coop_f16<10>};
   static const KernelFn hyb[kMaxDepth + 1] = {
-      lookup_hybrid<0>, lookup_hybrid<1>, lookup_hybrid<2>, lookup_hybrid<3>,
-      lookup_hybrid<4>, lookup_hybrid<5>, lookup_hybrid<6>, lookup_hybrid<7>,
-      lookup_hybrid<8>, lookup_hybrid<9>, lookup_hybrid<10>};
+      lookup_hybrid<0, false>, lookup_hybrid<1, false>, lookup_hybrid<2, false>,
+      lookup_hybrid<3, false>, lookup_hybrid<4, false>, lookup_hybrid<5, false>,
+      lookup_hybrid<6, false>, lookup_hybrid<7, false>, lookup_hybrid<8, false>,
+      lookup_hybrid<9, false>, lookup_hybrid<10, false>};
+  static const KernelFn hyb_packed[kMaxDepth + 1] = {
+      lookup_hybrid<0, true>, lookup_hybrid<1, true>, lookup_hybrid<2, true>,
+      lookup_hybrid<3, true>, lookup_hybrid<4, true>, lookup_hybrid<5, true>,
+      lookup_hybrid<6, true>, lookup_hybrid<7, true>, lookup_hybrid<8, true>,
+      lookup_hybrid<9, true>, lookup_hybrid<10, true>};
   const uint32_t D = t.depth;
   if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
   if (t.format == PLANB_FMT_F16HI) return f16[D];
+  if (t.format == PLANB_FMT_F8V7)
+    return (t.kernel == kHybrid && t.smem_levels <= D) ? hyb_packed[D - t.smem_levels] : nullptr;
   switch (t.kernel) {
     case kHybrid: return t.smem_levels <= D ? hyb[D - t.smem_levels] : nullptr;
     case kFlat: return lookup_flat;
@@ -376,7 +407,7 @@ size_t smem_bytes_for(const Layout& L, uint32_t format, uint32_t levels) {
 int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, LaunchCfg& cfg) {
   KernelFn fn = kernel_for(t);
   if (!fn) return PLANB_EINVAL;
-  const bool f8 = t.format == PLANB_FMT_F8X128;
+  const bool f8 = t.format != PLANB_FMT_F16HI;
   const int max_threads = (t.kernel == kHybrid && f8) ? 512 : 256;
   if (threads <= 0) threads = max_threads;
   if (threads % 32 || threads > max_threads) return PLANB_EINVAL;
@@ -428,7 +459,7 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   p.sidx_node = static_cast<uint32_t>(t.sidx_node);
   p.status = d_status;
   uint64_t blocks;
-  if (t.kernel == kFlat && t.format == PLANB_FMT_F8X128) {
+  if (t.kernel == kFlat) {
     blocks = (n + cfg.threads - 1) / cfg.threads;
   } else {
     const uint64_t tiles = (n + 31) / 32;

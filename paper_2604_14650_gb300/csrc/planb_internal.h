@@ -53,7 +53,9 @@ void sweep(const std::vector<Prefix>& canon, bool merge_equal_nh, Intervals& out
 
 // Linearized B+-tree arithmetic (Section 3.2).
 struct Layout {
-  uint32_t k = 0, b = 0, D = 0;        // keys per node, fanout, levels incl. leaves
+  uint32_t k = 0, b = 0, D = 0;        // keys per internal node, fanout, levels incl. leaves
+  uint32_t kl = 0;                     // keys per leaf (k, or k - 1 when the leaf line also holds
+                                       // the next hops of its keys)
   uint64_t n_keys = 0;                 // real keys (m - 1 inclusive interval ends)
   uint64_t internal_nodes = 0;         // complete internal levels: sum_{l<D-1} b^l
   uint64_t leaf_capacity = 0;          // b^(D-1)
@@ -62,12 +64,19 @@ struct Layout {
   uint64_t total_nodes() const { return internal_nodes + leaf_nodes; }
 };
 
-// Smallest D with k * b^(D-1) >= n_keys (or depth_override). Returns PLANB_EINVAL when D > 16.
-int make_layout(uint32_t k, uint64_t n_keys, uint32_t depth_override, Layout& L);
+// Smallest D with kl * b^(D-1) >= n_keys (or depth_override); kl = 0 means kl = k. Returns
+// PLANB_EINVAL when D > 16.
+int make_layout(uint32_t k, uint64_t n_keys, uint32_t depth_override, Layout& L, uint32_t kl = 0);
 
 // Step a4 for PLANB_FMT_F8X128: node-major array of (hi, lo) key pairs, k = 8 per node.
 // keys are the inclusive interval ends start[i+1] - 1; padding is all-ones.
 void fill_f8x128(const Intervals& iv, const Layout& L, uint64_t* nodes /* 2*8*total_nodes */);
+
+// Step a4 for PLANB_FMT_F8V7: internal nodes as F8X128; a leaf holds 7 keys in slots 0..6 and, in
+// slot 7, the 7 next hops of those keys (u16, little-endian, bytes 0..13). The keys are the
+// inclusive interval ends of ALL m intervals (the last one is all-ones), so the count at a leaf is
+// always 0..6 and names a slot of that same leaf. Layout L must come from make_layout(8, m, 0, L, 7).
+void fill_f8v7(const Intervals& iv, const Layout& L, uint64_t* nodes /* 2*8*total_nodes */);
 
 // Step a4 for PLANB_FMT_F16HI: node-major hi halves (16 per node) and the parallel lo halves.
 void fill_f16hi(const Intervals& iv, const Layout& L, uint64_t* node_hi, uint64_t* node_lo);

@@ -62,8 +62,8 @@ def oracle_answer(ref, xh, xl):
     return oracle.Trie(h, l, L, n).lookup(xh, xl)
 
 
-@pytest.mark.parametrize("fmt,kernel", [("f8x128", "hybrid"), ("f8x128", "coop"),
-                                        ("f16hi", "coop")])
+@pytest.mark.parametrize("fmt,kernel", [("f8v7", "hybrid"), ("f8x128", "hybrid"),
+                                        ("f8x128", "coop"), ("f16hi", "coop")])
 def test_update_batches_match_oracle_rebuild(fmt, kernel):
     f = synth.gen_fib(20_000, seed=81, nh_max=4095)
     xh, xl = synth.gen_trace(f, 400_000, seed=82)
