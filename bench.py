@@ -360,11 +360,18 @@ def run_planb(args):
     ablation = None
     if args.ablation_steps > 0:
         ablation = {}
+        fib.lookup_ptr(hp, lp, n, op, stream)
+        stream.synchronize()
+        ref_out = d_out.clone()
         for name, fmt, kern in (("flat binary search (std::lower_bound analogue)", "f8x128", "flat"),
                                 ("linearized tree, coop 8-lane, 128-bit keys", "f8x128", "coop"),
                                 ("linearized tree, coop 16-lane, 64-bit key halves", "f16hi", "coop"),
                                 ("linearized tree, hybrid smem index + coop L2", "f8x128", "hybrid"),
-                                ("hybrid + next hops packed in the leaf line", "f8v7", "hybrid")):
+                                ("hybrid + next hops packed in the leaf line", "f8v7", "hybrid"),
+                                ("learned position model (RMI, MLP root) + tree, 128-bit keys",
+                                 "f8x128", "learned"),
+                                ("learned position model (RMI, MLP root) + tree, packed leaves",
+                                 "f8v7", "learned")):
             with pb.Fib(fib_in.hi, fib_in.lo, fib_in.len, fib_in.nh, format=fmt, kernel=kern,
                         device=local) as v:
                 for _ in range(2):
@@ -380,6 +387,14 @@ def run_planb(args):
                     "what": name, "B_lookups_per_s": n * args.ablation_steps / a.elapsed_time(b) / 1e6,
                     "depth": vs["depth"], "smem_levels": vs["smem_levels"],
                     "smem_bytes": vs["smem_bytes"], "threads": vs["threads"], "ctas": vs["ctas"]}
+                if kern == "learned":
+                    ablation[f"{fmt}/{kern}"]["model"] = {
+                        k[6:]: vs[k] for k in ("model_leaves", "model_iters", "model_max_err",
+                                               "model_loss0", "model_loss", "model_covered",
+                                               "model_mean_err", "model_train_ms")}
+                # results of every variant equal the headline launch's (exactness across kernels)
+                same = torch.equal(d_out.view(torch.int16), ref_out)
+                ablation[f"{fmt}/{kern}"]["same_results_as_headline"] = bool(same)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -416,6 +431,11 @@ def run_planb(args):
         "e2e": e2e,
         "latency": lat,
         "ablation": ablation,
+        "learned_vs_plain": ({"learned_B_lookups_per_s": ablation["f8v7/learned"]["B_lookups_per_s"],
+                              "plain_tree_B_lookups_per_s": ablation["f8v7/hybrid"]["B_lookups_per_s"],
+                              "paper_plain_tree_coop_B_lookups_per_s":
+                                  ablation["f8x128/coop"]["B_lookups_per_s"]}
+                             if ablation else None),
         "clocks": clk,
         "gpu_launches": args.steps,
     }

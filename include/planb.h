@@ -66,6 +66,13 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
 /* flat (F8X128 only): per-thread binary search over the sorted interval keys in global memory;
  * the GPU analogue of the paper's ablation baseline (Section 4.5, std::lower_bound) */
 #define PLANB_KERNEL_FLAT 3
+/* learned (F8X128 or F8V7): the hybrid kernel whose shared-memory search starts from a learned
+ * position model — a two-layer recursive model index (a 16-unit FP32 MLP root trained on the GPU
+ * at build time, linear leaves) that predicts each address's interval rank with a recorded per-leaf
+ * error bound; a bounded search inside that window fixes the rank exactly, and leaves whose bound
+ * exceeds 64 ranks (or addresses the window does not bracket) take the plain tree path. The paper
+ * has no learned component; this follows the learned-index idea on top of its tree. */
+#define PLANB_KERNEL_LEARNED 4
 
 typedef struct planb_fib planb_fib; /* opaque; owns all host and device memory of one table */
 
@@ -81,7 +88,9 @@ typedef struct {
     int32_t block_threads;  /* threads per CTA of the lookup kernel; 0 = automatic               */
     int32_t ctas_per_sm;    /* persistent CTAs per SM; 0 = as many as fit                        */
     int32_t kernel;         /* PLANB_KERNEL_*; default PLANB_KERNEL_AUTO                          */
-    int32_t reserved[7];    /* zero                                                              */
+    int32_t model_leaves;   /* learned: leaf models L; 0 = automatic                              */
+    int32_t model_iters;    /* learned: Adam steps of the root's training; -1 = default (2000)    */
+    int32_t reserved[5];    /* zero                                                              */
 } planb_opts;
 
 /* Fills *o with the defaults. */
@@ -109,6 +118,15 @@ typedef struct {
     uint32_t threads;          /* threads per CTA of the lookup kernel                           */
     uint32_t ctas;             /* persistent grid size (CTAs)                                    */
     uint32_t smem_bytes;       /* dynamic shared memory per CTA                                  */
+    uint32_t model_leaves;     /* learned: leaf models (0 for the other kernels)                 */
+    uint32_t model_iters;      /* learned: Adam steps run                                        */
+    uint32_t model_max_err;    /* learned: largest per-leaf bound, in ranks                      */
+    uint32_t reserved0;
+    double model_loss0;        /* learned: root's mean squared CDF error before training         */
+    double model_loss;         /* learned: ... and after                                         */
+    double model_covered;      /* learned: share of keys in leaves within the window limit       */
+    double model_mean_err;     /* learned: mean bound over those keys                            */
+    double model_train_ms;     /* learned: training time (GPU)                                   */
 } planb_stats_t;
 
 /*
@@ -193,6 +211,27 @@ void planb_destroy(planb_fib *fib);
 
 /* planb_strerror — a static string naming a PLANB_* code. */
 const char *planb_strerror(int code);
+
+/* ------------------------------------------------------ learned-model kernels (for checking) */
+
+/*
+ * planb_mlp_grad — the training kernels' full-batch gradient: for the root MLP
+ * y(u) = b2 + sum_h w2[h] max(w1[h] u + b1[h], 0) (16 hidden units) and the loss
+ * L = (1/n) sum_i (y(u_i) - t_i)^2, writes dL/dtheta to grad[49] and L to *loss.
+ *   d_u, d_t: device float arrays of n entries; w, grad: host float[49] in the order w1[16],
+ *   b1[16], w2[16], b2. Runs on `stream` and waits for it. Uses the current device.
+ * Errors: PLANB_EINVAL (null pointer, n >= 2^32), PLANB_ENOMEM, PLANB_ECUDA.
+ */
+int planb_mlp_grad(const float *d_u, const float *d_t, size_t n, const float *w, float *grad,
+                   double *loss, planb_stream_t stream);
+
+/*
+ * planb_mlp_forward — y(u) for every entry of the device array d_u (n floats) into d_y (device);
+ * w as in planb_mlp_grad. Asynchronous on `stream`.
+ * Errors: PLANB_EINVAL, PLANB_ECUDA.
+ */
+int planb_mlp_forward(const float *d_u, size_t n, const float *w, float *d_y,
+                      planb_stream_t stream);
 
 /* ------------------------------------------------------------------ host-only entry points */
 /* These run on the host alone and need no GPU; they expose the build steps for inspection.  */

@@ -20,7 +20,7 @@ LIB_DIR = os.path.join(HERE, "_build", platform.machine())
 PLANB_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EDEVICE", -5: "ENODEV", -6: "ETIMEOUT"}
 FORMATS = {"f8x128": 0, "f16hi": 1, "f8v7": 2}
-KERNELS = {"auto": 0, "coop": 1, "hybrid": 2, "flat": 3}
+KERNELS = {"auto": 0, "coop": 1, "hybrid": 2, "flat": 3, "learned": 4}
 
 
 class PlanbError(RuntimeError):
@@ -32,7 +32,8 @@ class PlanbError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("format", C.c_int32), ("merge_equal_nh", C.c_int32),
                 ("smem_levels", C.c_int32), ("device", C.c_int32), ("block_threads", C.c_int32),
-                ("ctas_per_sm", C.c_int32), ("kernel", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("ctas_per_sm", C.c_int32), ("kernel", C.c_int32), ("model_leaves", C.c_int32),
+                ("model_iters", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Stats(C.Structure):
@@ -43,7 +44,11 @@ class Stats(C.Structure):
                 ("node_bytes", C.c_uint64), ("value_bytes", C.c_uint64), ("version", C.c_uint64),
                 ("withdraw_absent", C.c_uint64), ("build_ms", C.c_double),
                 ("upload_ms", C.c_double), ("kernel", C.c_uint32), ("threads", C.c_uint32),
-                ("ctas", C.c_uint32), ("smem_bytes", C.c_uint32)]
+                ("ctas", C.c_uint32), ("smem_bytes", C.c_uint32), ("model_leaves", C.c_uint32),
+                ("model_iters", C.c_uint32), ("model_max_err", C.c_uint32),
+                ("reserved0", C.c_uint32), ("model_loss0", C.c_double), ("model_loss", C.c_double),
+                ("model_covered", C.c_double), ("model_mean_err", C.c_double),
+                ("model_train_ms", C.c_double)]
 
 
 class LayoutT(C.Structure):
@@ -80,6 +85,8 @@ _SIGS = {
     "planb_layout_info": (C.c_int, [C.c_uint32, C.c_uint64, C.c_uint32, _vp]),
     "planb_child_index": (C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32]),
     "planb_debug_inject": (C.c_int, [C.c_int]),
+    "planb_mlp_grad": (C.c_int, [_vp, _vp, _sz, _vp, _vp, C.POINTER(C.c_double), _vp]),
+    "planb_mlp_forward": (C.c_int, [_vp, _sz, _vp, _vp, _vp]),
 }
 
 
@@ -174,12 +181,37 @@ def debug_inject(point: int):
     _check(load().planb_debug_inject(point), "planb_debug_inject")
 
 
+def mlp_grad(u, t, w, stream=None):
+    """Root-MLP loss and gradient by the library's training kernels (CUDA float32 tensors u, t;
+    w: 49 floats w1, b1, w2, b2). Returns (loss, grad as float32 numpy array)."""
+    wv = np.ascontiguousarray(w, dtype=np.float32)
+    g = np.zeros(49, dtype=np.float32)
+    loss = C.c_double(0.0)
+    _check(load().planb_mlp_grad(C.c_void_p(u.data_ptr()), C.c_void_p(t.data_ptr()), u.numel(),
+                                 _ptr(wv), _ptr(g), C.byref(loss), _stream_handle(stream)),
+           "planb_mlp_grad")
+    return loss.value, g
+
+
+def mlp_forward(u, w, out=None, stream=None):
+    """y = root(u) by the library's inference kernel (CUDA float32 tensors)."""
+    import torch
+    wv = np.ascontiguousarray(w, dtype=np.float32)
+    if out is None:
+        out = torch.empty_like(u)
+    _check(load().planb_mlp_forward(C.c_void_p(u.data_ptr()), u.numel(), _ptr(wv),
+                                    C.c_void_p(out.data_ptr()), _stream_handle(stream)),
+           "planb_mlp_forward")
+    return out
+
+
 class Fib:
     """One lookup table on a GPU (a planb_fib)."""
 
     def __init__(self, hi, lo, ln, nh, *, format: str = "f8v7", merge: bool = False,
                  smem_levels: int = -1, device: int | None = None, block_threads: int = 0,
-                 ctas_per_sm: int = 0, kernel: str = "auto", variant: str = "libplanb.so"):
+                 ctas_per_sm: int = 0, kernel: str = "auto", model_leaves: int = 0,
+                 model_iters: int = -1, variant: str = "libplanb.so"):
         self._lib = load(variant)
         self._h = None
         hi, lo, ln, nh = _np(hi, np.uint64), _np(lo, np.uint64), _np(ln, np.uint8), _np(nh, np.uint16)
@@ -194,6 +226,8 @@ class Fib:
         o.block_threads = block_threads
         o.ctas_per_sm = ctas_per_sm
         o.kernel = KERNELS[kernel]
+        o.model_leaves = model_leaves
+        o.model_iters = model_iters
         h = C.c_void_p()
         _check(self._lib.planb_build(_ptr(hi), _ptr(lo), _ptr(ln), _ptr(nh), hi.size, C.byref(o),
                                      C.byref(h)), "planb_build")

@@ -11,6 +11,7 @@
 #include <new>
 #include <vector>
 
+#include "learned.cuh"
 #include "planb_internal.h"
 
 using planb::u128;
@@ -46,6 +47,7 @@ struct Table {
   planb::LaunchCfg cfg;
   uint64_t n_input = 0, n_prefixes = 0;
   double build_ms = 0, upload_ms = 0;
+  planb::LearnedBuild model;  // learned kernel only
   ~Table() {
     if (mem) {
       DeviceGuard g(device);
@@ -111,9 +113,9 @@ uint32_t auto_smem_levels(const planb::Layout& L, uint32_t format) {
 // levels resolved by the hybrid kernel's shared-memory index: every key when they fit, else the
 // deepest level whose subtree maxima fit
 uint32_t auto_index_levels(const planb::Layout& L, size_t budget) {
-  if (planb::sidx_entries(L, L.D) * 16 <= budget) return L.D;
+  if (planb::sidx_entries(L, L.D) * 8 <= budget) return L.D;   // 8 bytes (high half) per entry
   uint32_t s = 0;
-  while (s + 1 < L.D && planb::sidx_entries(L, s + 1) * 16 <= budget) s++;
+  while (s + 1 < L.D && planb::sidx_entries(L, s + 1) * 8 <= budget) s++;
   return s;
 }
 
@@ -132,6 +134,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   uint32_t kernel = static_cast<uint32_t>(o.kernel);
   if (format == PLANB_FMT_F16HI) kernel = planb::kCoop;
   else if (kernel == PLANB_KERNEL_AUTO) kernel = planb::kHybrid;
+  const bool learned = kernel == planb::kLearned;
   const uint64_t m = iv.size();
   auto t = std::make_shared<Table>();
   t->device = device;
@@ -145,10 +148,23 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   if (t->L.D > 10 || total >= (uint64_t(1) << 32)) return PLANB_EINVAL;
   // levels resolved in shared memory
   uint32_t s;
-  if (kernel == planb::kHybrid) {
+  uint32_t model_leaves = 0;
+  if (learned) {
+    // leaf models: about one per 128 keys, a power of two in [64, 2048], then the index gets the
+    // rest of the shared-memory budget
+    uint32_t want = o.model_leaves > 0 ? static_cast<uint32_t>(o.model_leaves) : 64u;
+    if (o.model_leaves <= 0)
+      while (want < 2048u && static_cast<uint64_t>(want) * 128u < m) want <<= 1;
+    model_leaves = std::min<uint32_t>(want, 8192u);
+    const size_t leaf_bytes = static_cast<size_t>(model_leaves) * 18u;
+    const size_t budget = kSmemBudget > leaf_bytes + 8192 ? kSmemBudget - leaf_bytes : 8192;
+    s = o.smem_levels < 0 ? auto_index_levels(t->L, budget)
+                          : std::min<uint32_t>(o.smem_levels, t->L.D);
+    while (s > 0 && planb::sidx_entries(t->L, s) * 8 + leaf_bytes > 200 * 1024) s--;
+  } else if (kernel == planb::kHybrid) {
     s = o.smem_levels < 0 ? auto_index_levels(t->L, kSmemBudget)
                           : std::min<uint32_t>(o.smem_levels, t->L.D);
-    while (s > 0 && planb::sidx_entries(t->L, s) * 16 > 200 * 1024) s--;
+    while (s > 0 && planb::sidx_entries(t->L, s) * 8 > 200 * 1024) s--;
   } else if (kernel == planb::kFlat) {
     s = 0;
   } else {
@@ -156,11 +172,14 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                           : std::min<uint32_t>(o.smem_levels, t->L.D);
     while (s > 0 && planb::smem_bytes_for(t->L, format, s) > 200 * 1024) s--;
   }
-  const uint64_t sidx_n = kernel == planb::kHybrid ? planb::sidx_entries(t->L, s) : 0;
+  const uint64_t sidx_n =
+      (kernel == planb::kHybrid || learned) ? planb::sidx_entries(t->L, s) : 0;
   const size_t node_bytes = static_cast<size_t>(total) * 128;
   const size_t lo_bytes = format == PLANB_FMT_F16HI ? node_bytes : 0;
   const size_t sidx_bytes = ((sidx_n * 16 + 127) / 128) * 128;
   const size_t val_bytes = ((static_cast<size_t>(m) * 2 + 255) / 256) * 256;
+  const size_t model_bytes =
+      learned ? ((static_cast<size_t>(model_leaves) * 18 + 255) / 256) * 256 : 0;
   std::vector<uint64_t> host((node_bytes + lo_bytes + sidx_bytes) / 8);
   if (format == PLANB_FMT_F16HI)
     planb::fill_f16hi(iv, t->L, host.data(), host.data() + node_bytes / 8);
@@ -174,7 +193,19 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   auto t1 = std::chrono::steady_clock::now();
   DeviceGuard g(device);
   if (!g.ok) return PLANB_ECUDA;
-  t->bytes = node_bytes + lo_bytes + sidx_bytes + val_bytes;
+  if (learned) {
+    // bucket width of the index: keys under one level-s subtree (1 when it holds every key)
+    uint64_t span = 1;
+    if (s < t->L.D) {
+      span = t->L.kl;
+      for (uint32_t l = s; l + 1 < t->L.D; l++) span *= t->L.b;
+    }
+    const uint32_t iters = o.model_iters < 0 ? 2000u : static_cast<uint32_t>(o.model_iters);
+    rc = planb::build_learned(iv, static_cast<uint32_t>(std::min<uint64_t>(span, 1u << 30)),
+                              model_leaves, iters, 0.01f, 64u, t->model);
+    if (rc) return rc;
+  }
+  t->bytes = node_bytes + lo_bytes + sidx_bytes + val_bytes + model_bytes;
   if (g_inject.load() == 2) {
     g_inject.store(0);
     return PLANB_ENOMEM;
@@ -189,6 +220,17 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   if (cudaMemcpy(base, host.data(), head, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(base + head, iv.nh.data(), m * 2, cudaMemcpyHostToDevice) != cudaSuccess)
     return PLANB_ECUDA;
+  if (learned) {
+    char* mb = base + head + val_bytes;
+    const size_t lb = static_cast<size_t>(model_leaves) * sizeof(planb::LeafModel);
+    if (cudaMemcpy(mb, t->model.leaves.data(), lb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(mb + lb, t->model.err.data(), model_leaves * 2, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      return PLANB_ECUDA;
+    t->dt.leaves = reinterpret_cast<const planb::LeafModel*>(mb);
+    t->dt.leaf_err = reinterpret_cast<const uint16_t*>(mb + lb);
+    t->dt.lp = t->model.P;
+  }
   t->dt.nodes = base;
   t->dt.nodes_lo = lo_bytes ? reinterpret_cast<const uint64_t*>(base + node_bytes) : nullptr;
   t->dt.sidx = sidx_n ? reinterpret_cast<const uint64_t*>(base + node_bytes + lo_bytes) : nullptr;
@@ -286,6 +328,8 @@ void planb_opts_default(planb_opts* o) {
   o->block_threads = 0;
   o->ctas_per_sm = 0;
   o->kernel = PLANB_KERNEL_AUTO;
+  o->model_leaves = 0;
+  o->model_iters = -1;
 }
 
 const char* planb_strerror(int code) {
@@ -316,11 +360,13 @@ int planb_build(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint
   }
   if (o.format != PLANB_FMT_F8X128 && o.format != PLANB_FMT_F16HI && o.format != PLANB_FMT_F8V7)
     return PLANB_EINVAL;
-  if (o.format == PLANB_FMT_F8V7 && o.kernel != PLANB_KERNEL_AUTO && o.kernel != PLANB_KERNEL_HYBRID)
+  if (o.format == PLANB_FMT_F8V7 && o.kernel != PLANB_KERNEL_AUTO &&
+      o.kernel != PLANB_KERNEL_HYBRID && o.kernel != PLANB_KERNEL_LEARNED)
     return PLANB_EINVAL;
   if (o.block_threads < 0 || o.block_threads > 512 || o.block_threads % 32) return PLANB_EINVAL;
-  if (o.kernel < PLANB_KERNEL_AUTO || o.kernel > PLANB_KERNEL_FLAT) return PLANB_EINVAL;
+  if (o.kernel < PLANB_KERNEL_AUTO || o.kernel > PLANB_KERNEL_LEARNED) return PLANB_EINVAL;
   if (o.format == PLANB_FMT_F16HI && o.kernel > PLANB_KERNEL_COOP) return PLANB_EINVAL;
+  if (o.model_leaves < 0 || o.model_leaves > 8192 || o.model_iters < -1) return PLANB_EINVAL;
   try {
     int dev = o.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return PLANB_ENODEV;
@@ -540,6 +586,16 @@ int planb_stats(const planb_fib* fib_c, planb_stats_t* out) {
   out->threads = static_cast<uint32_t>(t->cfg.threads);
   out->ctas = static_cast<uint32_t>(t->cfg.blocks);
   out->smem_bytes = static_cast<uint32_t>(t->cfg.smem_bytes);
+  if (t->dt.kernel == planb::kLearned) {
+    out->model_leaves = t->model.P.leaves;
+    out->model_iters = t->model.iters;
+    out->model_max_err = t->model.max_err;
+    out->model_loss0 = t->model.loss0;
+    out->model_loss = t->model.loss;
+    out->model_covered = t->model.covered;
+    out->model_mean_err = t->model.mean_err;
+    out->model_train_ms = t->model.train_ms;
+  }
   return PLANB_OK;
 }
 
@@ -624,6 +680,22 @@ uint64_t planb_child_index(uint32_t keys_per_node, uint32_t d, uint64_t j, uint3
     pw *= b;
   }
   return (level + j * b + c) * k;
+}
+
+int planb_mlp_grad(const float* d_u, const float* d_t, size_t n, const float* w, float* grad,
+                   double* loss, planb_stream_t stream) {
+  if ((n && (!d_u || !d_t)) || !w || !grad || !loss) return PLANB_EINVAL;
+  try {
+    return planb::mlp_grad_host(d_u, d_t, n, w, grad, loss, reinterpret_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return PLANB_ENOMEM;
+  }
+}
+
+int planb_mlp_forward(const float* d_u, size_t n, const float* w, float* d_y,
+                      planb_stream_t stream) {
+  if ((n && (!d_u || !d_y)) || !w) return PLANB_EINVAL;
+  return planb::mlp_forward_host(d_u, n, w, d_y, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int planb_debug_inject(int point) {

@@ -1,0 +1,366 @@
+// Learned position model (the root MLP of a two-layer recursive model index): training on the GPU
+// by hand-written forward/backward and Adam kernels, leaf fitting, and the error bounds the lookup
+// kernel relies on. Inference arithmetic lives in learned.cuh and is shared with lookup.cu.
+//
+// Training fits the root to the empirical CDF of the keys: targets t_i = (i + 0.5) / n for the i-th
+// key's range-reduced high half u_i, loss L = mean (y(u_i) - t_i)^2, full batch. The gradient
+// kernel accumulates per-thread sums, reduces them per block in a fixed order and writes one row
+// of 50 partials (49 gradients + the loss) per block; the update kernel adds the rows in block
+// order in double precision and applies Adam (Kingma and Ba, 2015). The result is deterministic for
+// a given grid. The iterations are captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "learned.cuh"
+#include "planb_internal.h"
+
+namespace planb {
+
+namespace {
+
+constexpr int kRow = kMlpParams + 1;     // 49 gradients + loss
+constexpr int kGradThreads = 256;
+constexpr int kGradBlocks = 304;         // fixed grid: the partial sums' order never changes
+
+__global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(const float* __restrict__ u,
+                                                                const float* __restrict__ t,
+                                                                uint32_t n,
+                                                                const float* __restrict__ w,
+                                                                float* __restrict__ partials) {
+  __shared__ float sw[kMlpParams];
+  __shared__ float red[kGradThreads / 32][kRow];
+  if (threadIdx.x < kMlpParams) sw[threadIdx.x] = w[threadIdx.x];
+  __syncthreads();
+  float g[kRow];
+#pragma unroll
+  for (int k = 0; k < kRow; k++) g[k] = 0.0f;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float ui = u[i];
+    float z[kMlpHidden];
+    float y = sw[3 * kMlpHidden];
+#pragma unroll
+    for (int h = 0; h < kMlpHidden; h++) {
+      z[h] = fmaf(sw[h], ui, sw[kMlpHidden + h]);
+      y = fmaf(sw[2 * kMlpHidden + h], fmaxf(z[h], 0.0f), y);
+    }
+    const float r = y - t[i];
+    const float dy = 2.0f * r;              // the 1/n of the mean is applied after the reduction
+    g[3 * kMlpHidden] += dy;
+    g[kMlpParams] = fmaf(r, r, g[kMlpParams]);
+#pragma unroll
+    for (int h = 0; h < kMlpHidden; h++) {
+      const bool on = z[h] > 0.0f;
+      g[2 * kMlpHidden + h] = fmaf(dy, on ? z[h] : 0.0f, g[2 * kMlpHidden + h]);
+      const float dz = on ? dy * sw[2 * kMlpHidden + h] : 0.0f;
+      g[h] = fmaf(dz, ui, g[h]);
+      g[kMlpHidden + h] += dz;
+    }
+  }
+  const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kRow; k++) {
+    float v = g[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+    if (lane == 0) red[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kRow) {
+    float s = 0.0f;
+    for (int wi = 0; wi < kGradThreads / 32; wi++) s += red[wi][threadIdx.x];
+    partials[blockIdx.x * kRow + threadIdx.x] = s;
+  }
+}
+
+// Sums the partial rows (block order, double) into grad[49] and loss; with adam != 0 also applies
+// one Adam step to w (moments m, v; step counter in *step, incremented here).
+__global__ void reduce_adam_kernel(const float* __restrict__ partials, uint32_t nblocks, uint32_t n,
+                                   float* __restrict__ w, float* __restrict__ m,
+                                   float* __restrict__ v, int* __restrict__ step, float lr,
+                                   int adam, float* __restrict__ grad_out,
+                                   double* __restrict__ loss_out) {
+  const int k = threadIdx.x;
+  if (k >= kRow) return;
+  double s = 0.0;
+  for (uint32_t b = 0; b < nblocks; b++) s += static_cast<double>(partials[b * kRow + k]);
+  const double mean = n ? s / static_cast<double>(n) : 0.0;
+  if (k == kMlpParams) {
+    if (loss_out) *loss_out = mean;
+    return;
+  }
+  if (grad_out) grad_out[k] = static_cast<float>(mean);
+  if (!adam) return;
+  const int tstep = *step + 1;
+  const float gk = static_cast<float>(mean);
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float mk = b1 * m[k] + (1.0f - b1) * gk;
+  const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+  m[k] = mk;
+  v[k] = vk;
+  const float mh = mk / (1.0f - powf(b1, static_cast<float>(tstep)));
+  const float vh = vk / (1.0f - powf(b2, static_cast<float>(tstep)));
+  w[k] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+__global__ void bump_step(int* step) { *step += 1; }
+
+__global__ void mlp_forward_kernel(const float* __restrict__ u, uint32_t n, MlpWeights w,
+                                   float* __restrict__ y) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = mlp_eval(w, u[i]);
+}
+
+__global__ void leaf_assign_kernel(const uint64_t* __restrict__ khi, uint32_t n, LearnedParams P,
+                                   uint32_t* __restrict__ leaf) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    leaf[i] = predict_leaf(P, khi[i]);
+}
+
+__global__ void leaf_error_kernel(const uint64_t* __restrict__ khi, uint32_t n, LearnedParams P,
+                                  const LeafModel* __restrict__ leaves,
+                                  uint32_t* __restrict__ err) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t l = predict_leaf(P, khi[i]);
+    const uint32_t p = predict_rank(P, leaves[l], khi[i]);
+    const uint32_t e = p > i ? p - i : i - p;
+    atomicMax(err + l, e);
+  }
+}
+
+void init_weights(MlpWeights& w) {
+  // knots evenly spaced over [0, 1); output = the first unit = u (the untrained root is the
+  // identity, i.e. plain linear range reduction)
+  for (int h = 0; h < kMlpHidden; h++) {
+    w.w1[h] = 1.0f;
+    w.b1[h] = -static_cast<float>(h) / kMlpHidden;
+    w.w2[h] = h == 0 ? 1.0f : 0.0f;
+  }
+  w.b2 = 0.0f;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  bool alloc(size_t bytes) { return cudaMalloc(&p, bytes) == cudaSuccess; }
+  template <class T>
+  T* as() { return static_cast<T*>(p); }
+};
+
+}  // namespace
+
+int mlp_grad_host(const float* d_u, const float* d_t, size_t n, const float* w_host,
+                  float* grad_host, double* loss_host, cudaStream_t st) {
+  if (n >= (size_t(1) << 32)) return PLANB_EINVAL;
+  DevBuf part, wb, gb, lb;
+  if (!part.alloc(kGradBlocks * kRow * sizeof(float)) || !wb.alloc(kMlpParams * sizeof(float)) ||
+      !gb.alloc(kMlpParams * sizeof(float)) || !lb.alloc(sizeof(double))) {
+    cudaGetLastError();
+    return PLANB_ENOMEM;
+  }
+  if (cudaMemcpyAsync(wb.p, w_host, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return PLANB_ECUDA;
+  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(d_u, d_t, static_cast<uint32_t>(n),
+                                                        wb.as<float>(), part.as<float>());
+  reduce_adam_kernel<<<1, 64, 0, st>>>(part.as<float>(), kGradBlocks, static_cast<uint32_t>(n),
+                                       nullptr, nullptr, nullptr, nullptr, 0.0f, 0, gb.as<float>(),
+                                       lb.as<double>());
+  if (cudaGetLastError() != cudaSuccess) return PLANB_ECUDA;
+  if (cudaMemcpyAsync(grad_host, gb.p, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(loss_host, lb.p, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return PLANB_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+int mlp_forward_host(const float* d_u, size_t n, const float* w_host, float* d_y, cudaStream_t st) {
+  if (n >= (size_t(1) << 32)) return PLANB_EINVAL;
+  if (n == 0) return PLANB_OK;
+  MlpWeights w;
+  std::copy(w_host, w_host + kMlpHidden, w.w1);
+  std::copy(w_host + kMlpHidden, w_host + 2 * kMlpHidden, w.b1);
+  std::copy(w_host + 2 * kMlpHidden, w_host + 3 * kMlpHidden, w.w2);
+  w.b2 = w_host[3 * kMlpHidden];
+  const uint32_t blocks = static_cast<uint32_t>(std::min<size_t>((n + 255) / 256, 4096));
+  mlp_forward_kernel<<<blocks, 256, 0, st>>>(d_u, static_cast<uint32_t>(n), w, d_y);
+  return cudaGetLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+int build_learned(const Intervals& iv, uint32_t span, uint32_t leaves, uint32_t iters, float lr,
+                  uint32_t max_window, LearnedBuild& out) {
+  auto t0 = std::chrono::steady_clock::now();
+  const uint64_t m = iv.size();
+  const uint64_t n64 = m > 0 ? m - 1 : 0;       // finite keys: the inclusive ends start[i+1] - 1
+  if (n64 >= (uint64_t(1) << 24)) return PLANB_EINVAL;   // ranks must stay exact in FP32
+  const uint32_t n = static_cast<uint32_t>(n64);
+  out = LearnedBuild();
+  LearnedParams& P = out.P;
+  init_weights(P.mlp);
+  P.leaves = std::max<uint32_t>(1, leaves);
+  P.span = span;
+  P.inv_span = 1.0f / static_cast<float>(span);
+  P.n_keys = static_cast<uint32_t>(m);           // counts range over [0, m - 1]
+  out.leaves.assign(P.leaves, LeafModel{0, 0.0f, 0.0f});
+  out.err.assign(P.leaves, kLeafFallback);
+  if (n < 2) return PLANB_OK;                    // nothing to learn: every leaf takes the tree path
+  std::vector<uint64_t> khi(n);
+  for (uint32_t i = 0; i < n; i++) khi[i] = hi64(iv.start[i + 1] - 1);
+  P.kmin = khi[0];
+  const uint64_t range = khi[n - 1] - khi[0];
+  P.inv_range = range ? 1.0f / static_cast<float>(range) : 0.0f;
+  std::vector<float> hu(n), ht(n);
+  for (uint32_t i = 0; i < n; i++) {
+    hu[i] = std::min(static_cast<float>(khi[i] - P.kmin) * P.inv_range, 1.0f);
+    ht[i] = (static_cast<float>(i) + 0.5f) / static_cast<float>(n);
+  }
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return PLANB_ECUDA;
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } sg{st};
+  DevBuf dk, du, dt, dpart, dw, dm, dv, dstep, dloss, dleaf, dleaves, derr;
+  if (!dk.alloc(n * 8ull) || !du.alloc(n * 4ull) || !dt.alloc(n * 4ull) ||
+      !dpart.alloc(kGradBlocks * kRow * 4ull) || !dw.alloc(kMlpParams * 4) ||
+      !dm.alloc(kMlpParams * 4) || !dv.alloc(kMlpParams * 4) || !dstep.alloc(sizeof(int)) ||
+      !dloss.alloc(sizeof(double)) || !dleaf.alloc(n * 4ull) ||
+      !dleaves.alloc(P.leaves * sizeof(LeafModel)) || !derr.alloc(P.leaves * 4ull)) {
+    cudaGetLastError();
+    return PLANB_ENOMEM;
+  }
+  float w0[kMlpParams];
+  std::copy(P.mlp.w1, P.mlp.w1 + kMlpHidden, w0);
+  std::copy(P.mlp.b1, P.mlp.b1 + kMlpHidden, w0 + kMlpHidden);
+  std::copy(P.mlp.w2, P.mlp.w2 + kMlpHidden, w0 + 2 * kMlpHidden);
+  w0[3 * kMlpHidden] = P.mlp.b2;
+  bool ok = cudaMemcpyAsync(dk.p, khi.data(), n * 8ull, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(du.p, hu.data(), n * 4ull, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(dt.p, ht.data(), n * 4ull, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(dw.p, w0, sizeof(w0), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemsetAsync(dm.p, 0, kMlpParams * 4, st) == cudaSuccess &&
+            cudaMemsetAsync(dv.p, 0, kMlpParams * 4, st) == cudaSuccess &&
+            cudaMemsetAsync(dstep.p, 0, sizeof(int), st) == cudaSuccess;
+  if (!ok) return PLANB_ECUDA;
+  // loss before training
+  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(du.as<float>(), dt.as<float>(), n,
+                                                        dw.as<float>(), dpart.as<float>());
+  reduce_adam_kernel<<<1, 64, 0, st>>>(dpart.as<float>(), kGradBlocks, n, nullptr, nullptr,
+                                       nullptr, nullptr, 0.0f, 0, nullptr, dloss.as<double>());
+  if (cudaMemcpyAsync(&out.loss0, dloss.p, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+      cudaSuccess)
+    return PLANB_ECUDA;
+  // training: one graph holds `chunk` iterations (gradient, then update); replayed
+  if (iters > 0) {
+    const uint32_t chunk = std::min<uint32_t>(iters, 50);
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return PLANB_ECUDA;
+    for (uint32_t it = 0; it < chunk; it++) {
+      mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(du.as<float>(), dt.as<float>(), n,
+                                                            dw.as<float>(), dpart.as<float>());
+      reduce_adam_kernel<<<1, 64, 0, st>>>(dpart.as<float>(), kGradBlocks, n, dw.as<float>(),
+                                           dm.as<float>(), dv.as<float>(), dstep.as<int>(), lr, 1,
+                                           nullptr, dloss.as<double>());
+      bump_step<<<1, 1, 0, st>>>(dstep.as<int>());
+    }
+    if (cudaStreamEndCapture(st, &graph) != cudaSuccess) return PLANB_ECUDA;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return PLANB_ECUDA;
+    }
+    bool gok = true;
+    for (uint32_t done = 0; done < iters && gok; done += chunk)
+      gok = cudaGraphLaunch(exec, st) == cudaSuccess;
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (!gok) return PLANB_ECUDA;
+    out.iters = ((iters + chunk - 1) / chunk) * chunk;
+  }
+  // final loss with the trained weights
+  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(du.as<float>(), dt.as<float>(), n,
+                                                        dw.as<float>(), dpart.as<float>());
+  reduce_adam_kernel<<<1, 64, 0, st>>>(dpart.as<float>(), kGradBlocks, n, nullptr, nullptr,
+                                       nullptr, nullptr, 0.0f, 0, nullptr, dloss.as<double>());
+  float w1[kMlpParams];
+  if (cudaMemcpyAsync(w1, dw.p, sizeof(w1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&out.loss, dloss.p, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PLANB_ECUDA;
+  std::copy(w1, w1 + kMlpHidden, P.mlp.w1);
+  std::copy(w1 + kMlpHidden, w1 + 2 * kMlpHidden, P.mlp.b1);
+  std::copy(w1 + 2 * kMlpHidden, w1 + 3 * kMlpHidden, P.mlp.w2);
+  P.mlp.b2 = w1[3 * kMlpHidden];
+  out.train_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                     .count();
+  // leaves: route every key with the device arithmetic, fit each leaf on the host (least squares
+  // of rank on the high half in double), then measure each leaf's error on the device
+  const uint32_t gb = std::min<uint32_t>((n + 255) / 256, 4096);
+  leaf_assign_kernel<<<gb, 256, 0, st>>>(dk.as<uint64_t>(), n, P, dleaf.as<uint32_t>());
+  std::vector<uint32_t> leaf(n);
+  if (cudaMemcpyAsync(leaf.data(), dleaf.p, n * 4ull, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PLANB_ECUDA;
+  std::vector<uint64_t> base(P.leaves, ~0ull);
+  std::vector<double> sx(P.leaves, 0), sy(P.leaves, 0), sxx(P.leaves, 0), sxy(P.leaves, 0);
+  std::vector<uint32_t> cnt(P.leaves, 0);
+  for (uint32_t i = 0; i < n; i++) base[leaf[i]] = std::min(base[leaf[i]], khi[i]);
+  for (uint32_t i = 0; i < n; i++) {
+    const uint32_t l = leaf[i];
+    const double x = static_cast<double>(khi[i] - base[l]);
+    const double y = static_cast<double>(i);
+    sx[l] += x; sy[l] += y; sxx[l] += x * x; sxy[l] += x * y; cnt[l]++;
+  }
+  for (uint32_t l = 0; l < P.leaves; l++) {
+    LeafModel& lm = out.leaves[l];
+    if (!cnt[l]) continue;
+    lm.base = base[l];
+    const double c = cnt[l];
+    const double var = sxx[l] - sx[l] * sx[l] / c;
+    const double slope = var > 0 ? (sxy[l] - sx[l] * sy[l] / c) / var : 0.0;
+    lm.s = static_cast<float>(std::max(slope, 0.0));
+    lm.a = static_cast<float>((sy[l] - slope * sx[l]) / c);
+    if (!(var > 0)) lm.a = static_cast<float>(sy[l] / c);
+  }
+  if (cudaMemcpyAsync(dleaves.p, out.leaves.data(), P.leaves * sizeof(LeafModel),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(derr.p, 0, P.leaves * 4ull, st) != cudaSuccess)
+    return PLANB_ECUDA;
+  leaf_error_kernel<<<gb, 256, 0, st>>>(dk.as<uint64_t>(), n, P, dleaves.as<LeafModel>(),
+                                        derr.as<uint32_t>());
+  std::vector<uint32_t> e(P.leaves);
+  if (cudaMemcpyAsync(e.data(), derr.p, P.leaves * 4ull, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return PLANB_ECUDA;
+  uint64_t covered = 0;
+  double esum = 0;
+  for (uint32_t l = 0; l < P.leaves; l++) {
+    if (!cnt[l]) continue;
+    const uint32_t bound = e[l] + 1;             // + 1: addresses between two keys
+    out.max_err = std::max(out.max_err, bound);
+    if (bound <= max_window) {
+      out.err[l] = static_cast<uint16_t>(bound);
+      covered += cnt[l];
+      esum += static_cast<double>(bound) * cnt[l];
+    }
+  }
+  out.covered = static_cast<double>(covered) / n;
+  out.mean_err = covered ? esum / covered : 0.0;
+  out.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                     .count();
+  return PLANB_OK;
+}
+
+}  // namespace planb

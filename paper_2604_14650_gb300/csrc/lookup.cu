@@ -34,6 +34,7 @@
 // coalesced.
 #include <cuda_runtime.h>
 
+#include "learned.cuh"
 #include "planb_internal.h"
 
 namespace planb {
@@ -60,6 +61,9 @@ struct KParams {
   uint32_t sidx_n;
   uint32_t sidx_node;
   uint32_t* status;
+  const LeafModel* leaves;    // learned: leaf models (copied to shared memory)
+  const uint16_t* leaf_err;   // learned: per-leaf window half-width or kLeafFallback
+  LearnedParams lp;           // learned: root weights and range reduction
 };
 
 // 128-bit unsigned k < x
@@ -201,28 +205,37 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
 // ------------------------------------------------------------------------------- hybrid
 // DB = levels left after the shared-memory index (D - S); 0 when the index holds every key.
 //
-// The index sits in shared memory as two arrays, high halves then low halves. The binary search
-// reads only the 8-byte high halves (half the shared-memory wavefronts of 16-byte entries); it
-// counts the entries whose high half is below the address's, and the entries whose high half
-// equals it — contiguous and sorted by low half right after that count — are then added one by one
-// while their low half is below the address's (a /65+ boundary shares its high half with the
-// address; rare, and a short loop when it happens).
+// Only the index's 8-byte high halves sit in shared memory (half the footprint and half the
+// shared-memory wavefronts of 16-byte entries). The binary search counts the entries whose high
+// half is below the address's; the entries whose high half equals it — contiguous and sorted by low
+// half right after that count — are then added one by one while their low half, read from the
+// global copy of the index, is below the address's (a /65+ boundary sharing the address's high
+// half; rare, and a short loop when it happens).
 //
 // In the L2 levels a group needs the address of the lane it serves: only the high half and the node
 // index are broadcast; the low half is broadcast only when some lane of the warp finds a key whose
 // high half equals the address's.
 constexpr int kRounds = 4;  // addresses per group in flight during the L2 levels
 
-template <int DB, bool PACKED>
+//
+// LEARNED: phase A first asks the learned position model (learned.cuh) for the address's interval
+// rank and its leaf's recorded error e; the index entries that can hold the answer are those of the
+// buckets of ranks [rank - e, rank + e], and a short search among them gives the count — accepted
+// only when the entries just outside the window bracket the address (so the count is exact whatever
+// the model said). Otherwise, and for leaves marked for the tree, the full binary search runs.
+template <int DB, bool PACKED, bool LEARNED>
 __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
   uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
-  uint64_t* Ul = Uh + N;
-  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-    const ulonglong2 e = __ldg(p.sidx + i);
-    Uh[i] = e.x;
-    Ul[i] = e.y;
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
+  LeafModel* Lm = reinterpret_cast<LeafModel*>(Uh + ((N + 1u) & ~1u));
+  uint16_t* Le = reinterpret_cast<uint16_t*>(Lm + (LEARNED ? p.lp.leaves : 0u));
+  if (LEARNED) {
+    for (uint32_t i = threadIdx.x; i < p.lp.leaves; i += blockDim.x) {
+      Lm[i] = p.leaves[i];
+      Le[i] = p.leaf_err[i];
+    }
   }
   __syncthreads();
 
@@ -241,7 +254,37 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
     const uint64_t my_lo = ok ? p.xlo[mine] : 0ull;
     // phase A: per-thread count over the level-S subtree maxima in shared memory
     uint32_t cnt = 0;
-    if (N) {
+    bool have = false;
+    if constexpr (LEARNED) {
+      auto below = [&](uint32_t q) {   // index entry q < address
+        const uint64_t h = Uh[q];
+        return h < my_hi || (h == my_hi && __ldg(&p.sidx[q].y) < my_lo);
+      };
+      const uint32_t leaf = predict_leaf(p.lp, my_hi);
+      const uint32_t e = Le[leaf];
+      if (e != kLeafFallback) {
+        const uint32_t r = predict_rank(p.lp, Lm[leaf], my_hi);
+        const uint32_t lo_r = r > e ? r - e : 0u;
+        const uint32_t hi_r = min(r + e, p.lp.n_keys - 1u);
+        const uint32_t qa = min(div_span(p.lp, lo_r), N);
+        const uint32_t qb = min(div_span(p.lp, hi_r), N);
+        bool ok = qa == 0u || below(qa - 1u);
+        ok = ok && (qb >= N || !below(qb));
+        uint32_t b = qa, len = qb - qa;   // count the entries of [qa, qb) below the address
+        while (len > 0u) {
+          const uint32_t half = len >> 1;
+          if (below(b + half)) {
+            b += half + 1u;
+            len -= half + 1u;
+          } else {
+            len = half;
+          }
+        }
+        cnt = b;
+        have = ok;
+      }
+    }
+    if (N && !have) {
       uint32_t b = 0, n = N;
       while (n > 1) {
         const uint32_t half = n >> 1;
@@ -249,7 +292,7 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
         n -= half;
       }
       cnt = b + (Uh[b] < my_hi ? 1u : 0u);
-      while (cnt < N && Uh[cnt] == my_hi && Ul[cnt] < my_lo) cnt++;
+      while (cnt < N && Uh[cnt] == my_hi && __ldg(&p.sidx[cnt].y) < my_lo) cnt++;
     }
     if constexpr (DB == 0) {
       uint32_t rank = cnt;
@@ -373,23 +416,25 @@ KernelFn kernel_for(const DevTable& t) {
       nullptr,             lookup_coop_f16<1>, lookup_coop_f16<2>, lookup_coop_f16<3>,
       lookup_coop_f16<4>,  lookup_coop_f16<5>, lookup_coop_f16<6>, lookup_coop_f16<7>,
       lookup_coop_f16<8>,  lookup_coop_f16<9>, lookup_coop_f16<10>};
-  static const KernelFn hyb[kMaxDepth + 1] = {
-      lookup_hybrid<0, false>, lookup_hybrid<1, false>, lookup_hybrid<2, false>,
-      lookup_hybrid<3, false>, lookup_hybrid<4, false>, lookup_hybrid<5, false>,
-      lookup_hybrid<6, false>, lookup_hybrid<7, false>, lookup_hybrid<8, false>,
-      lookup_hybrid<9, false>, lookup_hybrid<10, false>};
-  static const KernelFn hyb_packed[kMaxDepth + 1] = {
-      lookup_hybrid<0, true>, lookup_hybrid<1, true>, lookup_hybrid<2, true>,
-      lookup_hybrid<3, true>, lookup_hybrid<4, true>, lookup_hybrid<5, true>,
-      lookup_hybrid<6, true>, lookup_hybrid<7, true>, lookup_hybrid<8, true>,
-      lookup_hybrid<9, true>, lookup_hybrid<10, true>};
+#define PLANB_HYB(P, L)                                                                          \
+  {                                                                                               \
+    lookup_hybrid<0, P, L>, lookup_hybrid<1, P, L>, lookup_hybrid<2, P, L>,                       \
+        lookup_hybrid<3, P, L>, lookup_hybrid<4, P, L>, lookup_hybrid<5, P, L>,                   \
+        lookup_hybrid<6, P, L>, lookup_hybrid<7, P, L>, lookup_hybrid<8, P, L>,                   \
+        lookup_hybrid<9, P, L>, lookup_hybrid<10, P, L>                                           \
+  }
+  static const KernelFn hyb[2][2][kMaxDepth + 1] = {
+      {PLANB_HYB(false, false), PLANB_HYB(false, true)},
+      {PLANB_HYB(true, false), PLANB_HYB(true, true)}};
+#undef PLANB_HYB
   const uint32_t D = t.depth;
   if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
   if (t.format == PLANB_FMT_F16HI) return f16[D];
-  if (t.format == PLANB_FMT_F8V7)
-    return (t.kernel == kHybrid && t.smem_levels <= D) ? hyb_packed[D - t.smem_levels] : nullptr;
+  const bool packed = t.format == PLANB_FMT_F8V7;
+  if (t.kernel == kHybrid || t.kernel == kLearned)
+    return t.smem_levels <= D ? hyb[packed][t.kernel == kLearned][D - t.smem_levels] : nullptr;
+  if (packed) return nullptr;
   switch (t.kernel) {
-    case kHybrid: return t.smem_levels <= D ? hyb[D - t.smem_levels] : nullptr;
     case kFlat: return lookup_flat;
     default: return f8[D];
   }
@@ -408,12 +453,14 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
   KernelFn fn = kernel_for(t);
   if (!fn) return PLANB_EINVAL;
   const bool f8 = t.format != PLANB_FMT_F16HI;
-  const int max_threads = (t.kernel == kHybrid && f8) ? 512 : 256;
+  const bool hyb = (t.kernel == kHybrid || t.kernel == kLearned) && f8;
+  const int max_threads = hyb ? 512 : 256;
   if (threads <= 0) threads = max_threads;
   if (threads % 32 || threads > max_threads) return PLANB_EINVAL;
   cfg.threads = threads;
-  if (t.kernel == kHybrid && f8)
-    cfg.smem_bytes = static_cast<size_t>(t.sidx_n) * 16u;
+  if (hyb)
+    cfg.smem_bytes = static_cast<size_t>((t.sidx_n + 1) & ~1ull) * 8u +
+                     (t.kernel == kLearned ? static_cast<size_t>(t.lp.leaves) * 18u : 0u);
   else if (t.kernel == kFlat && f8)
     cfg.smem_bytes = 0;
   else
@@ -458,6 +505,9 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   p.sidx_n = static_cast<uint32_t>(t.sidx_n);
   p.sidx_node = static_cast<uint32_t>(t.sidx_node);
   p.status = d_status;
+  p.leaves = t.leaves;
+  p.leaf_err = t.leaf_err;
+  p.lp = t.lp;
   uint64_t blocks;
   if (t.kernel == kFlat) {
     blocks = (n + cfg.threads - 1) / cfg.threads;

@@ -10,6 +10,37 @@
 
 namespace planb {
 
+// ------------------------------------------------------------- learned position model (data)
+// (inference and training code: learned.cuh / learned.cu)
+constexpr int kMlpHidden = 16;
+constexpr int kMlpParams = 3 * kMlpHidden + 1;   // w1, b1, w2, b2
+constexpr uint16_t kLeafFallback = 0xFFFFu;       // error value that sends a leaf to the tree path
+
+struct MlpWeights {
+  float w1[kMlpHidden];
+  float b1[kMlpHidden];
+  float w2[kMlpHidden];
+  float b2;
+};
+
+struct LeafModel {
+  uint64_t base;  // high half of the leaf's first key
+  float a;        // predicted rank at base
+  float s;        // ranks per unit of the high half
+};
+
+// Everything a lookup needs of the model besides the leaves (passed by value to the kernel).
+struct LearnedParams {
+  MlpWeights mlp;
+  uint64_t kmin;      // high half of the smallest key
+  float inv_range;    // 1 / (kmax - kmin) of the high halves
+  uint32_t leaves;    // L
+  uint32_t span;      // keys per level-S subtree of the tree (the index's bucket width)
+  float inv_span;     // 1 / span
+  uint32_t n_keys;    // ranks are in [0, n_keys)
+  uint32_t pad;
+};
+
 typedef unsigned __int128 u128;
 
 inline u128 mk128(uint64_t hi, uint64_t lo) { return (static_cast<u128>(hi) << 64) | lo; }
@@ -92,7 +123,7 @@ void fill_sidx(const Intervals& iv, const Layout& L, uint32_t S, uint64_t* out /
 // ------------------------------------------------------------------------- device side
 
 // Everything a lookup kernel needs about one table (device pointers).
-enum Kernel : uint32_t { kCoop = 1, kHybrid = 2, kFlat = 3 };
+enum Kernel : uint32_t { kCoop = 1, kHybrid = 2, kFlat = 3, kLearned = 4 };
 
 struct DevTable {
   const void* nodes;        // F8X128: ulonglong2[total_nodes * 8]; F16HI: uint64_t[total * 16]
@@ -109,6 +140,9 @@ struct DevTable {
   uint32_t format;
   uint32_t smem_levels;     // levels staged in shared memory
   uint32_t smem_nodes;      // nodes staged (the first smem_nodes of the array)
+  const LeafModel* leaves;  // learned: leaf models (device)
+  const uint16_t* leaf_err; // learned: per-leaf window half-width (device)
+  LearnedParams lp;         // learned: root weights and constants
 };
 
 struct LaunchCfg {

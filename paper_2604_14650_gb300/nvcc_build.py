@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "_build", platform.machine())
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["builder.cpp", "lookup.cu", "capi.cu"]
+SOURCES = ["builder.cpp", "lookup.cu", "learned.cu", "capi.cu"]
 LIBS = {"libplanb.so": [], "libplanb_checked.so": ["-DPLANB_BOUNDS_CHECK"]}
 
 
@@ -45,7 +45,8 @@ def build(force: bool = False, verbose: bool = False) -> dict:
     """Compiles every library variant; returns {name: path}."""
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, "planb_internal.h"), os.path.join(INCLUDE, "planb.h")]
+    headers = [os.path.join(CSRC, "planb_internal.h"), os.path.join(CSRC, "learned.cuh"),
+               os.path.join(INCLUDE, "planb.h")]
     jobs, links = [], {}
     for lib, defines in LIBS.items():
         tag = "chk" if defines else "rel"

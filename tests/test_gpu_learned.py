@@ -1,0 +1,91 @@
+"""GPU tests of the learned position model: the library's forward and gradient kernels against the
+float64 CPU oracle (oracle/learned.py), and what the trained root gains over the untrained one."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import learned as OL
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2604_14650_gb300 as pb  # noqa: E402
+
+H = 16
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pb.build()
+
+
+def weights(rng):
+    return np.concatenate([rng.normal(size=H), rng.normal(size=H) * 0.5, rng.normal(size=H),
+                           [rng.normal()]]).astype(np.float32)
+
+
+@pytest.mark.parametrize("n", [1, 1000, 300_001])
+def test_forward_matches_oracle(n):
+    rng = np.random.default_rng(n)
+    w = weights(rng)
+    u = rng.random(n).astype(np.float32)
+    y = pb.mlp_forward(torch.from_numpy(u).cuda(), w)
+    torch.cuda.synchronize()
+    ref = OL.forward(w.astype(np.float64), u.astype(np.float64))
+    # 16 fused multiply-adds in FP32 on O(1) values: a few units in the last place of O(10)
+    assert np.max(np.abs(y.cpu().numpy() - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (777, 2), (200_000, 3), (1_000_003, 4)])
+def test_gradient_matches_oracle(n, seed):
+    """The training kernels' full-batch gradient equals the float64 chain rule: FP32 sums of n
+    terms carry a relative error of order 1e-6 of the summed magnitudes; the bound below is
+    1e-4 of the largest gradient component."""
+    rng = np.random.default_rng(seed)
+    w = weights(rng)
+    u = rng.random(n).astype(np.float32)
+    t = np.sort(rng.random(n)).astype(np.float32)
+    loss, g = pb.mlp_grad(torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda(), w)
+    ref_loss, ref = OL.grad(w.astype(np.float64), u.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - ref_loss) <= 1e-5 * max(ref_loss, 1e-12)
+    tol = 1e-4 * np.max(np.abs(ref)) + 1e-7
+    assert np.max(np.abs(g - ref)) <= tol, (np.max(np.abs(g - ref)), tol)
+
+
+def test_gradient_descent_direction():
+    """A small step against the library's gradient lowers the oracle's loss."""
+    rng = np.random.default_rng(5)
+    w = weights(rng)
+    u = rng.random(50_000).astype(np.float32)
+    t = np.sort(rng.random(50_000)).astype(np.float32)
+    _, g = pb.mlp_grad(torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda(), w)
+    l0 = OL.loss(w.astype(np.float64), u, t)
+    l1 = OL.loss((w - 1e-3 * g / np.linalg.norm(g)).astype(np.float64), u, t)
+    assert l1 < l0
+
+
+def test_trained_root_gains_over_untrained():
+    """Same table, same leaves: the trained root fits the key CDF better than the untrained one
+    (the identity, i.e. plain linear range reduction), so its leaves are better balanced and more
+    keys fall in leaves whose error window is within the limit; lookups stay exact either way."""
+    f = synth.gen_fib(200_000, seed=2604, nh_max=4095)
+    xh, xl = synth.gen_trace(f, 2_000_000, seed=9)
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl)
+    stats = {}
+    for iters in (0, 2000):
+        with pb.Fib(f.hi, f.lo, f.len, f.nh, kernel="learned", model_iters=iters) as fib:
+            st = fib.stats()
+            stats[iters] = st
+            out = fib.lookup(torch.from_numpy(xh.view(np.int64)).cuda(),
+                             torch.from_numpy(xl.view(np.int64)).cuda())
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy().view(np.uint16), want)
+    a, b = stats[0], stats[2000]
+    assert b["model_iters"] >= 2000 and a["model_iters"] == 0
+    assert b["model_loss"] < 0.1 * a["model_loss0"]
+    assert b["model_covered"] > a["model_covered"]
+    assert b["model_covered"] > 0.9
