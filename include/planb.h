@@ -47,7 +47,7 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
 /* F16HI: 16 key high halves per 128-byte node, 17-ary (Section 3.2: 128-byte lines give 16-key,
  * 17-ary nodes); a parallel array holds the low halves, read only when a high half ties. */
 #define PLANB_FMT_F16HI 1
-/* F8V7 (default): internal nodes as F8X128; each 128-byte leaf line holds 7 keys and, in its last
+/* F8V7: internal nodes as F8X128; each 128-byte leaf line holds 7 keys and, in its last
  * 16 bytes, the 7 next hops of those keys. The paper keeps values in a separate array (Section 3.2,
  * "Separation of Keys and Values") and fetches one after the descent; packing them into the leaf
  * line removes that dependent memory access. The last interval gets an explicit all-ones key, so the
@@ -78,7 +78,7 @@ typedef struct planb_fib planb_fib; /* opaque; owns all host and device memory o
 
 typedef struct {
     uint32_t struct_size;   /* sizeof(planb_opts); lets the library accept older callers        */
-    int32_t format;         /* PLANB_FMT_*; default PLANB_FMT_F8V7                              */
+    int32_t format;         /* PLANB_FMT_*; default PLANB_FMT_F8X128                            */
     int32_t merge_equal_nh; /* 1: merge neighbouring intervals with equal next hops (Section 3
                                intro allows compressing routes that share a next hop); results
                                are unchanged. Default 0.                                        */
@@ -212,14 +212,48 @@ void planb_destroy(planb_fib *fib);
 /* planb_strerror — a static string naming a PLANB_* code. */
 const char *planb_strerror(int code);
 
+/* ------------------------------------------------------------------------ multi-table lookups */
+
+typedef struct planb_multi planb_multi; /* several tables (VRFs) served by one captured graph */
+
+/*
+ * planb_multi_create — groups n_tables built tables (all on one device) for lookups whose
+ * addresses each carry a u8 table id. The paper serves one table; many tables per box are the
+ * same lookup applied per table. fibs: n_tables table handles (1..255), not owned: they must
+ * outlive the group; updates to them are picked up by later lookups. max_batch: most addresses per
+ * planb_multi_lookup call (< 2^32); the group owns max_batch x 20 bytes of device scratch.
+ * Tables built with PLANB_KERNEL_LEARNED cannot join a group.
+ * Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ECUDA.
+ */
+int planb_multi_create(planb_fib *const *fibs, uint32_t n_tables, size_t max_batch,
+                       planb_multi **out);
+
+/*
+ * planb_multi_lookup — next hop of n addresses, address i looked up in table d_table[i]
+ * (ids >= n_tables give 0). d_addr_hi, d_addr_lo: device u64 arrays; d_table: device u8 array;
+ * d_out: device u16 array; all of n entries. The batch is grouped by table (a counting sort on the
+ * device), each table's group is looked up by its own kernel (the tables' shared-memory index and
+ * nodes stay hot while it runs), and results are written back in the input order. The whole
+ * pipeline is captured once as a CUDA graph and replayed while the buffers, n and the tables stay
+ * the same; a table swapped by planb_update, or new buffers, cause one new capture. Enqueued on
+ * `stream`; calls on one group are serialised.
+ * Errors: PLANB_EINVAL (null pointer, misalignment, n > max_batch), PLANB_ECUDA.
+ */
+int planb_multi_lookup(planb_multi *m, const uint64_t *d_addr_hi, const uint64_t *d_addr_lo,
+                       const uint8_t *d_table, size_t n, uint16_t *d_out, planb_stream_t stream);
+
+/* planb_multi_destroy — waits for the device and frees the group (not its tables). */
+void planb_multi_destroy(planb_multi *m);
+
 /* ------------------------------------------------------ learned-model kernels (for checking) */
 
 /*
  * planb_mlp_grad — the training kernels' full-batch gradient: for the root MLP
- * y(u) = b2 + sum_h w2[h] max(w1[h] u + b1[h], 0) (16 hidden units) and the loss
- * L = (1/n) sum_i (y(u_i) - t_i)^2, writes dL/dtheta to grad[49] and L to *loss.
- *   d_u, d_t: device float arrays of n entries; w, grad: host float[49] in the order w1[16],
- *   b1[16], w2[16], b2. Runs on `stream` and waits for it. Uses the current device.
+ * y(u) = b2 + sum_h w2[h] min(max(w1[h] u + b1[h], 0), cap[h]) (16 saturating ReLU units) and the
+ * loss L = (1/n) sum_i (y(u_i) - t_i)^2, writes dL/dtheta to grad[49] and L to *loss.
+ *   d_u, d_t: device float arrays of n entries; w: host float[65] in the order w1[16], b1[16],
+ *   w2[16], b2, cap[16]; grad: host float[49] (the caps are fixed, not trained).
+ *   Runs on `stream` and waits for it. Uses the current device.
  * Errors: PLANB_EINVAL (null pointer, n >= 2^32), PLANB_ENOMEM, PLANB_ECUDA.
  */
 int planb_mlp_grad(const float *d_u, const float *d_t, size_t n, const float *w, float *grad,
@@ -227,7 +261,7 @@ int planb_mlp_grad(const float *d_u, const float *d_t, size_t n, const float *w,
 
 /*
  * planb_mlp_forward — y(u) for every entry of the device array d_u (n floats) into d_y (device);
- * w as in planb_mlp_grad. Asynchronous on `stream`.
+ * w (65 floats) as in planb_mlp_grad. Asynchronous on `stream`.
  * Errors: PLANB_EINVAL, PLANB_ECUDA.
  */
 int planb_mlp_forward(const float *d_u, size_t n, const float *w, float *d_y,

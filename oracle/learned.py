@@ -1,17 +1,18 @@
 """CPU oracle of the learned position model's arithmetic — TEST INFRASTRUCTURE.
 
 The model is the root of a two-layer recursive model index: a 1 -> H -> 1 multilayer perceptron with
-ReLU hidden units,
+saturating ReLU hidden units (a unit's output is capped at cap[h]; cap = inf gives plain ReLUs),
 
-    y(u) = b2 + sum_h w2[h] * max(w1[h] * u + b1[h], 0),
+    y(u) = b2 + sum_h w2[h] * min(max(w1[h] * u + b1[h], 0), cap[h]),
 
 fitted to the empirical CDF of the keys by mean squared error,
 
     L = (1/n) * sum_i (y(u_i) - t_i)^2.
 
 This module writes the forward pass, the loss and its gradient out in float64 from these definitions
-(plain numpy, no fusion), for checking the CUDA training kernels. Parameters are packed as one
-vector ``theta = [w1 (H), b1 (H), w2 (H), b2]`` (3H + 1 values).
+(plain numpy, no fusion), for checking the CUDA training kernels. Trained parameters are packed as
+one vector ``theta = [w1 (H), b1 (H), w2 (H), b2]`` (3H + 1 values); the caps are fixed and passed
+separately.
 
 Pins (tests): central finite differences of the loss; zero gradient at the least-squares optimum that
 ``numpy.linalg.lstsq`` finds when every hidden unit is active (the model is then linear in w2, b2).
@@ -27,35 +28,40 @@ def unpack(theta, H: int = 16):
     return theta[:H], theta[H:2 * H], theta[2 * H:3 * H], theta[3 * H]
 
 
-def forward(theta, u, H: int = 16):
+def _caps(cap, H):
+    return np.full(H, np.inf) if cap is None else np.asarray(cap, dtype=np.float64)
+
+
+def forward(theta, u, H: int = 16, cap=None):
     """y(u) for every input (float64)."""
     w1, b1, w2, b2 = unpack(theta, H)
     u = np.asarray(u, dtype=np.float64)
     z = np.outer(u, w1) + b1            # (n, H) pre-activations
-    a = np.maximum(z, 0.0)              # ReLU
+    a = np.minimum(np.maximum(z, 0.0), _caps(cap, H))   # saturating ReLU
     return a @ w2 + b2
 
 
-def loss(theta, u, t, H: int = 16) -> float:
-    y = forward(theta, u, H)
+def loss(theta, u, t, H: int = 16, cap=None) -> float:
+    y = forward(theta, u, H, cap)
     r = y - np.asarray(t, dtype=np.float64)
     return float(np.mean(r * r))
 
 
-def grad(theta, u, t, H: int = 16):
+def grad(theta, u, t, H: int = 16, cap=None):
     """(loss, dL/dtheta) in float64, by the chain rule through the two layers."""
     w1, b1, w2, b2 = unpack(theta, H)
+    c = _caps(cap, H)
     u = np.asarray(u, dtype=np.float64)
     t = np.asarray(t, dtype=np.float64)
     n = u.size
     z = np.outer(u, w1) + b1
-    a = np.maximum(z, 0.0)
+    a = np.minimum(np.maximum(z, 0.0), c)
     y = a @ w2 + b2
     r = y - t
     dy = 2.0 * r / n                    # dL/dy_i
     g_w2 = a.T @ dy
     g_b2 = dy.sum()
-    dz = np.outer(dy, w2) * (z > 0.0)   # dL/dz_ih (ReLU derivative 0 at z <= 0)
+    dz = np.outer(dy, w2) * ((z > 0.0) & (z < c))   # unit slope 1 inside (0, cap), else 0
     g_w1 = dz.T @ u
     g_b1 = dz.sum(axis=0)
     return float(np.mean(r * r)), np.concatenate([g_w1, g_b1, g_w2, [g_b2]])

@@ -87,6 +87,9 @@ _SIGS = {
     "planb_debug_inject": (C.c_int, [C.c_int]),
     "planb_mlp_grad": (C.c_int, [_vp, _vp, _sz, _vp, _vp, C.POINTER(C.c_double), _vp]),
     "planb_mlp_forward": (C.c_int, [_vp, _sz, _vp, _vp, _vp]),
+    "planb_multi_create": (C.c_int, [_vp, C.c_uint32, _sz, C.POINTER(_vp)]),
+    "planb_multi_lookup": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "planb_multi_destroy": (None, [_vp]),
 }
 
 
@@ -183,8 +186,10 @@ def debug_inject(point: int):
 
 def mlp_grad(u, t, w, stream=None):
     """Root-MLP loss and gradient by the library's training kernels (CUDA float32 tensors u, t;
-    w: 49 floats w1, b1, w2, b2). Returns (loss, grad as float32 numpy array)."""
+    w: 65 floats w1, b1, w2, b2, cap). Returns (loss, grad of the 49 trained parameters)."""
     wv = np.ascontiguousarray(w, dtype=np.float32)
+    if wv.size != 65:
+        raise ValueError("w holds 65 floats: w1, b1, w2, b2, cap")
     g = np.zeros(49, dtype=np.float32)
     loss = C.c_double(0.0)
     _check(load().planb_mlp_grad(C.c_void_p(u.data_ptr()), C.c_void_p(t.data_ptr()), u.numel(),
@@ -194,9 +199,11 @@ def mlp_grad(u, t, w, stream=None):
 
 
 def mlp_forward(u, w, out=None, stream=None):
-    """y = root(u) by the library's inference kernel (CUDA float32 tensors)."""
+    """y = root(u) by the library's inference kernel (CUDA float32 tensors; w: 65 floats)."""
     import torch
     wv = np.ascontiguousarray(w, dtype=np.float32)
+    if wv.size != 65:
+        raise ValueError("w holds 65 floats: w1, b1, w2, b2, cap")
     if out is None:
         out = torch.empty_like(u)
     _check(load().planb_mlp_forward(C.c_void_p(u.data_ptr()), u.numel(), _ptr(wv),
@@ -208,7 +215,7 @@ def mlp_forward(u, w, out=None, stream=None):
 class Fib:
     """One lookup table on a GPU (a planb_fib)."""
 
-    def __init__(self, hi, lo, ln, nh, *, format: str = "f8v7", merge: bool = False,
+    def __init__(self, hi, lo, ln, nh, *, format: str = "f8x128", merge: bool = False,
                  smem_levels: int = -1, device: int | None = None, block_threads: int = 0,
                  ctas_per_sm: int = 0, kernel: str = "auto", model_leaves: int = 0,
                  model_iters: int = -1, variant: str = "libplanb.so"):
@@ -325,3 +332,53 @@ def _host_ptrs(hi, lo):
     if hi.size != lo.size:
         raise ValueError("hi and lo differ in length")
     return hi.ctypes.data, lo.ctypes.data, hi.size, (hi, lo)
+
+
+class MultiFib:
+    """Several tables (VRFs) looked up by one captured graph; each address carries a table id."""
+
+    def __init__(self, fibs, max_batch: int):
+        self._lib = fibs[0]._lib
+        self.fibs = list(fibs)                 # keep the tables alive while the group exists
+        arr = (C.c_void_p * len(fibs))(*[f._h.value for f in fibs])
+        h = C.c_void_p()
+        _check(self._lib.planb_multi_create(arr, len(fibs), max_batch, C.byref(h)),
+               "planb_multi_create")
+        self._h = h
+
+    def lookup(self, addr_hi, addr_lo, table, out=None, stream=None):
+        """CUDA tensors: addresses int64 (u64 bits), table ids uint8; returns int16 (u16 bits)."""
+        import torch
+        n = addr_hi.numel()
+        if addr_lo.numel() != n or table.numel() != n or table.element_size() != 1:
+            raise ValueError("addresses and table ids differ in length, or ids are not bytes")
+        if out is None:
+            out = torch.empty(n, dtype=torch.int16, device=addr_hi.device)
+        _check(self._lib.planb_multi_lookup(self._h, C.c_void_p(addr_hi.data_ptr()),
+                                            C.c_void_p(addr_lo.data_ptr()),
+                                            C.c_void_p(table.data_ptr()), n,
+                                            C.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "planb_multi_lookup")
+        return out
+
+    def lookup_ptr(self, hi_ptr: int, lo_ptr: int, tid_ptr: int, n: int, out_ptr: int, stream=None):
+        _check(self._lib.planb_multi_lookup(self._h, C.c_void_p(hi_ptr), C.c_void_p(lo_ptr),
+                                            C.c_void_p(tid_ptr), n, C.c_void_p(out_ptr),
+                                            _stream_handle(stream)), "planb_multi_lookup")
+
+    def close(self):
+        if self._h:
+            self._lib.planb_multi_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

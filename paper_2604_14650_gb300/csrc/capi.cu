@@ -321,7 +321,7 @@ void planb_opts_default(planb_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->struct_size = sizeof(planb_opts);
-  o->format = PLANB_FMT_F8V7;
+  o->format = PLANB_FMT_F8X128;
   o->merge_equal_nh = 0;
   o->smem_levels = -1;
   o->device = -1;
@@ -702,6 +702,153 @@ int planb_debug_inject(int point) {
   if (point < 0 || point > 2) return PLANB_EINVAL;
   g_inject.store(point);
   return PLANB_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------ multi-table lookups
+
+struct planb_multi {
+  int device = 0;
+  std::vector<planb_fib*> fibs;  // not owned
+  uint32_t T = 0;
+  size_t cap = 0;
+  uint32_t G = 0;                // bucketing chunks
+  void* mem = nullptr;
+  uint64_t *bhi = nullptr, *blo = nullptr, *range = nullptr;
+  uint32_t *perm = nullptr, *counts = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void *g_hi = nullptr, *g_lo = nullptr, *g_tid = nullptr, *g_out = nullptr;
+  size_t g_n = 0;
+  std::vector<std::shared_ptr<Table>> snap;  // the tables the captured graph reads
+  std::mutex mu;
+};
+
+extern "C" {
+
+int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_batch,
+                       planb_multi** out) {
+  if (!out) return PLANB_EINVAL;
+  *out = nullptr;
+  if (!fibs || n_tables == 0 || n_tables > 255 || max_batch == 0 ||
+      max_batch >= (size_t(1) << 32))
+    return PLANB_EINVAL;
+  for (uint32_t t = 0; t < n_tables; t++)
+    if (!fibs[t] || fibs[t]->device != fibs[0]->device ||
+        fibs[t]->opts.kernel == PLANB_KERNEL_LEARNED)
+      return PLANB_EINVAL;
+  try {
+    std::unique_ptr<planb_multi> m(new planb_multi());
+    m->device = fibs[0]->device;
+    m->fibs.assign(fibs, fibs + n_tables);
+    m->T = n_tables;
+    m->cap = max_batch;
+    DeviceGuard g(m->device);
+    if (!g.ok) return PLANB_ECUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess)
+      return PLANB_ECUDA;
+    m->G = static_cast<uint32_t>(sms) * 8u;
+    const size_t cap = max_batch;
+    const size_t bytes = cap * 8 * 2 + ((cap * 4 + 255) / 256) * 256 +
+                         ((static_cast<size_t>(m->T + 1) * m->G * 4 + 255) / 256) * 256 +
+                         (m->T + 2) * 8;
+    if (cudaMalloc(&m->mem, bytes) != cudaSuccess) {
+      m->mem = nullptr;
+      cudaGetLastError();
+      return PLANB_ENOMEM;
+    }
+    char* b = static_cast<char*>(m->mem);
+    m->bhi = reinterpret_cast<uint64_t*>(b);
+    m->blo = m->bhi + cap;
+    m->perm = reinterpret_cast<uint32_t*>(m->blo + cap);
+    m->counts = reinterpret_cast<uint32_t*>(b + cap * 16 + ((cap * 4 + 255) / 256) * 256);
+    m->range = reinterpret_cast<uint64_t*>(
+        reinterpret_cast<char*>(m->counts) +
+        ((static_cast<size_t>(m->T + 1) * m->G * 4 + 255) / 256) * 256);
+    if (cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaFree(m->mem);
+      return PLANB_ECUDA;
+    }
+    *out = m.release();
+    return PLANB_OK;
+  } catch (const std::bad_alloc&) {
+    return PLANB_ENOMEM;
+  }
+}
+
+int planb_multi_lookup(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t* d_addr_lo,
+                       const uint8_t* d_table, size_t n, uint16_t* d_out, planb_stream_t stream) {
+  if (!m) return PLANB_EINVAL;
+  if (n == 0) return PLANB_OK;
+  if (!d_addr_hi || !d_addr_lo || !d_table || !d_out || n > m->cap) return PLANB_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_addr_hi) | reinterpret_cast<uintptr_t>(d_addr_lo)) & 7u ||
+      reinterpret_cast<uintptr_t>(d_out) & 1u)
+    return PLANB_EINVAL;
+  std::lock_guard<std::mutex> lk(m->mu);
+  DeviceGuard g(m->device);
+  if (!g.ok) return PLANB_ECUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::vector<std::shared_ptr<Table>> cur(m->T);
+  for (uint32_t t = 0; t < m->T; t++) {
+    planb_fib* f = m->fibs[t];
+    std::lock_guard<std::mutex> lk2(f->cur_mu);
+    cur[t] = f->cur;
+    note_stream(f, st);
+    note_stream(f, m->cap_stream);
+  }
+  bool same = m->exec && m->g_hi == d_addr_hi && m->g_lo == d_addr_lo && m->g_tid == d_table &&
+              m->g_out == d_out && m->g_n == n;
+  for (uint32_t t = 0; same && t < m->T; t++) same = m->snap[t] == cur[t];
+  if (!same) {
+    // a table was swapped by an update, or the buffers changed: capture the pipeline again
+    if (m->exec) {
+      if (cudaStreamSynchronize(st) != cudaSuccess) return PLANB_ECUDA;
+      cudaGraphExecDestroy(m->exec);
+      m->exec = nullptr;
+    }
+    if (cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return PLANB_ECUDA;
+    int rc = planb::launch_bucketing(d_addr_hi, d_addr_lo, d_table, n, m->T, m->G, m->counts,
+                                     m->range, m->bhi, m->blo, m->perm, m->cap_stream);
+    for (uint32_t t = 0; rc == PLANB_OK && t < m->T; t++)
+      rc = planb::launch_lookup(cur[t]->dt, cur[t]->cfg, m->bhi, m->blo, n, d_out,
+                                m->fibs[t]->d_status, m->cap_stream, m->range + t, m->perm);
+    if (rc == PLANB_OK) rc = planb::launch_invalid_fill(m->range, m->T, m->perm, d_out, m->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(m->cap_stream, &graph);
+    if (rc != PLANB_OK || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != PLANB_OK ? rc : PLANB_ECUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&m->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      m->exec = nullptr;
+      return PLANB_ECUDA;
+    }
+    m->g_hi = d_addr_hi;
+    m->g_lo = d_addr_lo;
+    m->g_tid = d_table;
+    m->g_out = d_out;
+    m->g_n = n;
+    m->snap = cur;
+  }
+  return cudaGraphLaunch(m->exec, st) == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+void planb_multi_destroy(planb_multi* m) {
+  if (!m) return;
+  {
+    DeviceGuard g(m->device);
+    cudaDeviceSynchronize();
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    if (m->mem) cudaFree(m->mem);
+  }
+  delete m;
 }
 
 }  // extern "C"

@@ -8,6 +8,11 @@
 // of 50 partials (49 gradients + the loss) per block; the update kernel adds the rows in block
 // order in double precision and applies Adam (Kingma and Ba, 2015). The result is deterministic for
 // a given grid. The iterations are captured once in a CUDA graph and replayed.
+//
+// Training starts from the piecewise-linear interpolation of the CDF through the inputs' 16
+// quantiles (the hidden units' knots, kept fixed) and fits the output layer — a convex least-squares
+// problem for fixed knots — by Adam on the spline's values at the knots (knot_adam_kernel). Without
+// training the root is the identity (plain linear range reduction).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,13 +32,14 @@ constexpr int kGradThreads = 256;
 constexpr int kGradBlocks = 304;         // fixed grid: the partial sums' order never changes
 
 __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(const float* __restrict__ u,
+                                                                const float* __restrict__ ulo,
                                                                 const float* __restrict__ t,
                                                                 uint32_t n,
                                                                 const float* __restrict__ w,
                                                                 float* __restrict__ partials) {
-  __shared__ float sw[kMlpParams];
+  __shared__ float sw[kMlpWeights];
   __shared__ float red[kGradThreads / 32][kRow];
-  if (threadIdx.x < kMlpParams) sw[threadIdx.x] = w[threadIdx.x];
+  if (threadIdx.x < kMlpWeights) sw[threadIdx.x] = w[threadIdx.x];
   __syncthreads();
   float g[kRow];
 #pragma unroll
@@ -41,12 +47,13 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(const float* __r
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const float ui = u[i];
+    const float li = ulo ? ulo[i] : 0.0f;
     float z[kMlpHidden];
     float y = sw[3 * kMlpHidden];
 #pragma unroll
     for (int h = 0; h < kMlpHidden; h++) {
-      z[h] = fmaf(sw[h], ui, sw[kMlpHidden + h]);
-      y = fmaf(sw[2 * kMlpHidden + h], fmaxf(z[h], 0.0f), y);
+      z[h] = fmaf(sw[h], li, fmaf(sw[h], ui, sw[kMlpHidden + h]));
+      y = fmaf(sw[2 * kMlpHidden + h], fminf(fmaxf(z[h], 0.0f), sw[kMlpParams + h]), y);
     }
     const float r = y - t[i];
     const float dy = 2.0f * r;              // the 1/n of the mean is applied after the reduction
@@ -54,10 +61,11 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(const float* __r
     g[kMlpParams] = fmaf(r, r, g[kMlpParams]);
 #pragma unroll
     for (int h = 0; h < kMlpHidden; h++) {
-      const bool on = z[h] > 0.0f;
-      g[2 * kMlpHidden + h] = fmaf(dy, on ? z[h] : 0.0f, g[2 * kMlpHidden + h]);
+      const float cap = sw[kMlpParams + h];
+      const bool on = z[h] > 0.0f && z[h] < cap;          // the unit's slope is 1 inside (0, cap)
+      g[2 * kMlpHidden + h] = fmaf(dy, fminf(fmaxf(z[h], 0.0f), cap), g[2 * kMlpHidden + h]);
       const float dz = on ? dy * sw[2 * kMlpHidden + h] : 0.0f;
-      g[h] = fmaf(dz, ui, g[h]);
+      g[h] = fmaf(dz, ui + li, g[h]);
       g[kMlpHidden + h] += dz;
     }
   }
@@ -77,13 +85,10 @@ __global__ void __launch_bounds__(kGradThreads) mlp_grad_kernel(const float* __r
   }
 }
 
-// Sums the partial rows (block order, double) into grad[49] and loss; with adam != 0 also applies
-// one Adam step to w (moments m, v; step counter in *step, incremented here).
-__global__ void reduce_adam_kernel(const float* __restrict__ partials, uint32_t nblocks, uint32_t n,
-                                   float* __restrict__ w, float* __restrict__ m,
-                                   float* __restrict__ v, int* __restrict__ step, float lr,
-                                   int adam, float* __restrict__ grad_out,
-                                   double* __restrict__ loss_out) {
+// Sums the partial rows (block order, double) into grad[49] and loss (no update). Used for the
+// loss before and after training and by planb_mlp_grad.
+__global__ void reduce_kernel(const float* __restrict__ partials, uint32_t nblocks, uint32_t n,
+                              float* __restrict__ grad_out, double* __restrict__ loss_out) {
   const int k = threadIdx.x;
   if (k >= kRow) return;
   double s = 0.0;
@@ -91,20 +96,54 @@ __global__ void reduce_adam_kernel(const float* __restrict__ partials, uint32_t 
   const double mean = n ? s / static_cast<double>(n) : 0.0;
   if (k == kMlpParams) {
     if (loss_out) *loss_out = mean;
-    return;
+  } else if (grad_out) {
+    grad_out[k] = static_cast<float>(mean);
   }
-  if (grad_out) grad_out[k] = static_cast<float>(mean);
-  if (!adam) return;
-  const int tstep = *step + 1;
-  const float gk = static_cast<float>(mean);
-  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  const float mk = b1 * m[k] + (1.0f - b1) * gk;
-  const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
-  m[k] = mk;
-  v[k] = vk;
-  const float mh = mk / (1.0f - powf(b1, static_cast<float>(tstep)));
-  const float vh = vk / (1.0f - powf(b2, static_cast<float>(tstep)));
-  w[k] -= lr * mh / (sqrtf(vh) + eps);
+}
+
+// One training step on the piecewise-linear root in knot-value form. With unit input weights,
+// fixed knots c_0 < .. < c_16 (c_h = -b1[h], c_16 the largest input) and caps c_{h+1} - c_h, the
+// network is the linear spline through (c_h, v_h): b2 = v_0 and w2[h] = s_h = (v_{h+1} - v_h) /
+// (c_{h+1} - c_h). Adam (Kingma and Ba, 2015) runs on v, which is well conditioned (CDF values in
+// [0, 1]); dL/dv comes from the network's gradient by the chain rule through those relations:
+//   dL/dv_j = dL/dw2[j-1] / (c_j - c_{j-1}) - dL/dw2[j] / (c_{j+1} - c_j) (+ dL/db2 for j = 0).
+// The new v is written back as (w2, b2). State: v[17], m[17], q[17] (moments), knots c[17].
+__global__ void knot_adam_kernel(const float* __restrict__ partials, uint32_t nblocks, uint32_t n,
+                                 float* __restrict__ w, float* __restrict__ v,
+                                 float* __restrict__ m, float* __restrict__ q,
+                                 const float* __restrict__ c, int* __restrict__ step, float lr,
+                                 double* __restrict__ loss_out) {
+  __shared__ float g[kRow];
+  __shared__ float vs[kMlpHidden + 1];
+  const int k = threadIdx.x;
+  if (k < kRow) {
+    double s = 0.0;
+    for (uint32_t b = 0; b < nblocks; b++) s += static_cast<double>(partials[b * kRow + k]);
+    const double mean = n ? s / static_cast<double>(n) : 0.0;
+    g[k] = static_cast<float>(mean);
+    if (k == kMlpParams && loss_out) *loss_out = mean;
+  }
+  __syncthreads();
+  if (k <= kMlpHidden) {
+    float gv = 0.0f;
+    if (k >= 1) gv += g[2 * kMlpHidden + k - 1] / (c[k] - c[k - 1]);
+    if (k < kMlpHidden) gv -= g[2 * kMlpHidden + k] / (c[k + 1] - c[k]);
+    if (k == 0) gv += g[3 * kMlpHidden];
+    const int tstep = *step + 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float mk = b1 * m[k] + (1.0f - b1) * gv;
+    const float qk = b2 * q[k] + (1.0f - b2) * gv * gv;
+    m[k] = mk;
+    q[k] = qk;
+    const float mh = mk / (1.0f - powf(b1, static_cast<float>(tstep)));
+    const float qh = qk / (1.0f - powf(b2, static_cast<float>(tstep)));
+    const float nv = v[k] - lr * mh / (sqrtf(qh) + eps);
+    v[k] = nv;
+    vs[k] = nv;
+  }
+  __syncthreads();
+  if (k < kMlpHidden) w[2 * kMlpHidden + k] = (vs[k + 1] - vs[k]) / (c[k + 1] - c[k]);
+  if (k == 0) w[3 * kMlpHidden] = vs[0];
 }
 
 __global__ void bump_step(int* step) { *step += 1; }
@@ -113,7 +152,7 @@ __global__ void mlp_forward_kernel(const float* __restrict__ u, uint32_t n, MlpW
                                    float* __restrict__ y) {
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    y[i] = mlp_eval(w, u[i]);
+    y[i] = mlp_eval(w, u[i], 0.0f);
 }
 
 __global__ void leaf_assign_kernel(const uint64_t* __restrict__ khi, uint32_t n, LearnedParams P,
@@ -136,12 +175,13 @@ __global__ void leaf_error_kernel(const uint64_t* __restrict__ khi, uint32_t n, 
 }
 
 void init_weights(MlpWeights& w) {
-  // knots evenly spaced over [0, 1); output = the first unit = u (the untrained root is the
-  // identity, i.e. plain linear range reduction)
+  // knots evenly spaced over [0, 1); output = the first unit = u (its cap is above any input): the
+  // identity, i.e. plain linear range reduction (the root used when no training is asked for)
   for (int h = 0; h < kMlpHidden; h++) {
     w.w1[h] = 1.0f;
     w.b1[h] = -static_cast<float>(h) / kMlpHidden;
     w.w2[h] = h == 0 ? 1.0f : 0.0f;
+    w.cap[h] = h == 0 ? 4.0f : 1.0f / kMlpHidden;
   }
   w.b2 = 0.0f;
 }
@@ -162,19 +202,19 @@ int mlp_grad_host(const float* d_u, const float* d_t, size_t n, const float* w_h
                   float* grad_host, double* loss_host, cudaStream_t st) {
   if (n >= (size_t(1) << 32)) return PLANB_EINVAL;
   DevBuf part, wb, gb, lb;
-  if (!part.alloc(kGradBlocks * kRow * sizeof(float)) || !wb.alloc(kMlpParams * sizeof(float)) ||
+  if (!part.alloc(kGradBlocks * kRow * sizeof(float)) || !wb.alloc(kMlpWeights * sizeof(float)) ||
       !gb.alloc(kMlpParams * sizeof(float)) || !lb.alloc(sizeof(double))) {
     cudaGetLastError();
     return PLANB_ENOMEM;
   }
-  if (cudaMemcpyAsync(wb.p, w_host, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, st) !=
+  if (cudaMemcpyAsync(wb.p, w_host, kMlpWeights * sizeof(float), cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return PLANB_ECUDA;
-  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(d_u, d_t, static_cast<uint32_t>(n),
-                                                        wb.as<float>(), part.as<float>());
-  reduce_adam_kernel<<<1, 64, 0, st>>>(part.as<float>(), kGradBlocks, static_cast<uint32_t>(n),
-                                       nullptr, nullptr, nullptr, nullptr, 0.0f, 0, gb.as<float>(),
-                                       lb.as<double>());
+  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(d_u, nullptr, d_t,
+                                                        static_cast<uint32_t>(n), wb.as<float>(),
+                                                        part.as<float>());
+  reduce_kernel<<<1, 64, 0, st>>>(part.as<float>(), kGradBlocks, static_cast<uint32_t>(n),
+                                  gb.as<float>(), lb.as<double>());
   if (cudaGetLastError() != cudaSuccess) return PLANB_ECUDA;
   if (cudaMemcpyAsync(grad_host, gb.p, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, st) !=
           cudaSuccess ||
@@ -191,6 +231,7 @@ int mlp_forward_host(const float* d_u, size_t n, const float* w_host, float* d_y
   std::copy(w_host + kMlpHidden, w_host + 2 * kMlpHidden, w.b1);
   std::copy(w_host + 2 * kMlpHidden, w_host + 3 * kMlpHidden, w.w2);
   w.b2 = w_host[3 * kMlpHidden];
+  std::copy(w_host + kMlpParams, w_host + kMlpWeights, w.cap);
   const uint32_t blocks = static_cast<uint32_t>(std::min<size_t>((n + 255) / 256, 4096));
   mlp_forward_kernel<<<blocks, 256, 0, st>>>(d_u, static_cast<uint32_t>(n), w, d_y);
   return cudaGetLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
@@ -218,9 +259,9 @@ int build_learned(const Intervals& iv, uint32_t span, uint32_t leaves, uint32_t 
   P.kmin = khi[0];
   const uint64_t range = khi[n - 1] - khi[0];
   P.inv_range = range ? 1.0f / static_cast<float>(range) : 0.0f;
-  std::vector<float> hu(n), ht(n);
+  std::vector<float> hu(n), hl(n), ht(n);
   for (uint32_t i = 0; i < n; i++) {
-    hu[i] = std::min(static_cast<float>(khi[i] - P.kmin) * P.inv_range, 1.0f);
+    split_input(khi[i] - P.kmin, P.inv_range, &hu[i], &hl[i]);
     ht[i] = (static_cast<float>(i) + 0.5f) / static_cast<float>(n);
   }
   cudaStream_t st;
@@ -229,33 +270,62 @@ int build_learned(const Intervals& iv, uint32_t span, uint32_t leaves, uint32_t 
     cudaStream_t s;
     ~StreamGuard() { cudaStreamDestroy(s); }
   } sg{st};
-  DevBuf dk, du, dt, dpart, dw, dm, dv, dstep, dloss, dleaf, dleaves, derr;
-  if (!dk.alloc(n * 8ull) || !du.alloc(n * 4ull) || !dt.alloc(n * 4ull) ||
-      !dpart.alloc(kGradBlocks * kRow * 4ull) || !dw.alloc(kMlpParams * 4) ||
-      !dm.alloc(kMlpParams * 4) || !dv.alloc(kMlpParams * 4) || !dstep.alloc(sizeof(int)) ||
+  // knot-value state for training: knots c_0..c_16 at the inputs' quantiles, values v_h = the CDF
+  float c[kMlpHidden + 1], v0[kMlpHidden + 1];
+  if (iters > 0) {
+    for (int h = 0; h <= kMlpHidden; h++) {
+      const size_t i = std::min<size_t>(n - 1, (static_cast<size_t>(h) * n) / kMlpHidden);
+      c[h] = hu[i] + hl[i];
+      v0[h] = (static_cast<float>(i) + 0.5f) / static_cast<float>(n);
+    }
+    c[kMlpHidden] = hu[n - 1] + hl[n - 1];
+    v0[kMlpHidden] = 1.0f;
+    for (int h = 1; h <= kMlpHidden; h++)     // strictly increasing knots (one float step apart)
+      if (!(c[h] > c[h - 1])) c[h] = nextafterf(c[h - 1], 2.0f);
+    for (int h = 0; h < kMlpHidden; h++) {
+      P.mlp.w1[h] = 1.0f;
+      P.mlp.b1[h] = -c[h];
+      P.mlp.w2[h] = (v0[h + 1] - v0[h]) / (c[h + 1] - c[h]);
+      // the last unit keeps rising past c_16 (addresses above the largest key)
+      P.mlp.cap[h] = h + 1 < kMlpHidden ? c[h + 1] - c[h] : 4.0f;
+    }
+    P.mlp.b2 = v0[0];
+  }
+  DevBuf dk, du, dl, dt, dpart, dw, dm, dq, dv, dc, dstep, dloss, dleaf, dleaves, derr;
+  if (!dk.alloc(n * 8ull) || !du.alloc(n * 4ull) || !dl.alloc(n * 4ull) ||
+      !dt.alloc(n * 4ull) || !dpart.alloc(kGradBlocks * kRow * 4ull) ||
+      !dw.alloc(kMlpWeights * 4) || !dm.alloc(kRow * 4) || !dq.alloc(kRow * 4) ||
+      !dv.alloc(kRow * 4) || !dc.alloc(kRow * 4) || !dstep.alloc(sizeof(int)) ||
       !dloss.alloc(sizeof(double)) || !dleaf.alloc(n * 4ull) ||
       !dleaves.alloc(P.leaves * sizeof(LeafModel)) || !derr.alloc(P.leaves * 4ull)) {
     cudaGetLastError();
     return PLANB_ENOMEM;
   }
-  float w0[kMlpParams];
+  float w0[kMlpWeights];
   std::copy(P.mlp.w1, P.mlp.w1 + kMlpHidden, w0);
   std::copy(P.mlp.b1, P.mlp.b1 + kMlpHidden, w0 + kMlpHidden);
   std::copy(P.mlp.w2, P.mlp.w2 + kMlpHidden, w0 + 2 * kMlpHidden);
   w0[3 * kMlpHidden] = P.mlp.b2;
+  std::copy(P.mlp.cap, P.mlp.cap + kMlpHidden, w0 + kMlpParams);
   bool ok = cudaMemcpyAsync(dk.p, khi.data(), n * 8ull, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(du.p, hu.data(), n * 4ull, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(dl.p, hl.data(), n * 4ull, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(dt.p, ht.data(), n * 4ull, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(dw.p, w0, sizeof(w0), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-            cudaMemsetAsync(dm.p, 0, kMlpParams * 4, st) == cudaSuccess &&
-            cudaMemsetAsync(dv.p, 0, kMlpParams * 4, st) == cudaSuccess &&
+            cudaMemsetAsync(dm.p, 0, kRow * 4, st) == cudaSuccess &&
+            cudaMemsetAsync(dq.p, 0, kRow * 4, st) == cudaSuccess &&
             cudaMemsetAsync(dstep.p, 0, sizeof(int), st) == cudaSuccess;
+  if (iters > 0)
+    ok = ok &&
+         cudaMemcpyAsync(dv.p, v0, sizeof(v0), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+         cudaMemcpyAsync(dc.p, c, sizeof(c), cudaMemcpyHostToDevice, st) == cudaSuccess;
   if (!ok) return PLANB_ECUDA;
   // loss before training
-  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(du.as<float>(), dt.as<float>(), n,
-                                                        dw.as<float>(), dpart.as<float>());
-  reduce_adam_kernel<<<1, 64, 0, st>>>(dpart.as<float>(), kGradBlocks, n, nullptr, nullptr,
-                                       nullptr, nullptr, 0.0f, 0, nullptr, dloss.as<double>());
+  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(du.as<float>(), dl.as<float>(),
+                                                        dt.as<float>(), n, dw.as<float>(),
+                                                        dpart.as<float>());
+  reduce_kernel<<<1, 64, 0, st>>>(dpart.as<float>(), kGradBlocks, n, nullptr,
+                                  dloss.as<double>());
   if (cudaMemcpyAsync(&out.loss0, dloss.p, sizeof(double), cudaMemcpyDeviceToHost, st) !=
       cudaSuccess)
     return PLANB_ECUDA;
@@ -267,11 +337,12 @@ int build_learned(const Intervals& iv, uint32_t span, uint32_t leaves, uint32_t 
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return PLANB_ECUDA;
     for (uint32_t it = 0; it < chunk; it++) {
-      mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(du.as<float>(), dt.as<float>(), n,
-                                                            dw.as<float>(), dpart.as<float>());
-      reduce_adam_kernel<<<1, 64, 0, st>>>(dpart.as<float>(), kGradBlocks, n, dw.as<float>(),
-                                           dm.as<float>(), dv.as<float>(), dstep.as<int>(), lr, 1,
-                                           nullptr, dloss.as<double>());
+      mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(du.as<float>(), dl.as<float>(),
+                                                        dt.as<float>(), n, dw.as<float>(),
+                                                        dpart.as<float>());
+      knot_adam_kernel<<<1, 64, 0, st>>>(dpart.as<float>(), kGradBlocks, n, dw.as<float>(),
+                                         dv.as<float>(), dm.as<float>(), dq.as<float>(),
+                                         dc.as<float>(), dstep.as<int>(), lr, dloss.as<double>());
       bump_step<<<1, 1, 0, st>>>(dstep.as<int>());
     }
     if (cudaStreamEndCapture(st, &graph) != cudaSuccess) return PLANB_ECUDA;
@@ -288,11 +359,12 @@ int build_learned(const Intervals& iv, uint32_t span, uint32_t leaves, uint32_t 
     out.iters = ((iters + chunk - 1) / chunk) * chunk;
   }
   // final loss with the trained weights
-  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(du.as<float>(), dt.as<float>(), n,
-                                                        dw.as<float>(), dpart.as<float>());
-  reduce_adam_kernel<<<1, 64, 0, st>>>(dpart.as<float>(), kGradBlocks, n, nullptr, nullptr,
-                                       nullptr, nullptr, 0.0f, 0, nullptr, dloss.as<double>());
-  float w1[kMlpParams];
+  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(du.as<float>(), dl.as<float>(),
+                                                        dt.as<float>(), n, dw.as<float>(),
+                                                        dpart.as<float>());
+  reduce_kernel<<<1, 64, 0, st>>>(dpart.as<float>(), kGradBlocks, n, nullptr,
+                                  dloss.as<double>());
+  float w1[kMlpWeights];
   if (cudaMemcpyAsync(w1, dw.p, sizeof(w1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpyAsync(&out.loss, dloss.p, sizeof(double), cudaMemcpyDeviceToHost, st) !=
           cudaSuccess ||

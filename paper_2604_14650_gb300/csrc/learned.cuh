@@ -4,9 +4,9 @@
 //
 // The model is a two-layer recursive model index over the table's keys (the inclusive interval
 // ends), predicting for an address x the count of keys below x, i.e. its interval index:
-//   root   u = (x.hi - kmin) / (kmax - kmin) clamped to [0, 1] (an integer range reduction, then one
-//          FP32 conversion), y = b2 + sum_h w2[h] * max(w1[h] * u + b1[h], 0) with 16 hidden units;
-//          leaf = floor(y * L) clamped to [0, L).
+//   root   u = (x.hi - kmin) / (kmax - kmin) (an integer range reduction, then a two-float
+//          conversion), y = b2 + sum_h w2[h] * min(max(w1[h] * u + b1[h], 0), cap[h]) with 16
+//          saturating ReLU units; leaf = floor(y * L) clamped to [0, L).
 //   leaf   rank = a + s * (x.hi - base) in FP32, on the signed 64-bit distance to the leaf's base.
 // Each leaf records the largest |predicted - true rank| over the keys routed to it, plus one for
 // addresses between keys; a leaf whose bound exceeds the window limit is marked for the tree path.
@@ -21,21 +21,39 @@
 
 namespace planb {
 
-__host__ __device__ __forceinline__ float mlp_eval(const MlpWeights& w, float u) {
+// The root's input is carried as an unevaluated sum u = uh + ul of two floats (about 48 bits), so
+// that keys packed into a tiny part of the key range (a dense regional block) stay distinct; the
+// first layer adds the parts in an order that keeps the sum exact near each knot.
+// Saturating units keep every term of the output sum bounded by its unit's rise, so a steep segment
+// (a dense block of keys) does not cost the rest of the curve its FP32 precision by cancellation.
+__host__ __device__ __forceinline__ float mlp_eval(const MlpWeights& w, float uh, float ul) {
   float y = w.b2;
 #pragma unroll
-  for (int h = 0; h < kMlpHidden; h++) y = fmaf(w.w2[h], fmaxf(fmaf(w.w1[h], u, w.b1[h]), 0.0f), y);
+  for (int h = 0; h < kMlpHidden; h++) {
+    const float z = fmaf(w.w1[h], ul, fmaf(w.w1[h], uh, w.b1[h]));
+    y = fmaf(w.w2[h], fminf(fmaxf(z, 0.0f), w.cap[h]), y);
+  }
   return y;
 }
 
-#ifdef __CUDACC__
-__device__ __forceinline__ float root_input(const LearnedParams& P, uint64_t xh) {
-  const uint64_t d = xh > P.kmin ? xh - P.kmin : 0ull;
-  return fminf(__ull2float_rz(d) * P.inv_range, 1.0f);
+// (uh, ul) of (x - kmin) * inv_range for an offset d = x - kmin >= 0: uh = float(d) * inv_range
+// rounded, ul = the rest (the conversion's and the product's rounding errors).
+__host__ __device__ __forceinline__ void split_input(uint64_t d, float inv_range, float* uh,
+                                                     float* ul) {
+  const float f = static_cast<float>(d);                       // rounds to nearest
+  const uint64_t fi = f >= 18446744073709551616.0f ? ~0ull : static_cast<uint64_t>(f);
+  const long long r = static_cast<long long>(d - fi);          // |r| <= 2^39 for d < 2^64
+  const float hi = f * inv_range;
+  const float prod_err = fmaf(f, inv_range, -hi);              // exact error of the product
+  *uh = hi;
+  *ul = fmaf(static_cast<float>(r), inv_range, prod_err);
 }
 
+#ifdef __CUDACC__
 __device__ __forceinline__ uint32_t predict_leaf(const LearnedParams& P, uint64_t xh) {
-  const float y = mlp_eval(P.mlp, root_input(P, xh));
+  float uh, ul;
+  split_input(xh > P.kmin ? xh - P.kmin : 0ull, P.inv_range, &uh, &ul);
+  const float y = mlp_eval(P.mlp, uh, ul);
   int l = __float2int_rd(y * static_cast<float>(P.leaves));
   l = l < 0 ? 0 : l;
   return static_cast<uint32_t>(l) >= P.leaves ? P.leaves - 1u : static_cast<uint32_t>(l);
@@ -87,5 +105,7 @@ int mlp_grad_host(const float* d_u, const float* d_t, size_t n, const float* w_h
 
 // y = root(u) for device arrays; asynchronous on `st`.
 int mlp_forward_host(const float* d_u, size_t n, const float* w_host, float* d_y, cudaStream_t st);
+
+// (the two gradient/forward entry points take a single-float input: ul = 0)
 
 }  // namespace planb

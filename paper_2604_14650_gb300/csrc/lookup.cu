@@ -64,7 +64,26 @@ struct KParams {
   const LeafModel* leaves;    // learned: leaf models (copied to shared memory)
   const uint16_t* leaf_err;   // learned: per-leaf window half-width or kLeafFallback
   LearnedParams lp;           // learned: root weights and range reduction
+  const uint64_t* range;      // multi-table: device [begin, end) of this launch's addresses
+  const uint32_t* perm;       // multi-table: result of address j goes to out[perm[j]]
 };
+
+// The addresses a launch handles: [0, n), or the device-side range a bucketing pass wrote.
+struct Seg {
+  uint64_t off, n;
+};
+
+template <bool MULTI = true>
+__device__ __forceinline__ Seg segment(const KParams& p) {
+  if (!MULTI || !p.range) return Seg{0, p.n};
+  const uint64_t b = p.range[0], e = p.range[1];
+  return Seg{b, e > b ? e - b : 0};
+}
+
+template <bool MULTI = true>
+__device__ __forceinline__ void store_out(const KParams& p, uint64_t j, uint16_t v) {
+  p.out[(MULTI && p.perm) ? p.perm[j] : j] = v;
+}
 
 // 128-bit unsigned k < x
 __device__ __forceinline__ bool less128(uint64_t kh, uint64_t kl, uint64_t xh, uint64_t xl) {
@@ -109,11 +128,12 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f8(const KParams p) {
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
   const uint32_t S = p.smem_levels;
 
-  for (uint64_t base = warp * 32; base < p.n; base += nwarps * 32) {
+  const Seg seg = segment(p);
+  for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
     const uint64_t mine = base + lane;
-    const bool ok = mine < p.n;
-    const uint64_t my_hi = ok ? p.xhi[mine] : 0ull;
-    const uint64_t my_lo = ok ? p.xlo[mine] : 0ull;
+    const bool ok = mine < seg.n;
+    const uint64_t my_hi = ok ? p.xhi[seg.off + mine] : 0ull;
+    const uint64_t my_lo = ok ? p.xlo[seg.off + mine] : 0ull;
     uint32_t result = 0;
 #pragma unroll
     for (uint32_t r = 0; r < 8; r++) {
@@ -140,7 +160,7 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f8(const KParams p) {
       const uint32_t v = __ldg(p.values + rank);
       if (j == r) result = v;
     }
-    if (ok) p.out[mine] = static_cast<uint16_t>(result);
+    if (ok) store_out(p, seg.off + mine, static_cast<uint16_t>(result));
   }
 }
 
@@ -164,11 +184,12 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
   const uint32_t S = p.smem_levels;
 
-  for (uint64_t base = warp * 32; base < p.n; base += nwarps * 32) {
+  const Seg seg = segment(p);
+  for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
     const uint64_t mine = base + lane;
-    const bool ok = mine < p.n;
-    const uint64_t my_hi = ok ? p.xhi[mine] : 0ull;
-    const uint64_t my_lo = ok ? p.xlo[mine] : 0ull;
+    const bool ok = mine < seg.n;
+    const uint64_t my_hi = ok ? p.xhi[seg.off + mine] : 0ull;
+    const uint64_t my_lo = ok ? p.xlo[seg.off + mine] : 0ull;
     uint32_t result = 0;
 #pragma unroll 4
     for (uint32_t r = 0; r < 16; r++) {
@@ -198,7 +219,7 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
       const uint32_t v = __ldg(p.values + rank);
       if (j == r) result = v;
     }
-    if (ok) p.out[mine] = static_cast<uint16_t>(result);
+    if (ok) store_out(p, seg.off + mine, static_cast<uint16_t>(result));
   }
 }
 
@@ -223,7 +244,7 @@ constexpr int kRounds = 4;  // addresses per group in flight during the L2 level
 // buckets of ranks [rank - e, rank + e], and a short search among them gives the count — accepted
 // only when the entries just outside the window bracket the address (so the count is exact whatever
 // the model said). Otherwise, and for leaves marked for the tree, the full binary search runs.
-template <int DB, bool PACKED, bool LEARNED>
+template <int DB, bool PACKED, bool LEARNED, bool MULTI>
 __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
@@ -247,11 +268,12 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
 
-  for (uint64_t base = warp * 32; base < p.n; base += nwarps * 32) {
+  const Seg seg = segment<MULTI>(p);
+  for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
     const uint64_t mine = base + lane;
-    const bool ok = mine < p.n;
-    const uint64_t my_hi = ok ? p.xhi[mine] : 0ull;
-    const uint64_t my_lo = ok ? p.xlo[mine] : 0ull;
+    const bool ok = mine < seg.n;
+    const uint64_t my_hi = ok ? p.xhi[seg.off + mine] : 0ull;
+    const uint64_t my_lo = ok ? p.xlo[seg.off + mine] : 0ull;
     // phase A: per-thread count over the level-S subtree maxima in shared memory
     uint32_t cnt = 0;
     bool have = false;
@@ -303,7 +325,7 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
       }
 #endif
       const uint16_t v = __ldg(p.values + rank);
-      if (ok) p.out[mine] = v;
+      if (ok) store_out<MULTI>(p, seg.off + mine, v);
     } else {
       const uint32_t my_node = p.sidx_node + cnt;
       uint32_t result = 0;
@@ -378,7 +400,7 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
           }
         }
       }
-      if (ok) p.out[mine] = static_cast<uint16_t>(result);
+      if (ok) store_out<MULTI>(p, seg.off + mine, static_cast<uint16_t>(result));
     }
   }
 }
@@ -389,9 +411,10 @@ __global__ void __launch_bounds__(256) lookup_flat(const KParams p) {
   const uint32_t nk = static_cast<uint32_t>(p.n_intervals - 1);
   auto gload = [keys](uint32_t i) { return __ldg(keys + i); };
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < p.n;
+  const Seg seg = segment(p);
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < seg.n;
        i += stride) {
-    const uint64_t xh = p.xhi[i], xl = p.xlo[i];
+    const uint64_t xh = p.xhi[seg.off + i], xl = p.xlo[seg.off + i];
     uint32_t rank = nk ? count_below(gload, nk, xh, xl) : 0u;
 #ifdef PLANB_BOUNDS_CHECK
     if (rank >= p.n_intervals) {
@@ -399,7 +422,7 @@ __global__ void __launch_bounds__(256) lookup_flat(const KParams p) {
       rank = 0;
     }
 #endif
-    p.out[i] = __ldg(p.values + rank);
+    store_out(p, seg.off + i, __ldg(p.values + rank));
   }
 }
 
@@ -407,7 +430,7 @@ typedef void (*KernelFn)(const KParams);
 
 constexpr int kMaxDepth = 10;
 
-KernelFn kernel_for(const DevTable& t) {
+KernelFn kernel_for(const DevTable& t, bool multi = false) {
   static const KernelFn f8[kMaxDepth + 1] = {
       nullptr,            lookup_coop_f8<1>, lookup_coop_f8<2>, lookup_coop_f8<3>,
       lookup_coop_f8<4>,  lookup_coop_f8<5>, lookup_coop_f8<6>, lookup_coop_f8<7>,
@@ -416,21 +439,26 @@ KernelFn kernel_for(const DevTable& t) {
       nullptr,             lookup_coop_f16<1>, lookup_coop_f16<2>, lookup_coop_f16<3>,
       lookup_coop_f16<4>,  lookup_coop_f16<5>, lookup_coop_f16<6>, lookup_coop_f16<7>,
       lookup_coop_f16<8>,  lookup_coop_f16<9>, lookup_coop_f16<10>};
-#define PLANB_HYB(P, L)                                                                          \
+#define PLANB_HYB(P, L, M)                                                                       \
   {                                                                                               \
-    lookup_hybrid<0, P, L>, lookup_hybrid<1, P, L>, lookup_hybrid<2, P, L>,                       \
-        lookup_hybrid<3, P, L>, lookup_hybrid<4, P, L>, lookup_hybrid<5, P, L>,                   \
-        lookup_hybrid<6, P, L>, lookup_hybrid<7, P, L>, lookup_hybrid<8, P, L>,                   \
-        lookup_hybrid<9, P, L>, lookup_hybrid<10, P, L>                                           \
+    lookup_hybrid<0, P, L, M>, lookup_hybrid<1, P, L, M>, lookup_hybrid<2, P, L, M>,              \
+        lookup_hybrid<3, P, L, M>, lookup_hybrid<4, P, L, M>, lookup_hybrid<5, P, L, M>,          \
+        lookup_hybrid<6, P, L, M>, lookup_hybrid<7, P, L, M>, lookup_hybrid<8, P, L, M>,          \
+        lookup_hybrid<9, P, L, M>, lookup_hybrid<10, P, L, M>                                     \
   }
+  // [packed][learned][multi]; the learned kernel has no multi-table form
   static const KernelFn hyb[2][2][kMaxDepth + 1] = {
-      {PLANB_HYB(false, false), PLANB_HYB(false, true)},
-      {PLANB_HYB(true, false), PLANB_HYB(true, true)}};
+      {PLANB_HYB(false, false, false), PLANB_HYB(false, true, false)},
+      {PLANB_HYB(true, false, false), PLANB_HYB(true, true, false)}};
+  static const KernelFn hyb_multi[2][kMaxDepth + 1] = {PLANB_HYB(false, false, true),
+                                                       PLANB_HYB(true, false, true)};
 #undef PLANB_HYB
   const uint32_t D = t.depth;
   if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
   if (t.format == PLANB_FMT_F16HI) return f16[D];
   const bool packed = t.format == PLANB_FMT_F8V7;
+  if (t.kernel == kHybrid && multi)
+    return t.smem_levels <= D ? hyb_multi[packed][D - t.smem_levels] : nullptr;
   if (t.kernel == kHybrid || t.kernel == kLearned)
     return t.smem_levels <= D ? hyb[packed][t.kernel == kLearned][D - t.smem_levels] : nullptr;
   if (packed) return nullptr;
@@ -469,6 +497,11 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(cfg.smem_bytes)) != cudaSuccess)
     return PLANB_ECUDA;
+  if (KernelFn fm = (t.kernel == kHybrid) ? kernel_for(t, true) : nullptr)
+    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(fm),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(cfg.smem_bytes)) != cudaSuccess)
+      return PLANB_ECUDA;
   int sms = 0, per_sm = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
     return PLANB_ECUDA;
@@ -483,9 +516,11 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
 
 int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   const uint64_t* d_lo, size_t n, uint16_t* d_out, uint32_t* d_status,
-                  void* stream) {
+                  void* stream, const uint64_t* d_range, const uint32_t* d_perm) {
   if (n == 0) return PLANB_OK;
-  KernelFn fn = kernel_for(t);
+  const bool multi = d_range != nullptr || d_perm != nullptr;
+  if (multi && t.kernel == kLearned) return PLANB_EINVAL;   // no multi-table form
+  KernelFn fn = kernel_for(t, multi);
   if (!fn) return PLANB_EINVAL;
   KParams p;
   p.nodes = static_cast<const ulonglong2*>(t.nodes);
@@ -508,6 +543,8 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   p.leaves = t.leaves;
   p.leaf_err = t.leaf_err;
   p.lp = t.lp;
+  p.range = d_range;
+  p.perm = d_perm;
   uint64_t blocks;
   if (t.kernel == kFlat) {
     blocks = (n + cfg.threads - 1) / cfg.threads;

@@ -13,14 +13,18 @@ namespace planb {
 // ------------------------------------------------------------- learned position model (data)
 // (inference and training code: learned.cuh / learned.cu)
 constexpr int kMlpHidden = 16;
-constexpr int kMlpParams = 3 * kMlpHidden + 1;   // w1, b1, w2, b2
+constexpr int kMlpParams = 3 * kMlpHidden + 1;   // trained: w1, b1, w2, b2
+constexpr int kMlpWeights = kMlpParams + kMlpHidden;  // + cap (the units' fixed saturation widths)
 constexpr uint16_t kLeafFallback = 0xFFFFu;       // error value that sends a leaf to the tree path
 
+// Hidden unit h: a_h = min(max(w1[h] u + b1[h], 0), cap[h]) (a ReLU that saturates at cap[h]);
+// output y = b2 + sum_h w2[h] a_h.
 struct MlpWeights {
   float w1[kMlpHidden];
   float b1[kMlpHidden];
   float w2[kMlpHidden];
   float b2;
+  float cap[kMlpHidden];
 };
 
 struct LeafModel {
@@ -151,10 +155,23 @@ struct LaunchCfg {
   size_t smem_bytes = 0;
 };
 
-// Launches the lookup kernel for one table on `stream`. d_status may be null.
+// Launches the lookup kernel for one table on `stream`. d_status may be null. With d_range (device
+// [begin, end)) the launch handles addresses begin..end-1 of d_hi/d_lo instead of 0..n-1 (n then only
+// sizes the grid); with d_perm the result of address j is stored at d_out[d_perm[j]].
 int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   const uint64_t* d_lo, size_t n, uint16_t* d_out, uint32_t* d_status,
-                  void* stream);
+                  void* stream, const uint64_t* d_range = nullptr,
+                  const uint32_t* d_perm = nullptr);
+
+// Multi-table bucketing (multi.cu): groups n addresses by their u8 table id (ids >= T form one
+// extra segment) into d_bhi/d_blo, table-major, with d_perm[j] = original index; d_range[t] ..
+// d_range[t+1] bound table t's segment. d_counts holds (T+1) x G words. n < 2^32.
+int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
+                     uint32_t T, uint32_t G, uint32_t* d_counts, uint64_t* d_range,
+                     uint64_t* d_bhi, uint64_t* d_blo, uint32_t* d_perm, void* stream);
+// Writes next hop 0 for the addresses of the invalid-id segment.
+int launch_invalid_fill(const uint64_t* d_range, uint32_t T, const uint32_t* d_perm,
+                        uint16_t* d_out, void* stream);
 
 // Occupancy-derived launch configuration for a table on a device.
 int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, LaunchCfg& cfg);

@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "_build", platform.machine())
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["builder.cpp", "lookup.cu", "learned.cu", "capi.cu"]
+SOURCES = ["builder.cpp", "lookup.cu", "learned.cu", "multi.cu", "capi.cu"]
 LIBS = {"libplanb.so": [], "libplanb_checked.so": ["-DPLANB_BOUNDS_CHECK"]}
 
 

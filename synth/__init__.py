@@ -133,7 +133,8 @@ def gen_fib(n: int, seed: int, nh_max: int = 255, nested_frac: float = 0.30,
             default: bool = True, root_prefix_bits: int = 3, root_prefix_value: int = 0x1) -> Fib:
     """``n`` distinct synthetic prefixes (plus ::/0 -> 0 when ``default``), seeded.
 
-    Roots get their top ``root_prefix_bits`` bits equal to ``root_prefix_value`` (2000::/3 by default).
+    Roots get their top ``root_prefix_bits`` bits equal to ``root_prefix_value`` (2000::/3 by default);
+    a root too short to leave 12 free bits inside that region is placed in 2000::/3 instead.
     """
     lens = sample_lengths(seed, n)
     nested = unit(u64(seed, S_NEST, 0, n)) < nested_frac
@@ -148,6 +149,7 @@ def gen_fib(n: int, seed: int, nh_max: int = 255, nested_frac: float = 0.30,
     rpar_all = u64(seed, S_PARENT, 0, n)
     redraw_ctr = 0
     rp_hi = np.uint64((root_prefix_value << (64 - root_prefix_bits)) & 0xFFFFFFFFFFFFFFFF)
+    g_bits, g_hi = 3, np.uint64(0x2000000000000000)       # 2000::/3, for roots shorter than the region
     for L in order_lens:
         idx = np.nonzero(lens == L)[0]
         cand = np.nonzero(placed & (lens < L))[0]
@@ -159,8 +161,9 @@ def gen_fib(n: int, seed: int, nh_max: int = 255, nested_frac: float = 0.30,
             k = pend.size
             Lk = np.full(k, L, dtype=np.int64)
             # roots: fixed top bits, random bits in [root_prefix_bits, L)
-            mh, ml = bit_range_mask(np.full(k, root_prefix_bits), Lk)
-            ahi = (rhi & mh) | rp_hi
+            rb, rh = (root_prefix_bits, rp_hi) if L >= root_prefix_bits + 12 else (g_bits, g_hi)
+            mh, ml = bit_range_mask(np.full(k, rb), Lk)
+            ahi = (rhi & mh) | rh
             alo = rlo & ml
             if cand.size:
                 par = cand[below(rpar, cand.size)]

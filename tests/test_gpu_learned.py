@@ -24,8 +24,13 @@ def built():
 
 
 def weights(rng):
+    """65 floats: the 49 trained parameters (w1, b1, w2, b2), then the 16 saturation caps."""
     return np.concatenate([rng.normal(size=H), rng.normal(size=H) * 0.5, rng.normal(size=H),
-                           [rng.normal()]]).astype(np.float32)
+                           [rng.normal()], rng.random(H) * 1.5 + 0.05]).astype(np.float32)
+
+
+def split(w):
+    return w[:3 * H + 1].astype(np.float64), w[3 * H + 1:].astype(np.float64)
 
 
 @pytest.mark.parametrize("n", [1, 1000, 300_001])
@@ -35,7 +40,8 @@ def test_forward_matches_oracle(n):
     u = rng.random(n).astype(np.float32)
     y = pb.mlp_forward(torch.from_numpy(u).cuda(), w)
     torch.cuda.synchronize()
-    ref = OL.forward(w.astype(np.float64), u.astype(np.float64))
+    th, cap = split(w)
+    ref = OL.forward(th, u.astype(np.float64), H, cap)
     # 16 fused multiply-adds in FP32 on O(1) values: a few units in the last place of O(10)
     assert np.max(np.abs(y.cpu().numpy() - ref)) <= 1e-5 * max(1.0, np.max(np.abs(ref)))
 
@@ -50,7 +56,8 @@ def test_gradient_matches_oracle(n, seed):
     u = rng.random(n).astype(np.float32)
     t = np.sort(rng.random(n)).astype(np.float32)
     loss, g = pb.mlp_grad(torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda(), w)
-    ref_loss, ref = OL.grad(w.astype(np.float64), u.astype(np.float64), t.astype(np.float64))
+    th, cap = split(w)
+    ref_loss, ref = OL.grad(th, u.astype(np.float64), t.astype(np.float64), H, cap)
     assert abs(loss - ref_loss) <= 1e-5 * max(ref_loss, 1e-12)
     tol = 1e-4 * np.max(np.abs(ref)) + 1e-7
     assert np.max(np.abs(g - ref)) <= tol, (np.max(np.abs(g - ref)), tol)
@@ -63,16 +70,28 @@ def test_gradient_descent_direction():
     u = rng.random(50_000).astype(np.float32)
     t = np.sort(rng.random(50_000)).astype(np.float32)
     _, g = pb.mlp_grad(torch.from_numpy(u).cuda(), torch.from_numpy(t).cuda(), w)
-    l0 = OL.loss(w.astype(np.float64), u, t)
-    l1 = OL.loss((w - 1e-3 * g / np.linalg.norm(g)).astype(np.float64), u, t)
+    th, cap = split(w)
+    l0 = OL.loss(th, u, t, H, cap)
+    l1 = OL.loss(th - 1e-3 * g / np.linalg.norm(g), u, t, H, cap)
     assert l1 < l0
 
 
+def skewed_fib():
+    """150,000 prefixes spread over 2000::/3 plus 50,000 packed into one /24 (2a00:0100::/24): a key
+    distribution whose CDF is far from linear, as dense regional allocations make real tables."""
+    a = synth.gen_fib(150_000, seed=2604, nh_max=4095, default=False)
+    b = synth.gen_fib(50_000, seed=2605, nh_max=4095, root_prefix_bits=24,
+                      root_prefix_value=0x2A0001)
+    return synth.Fib(np.concatenate([a.hi, b.hi]), np.concatenate([a.lo, b.lo]),
+                     np.concatenate([a.len, b.len]), np.concatenate([a.nh, b.nh]), 0)
+
+
 def test_trained_root_gains_over_untrained():
-    """Same table, same leaves: the trained root fits the key CDF better than the untrained one
-    (the identity, i.e. plain linear range reduction), so its leaves are better balanced and more
-    keys fall in leaves whose error window is within the limit; lookups stay exact either way."""
-    f = synth.gen_fib(200_000, seed=2604, nh_max=4095)
+    """Same table, same leaf count: the untrained root is the identity (plain linear range
+    reduction); training it on the GPU to the key CDF routes keys evenly over the leaves, so more
+    keys land in leaves whose error window is within the limit and the mean window shrinks.
+    Lookups are exact either way."""
+    f = skewed_fib()
     xh, xl = synth.gen_trace(f, 2_000_000, seed=9)
     want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl)
     stats = {}
@@ -85,6 +104,8 @@ def test_trained_root_gains_over_untrained():
             torch.cuda.synchronize()
             assert np.array_equal(out.cpu().numpy().view(np.uint16), want)
     a, b = stats[0], stats[2000]
+    print("untrained", {k: a[k] for k in a if k.startswith("model")})
+    print("trained", {k: b[k] for k in b if k.startswith("model")})
     assert b["model_iters"] >= 2000 and a["model_iters"] == 0
     assert b["model_loss"] < 0.1 * a["model_loss0"]
     assert b["model_covered"] > a["model_covered"]

@@ -1,0 +1,111 @@
+"""Multi-table (VRF) lookups: each address carries a u8 table id; one captured graph buckets the
+batch by table, runs one lookup per table and writes results back in input order. Checked
+bit-exactly against the oracle of each table."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2604_14650_gb300 as pb  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pb.build()
+
+
+def dev(a, dtype=np.int64):
+    return torch.from_numpy(np.ascontiguousarray(a).view(dtype)).cuda()
+
+
+def workload(sizes, n, seed, invalid=0.01):
+    fibs = [synth.gen_fib(s, seed=seed + t, nh_max=4095) for t, s in enumerate(sizes)]
+    rng = np.random.default_rng(seed)
+    p = np.array(sizes, float) / sum(sizes)
+    tid = rng.choice(len(sizes), size=n, p=p).astype(np.uint8)
+    bad = rng.random(n) < invalid
+    tid[bad] = rng.integers(len(sizes), 256, size=int(bad.sum()), dtype=np.uint8)
+    xh = np.empty(n, np.uint64)
+    xl = np.empty(n, np.uint64)
+    for t, f in enumerate(fibs):
+        idx = np.nonzero(tid == t)[0]
+        h, l = synth.gen_trace(f, idx.size, seed=seed + 100 + t)
+        xh[idx], xl[idx] = h, l
+    idx = np.nonzero(tid >= len(sizes))[0]
+    xh[idx] = rng.integers(0, 2 ** 63, idx.size, dtype=np.uint64)
+    xl[idx] = rng.integers(0, 2 ** 63, idx.size, dtype=np.uint64)
+    return fibs, tid, xh, xl
+
+
+def expected(fibs, tid, xh, xl):
+    want = np.zeros(tid.size, np.uint16)
+    for t, f in enumerate(fibs):
+        idx = np.nonzero(tid == t)[0]
+        want[idx] = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh[idx], xl[idx])
+    return want
+
+
+@pytest.mark.parametrize("kinds", [("f8x128", "hybrid"), ("f8v7", "hybrid"), ("mixed", None)])
+def test_multi_table_parity_and_replay(kinds):
+    sizes = [500, 3000, 20_000, 1000, 60_000, 7, 12_000, 2500]
+    fibs_in, tid, xh, xl = workload(sizes, 600_000, seed=41)
+    want = expected(fibs_in, tid, xh, xl)
+    choices = [("f8x128", "hybrid"), ("f8v7", "hybrid"), ("f8x128", "coop"), ("f8x128", "flat"),
+               ("f16hi", "coop")]
+    fibs = []
+    for t, f in enumerate(fibs_in):
+        fmt, ker = kinds if kinds[0] != "mixed" else choices[t % len(choices)]
+        fibs.append(pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=ker))
+    with pb.MultiFib(fibs, max_batch=1 << 20) as mt:
+        dh, dl, dt = dev(xh), dev(xl), dev(tid, np.uint8)
+        out = torch.empty(tid.size, dtype=torch.int16, device="cuda")
+        for _ in range(3):                     # first call captures the graph, the others replay
+            out.fill_(-1)
+            mt.lookup(dh, dl, dt, out=out)
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy().view(np.uint16), want)
+        # a smaller batch (new capture) and an empty one
+        k = 12_345
+        small = mt.lookup(dh[:k], dl[:k], dt[:k])
+        torch.cuda.synchronize()
+        assert np.array_equal(small.cpu().numpy().view(np.uint16), want[:k])
+        mt.lookup(dh[:0], dl[:0], dt[:0])
+    for f in fibs:
+        f.close()
+
+
+def test_multi_table_sees_updates():
+    sizes = [5000, 20_000, 800]
+    fibs_in, tid, xh, xl = workload(sizes, 300_000, seed=51)
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh) for f in fibs_in]
+    with pb.MultiFib(fibs, max_batch=300_000) as mt:
+        dh, dl, dt = dev(xh), dev(xl), dev(tid, np.uint8)
+        out = mt.lookup(dh, dl, dt)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
+        # withdraw every prefix of table 1 except the default: its addresses then all get 0
+        f1 = fibs_in[1]
+        keep = f1.len == 0
+        fibs[1].update(wd_hi=f1.hi[~keep], wd_lo=f1.lo[~keep], wd_len=f1.len[~keep])
+        fibs_in[1] = synth.Fib(f1.hi[keep], f1.lo[keep], f1.len[keep], f1.nh[keep], 0)
+        out = mt.lookup(dh, dl, dt, out=out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint16)
+        assert np.array_equal(got, expected(fibs_in, tid, xh, xl))
+        assert np.all(got[tid == 1] == 0)
+    for f in fibs:
+        f.close()
+
+
+def test_learned_tables_cannot_join():
+    f = synth.gen_fib(2000, seed=3)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, kernel="learned") as fib:
+        with pytest.raises(pb.PlanbError):
+            pb.MultiFib([fib], max_batch=1000)

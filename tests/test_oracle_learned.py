@@ -1,22 +1,38 @@
 """Pins of the learned model's CPU oracle (oracle/learned.py) to facts outside it."""
 import numpy as np
+import pytest
 
 from oracle import learned as L
 
 
-def test_gradient_matches_central_differences():
+@pytest.mark.parametrize("capped", [False, True])
+def test_gradient_matches_central_differences(capped):
     rng = np.random.default_rng(1)
     H = 16
     theta = rng.normal(size=3 * H + 1)
+    cap = rng.random(H) * 1.5 + 0.05 if capped else None
     u = rng.random(500)
     t = np.sort(rng.random(500))
-    _, g = L.grad(theta, u, t, H)
+    _, g = L.grad(theta, u, t, H, cap)
     eps = 1e-6
     for k in range(theta.size):
         d = np.zeros_like(theta)
         d[k] = eps
-        num = (L.loss(theta + d, u, t, H) - L.loss(theta - d, u, t, H)) / (2 * eps)
+        num = (L.loss(theta + d, u, t, H, cap) - L.loss(theta - d, u, t, H, cap)) / (2 * eps)
         assert abs(num - g[k]) <= 1e-6 * max(1.0, abs(num)), k
+
+
+def test_capped_units_give_the_linear_spline_through_knots():
+    """Unit slopes, knots c_h, caps c_{h+1} - c_h, output weights the segment slopes: the network is
+    the linear interpolation through (c_h, v_h) — the same values as numpy.interp."""
+    rng = np.random.default_rng(4)
+    H = 16
+    c = np.sort(rng.random(H + 1))
+    v = np.sort(rng.random(H + 1))
+    s = np.diff(v) / np.diff(c)
+    theta = np.concatenate([np.ones(H), -c[:H], s, [v[0]]])
+    u = rng.uniform(c[0], c[-1], 1000)
+    assert np.allclose(L.forward(theta, u, H, np.diff(c)), np.interp(u, c, v), atol=1e-12)
 
 
 def test_zero_gradient_at_least_squares_optimum():
