@@ -212,6 +212,11 @@ void planb_destroy(planb_fib *fib);
 /* planb_strerror — a static string naming a PLANB_* code. */
 const char *planb_strerror(int code);
 
+/* planb_last_error — where the last failing call on this thread failed, with the CUDA error text
+ * when there was one ("" if none recorded). The string belongs to the library and stays valid until
+ * the next failing call on the same thread. */
+const char *planb_last_error(void);
+
 /* ------------------------------------------------------------------------ multi-table lookups */
 
 typedef struct planb_multi planb_multi; /* several tables (VRFs) served by one captured graph */
@@ -222,11 +227,12 @@ typedef struct planb_multi planb_multi; /* several tables (VRFs) served by one c
  * same lookup applied per table. fibs: n_tables table handles (1..255), not owned: they must
  * outlive the group; updates to them are picked up by later lookups. max_batch: most addresses per
  * planb_multi_lookup call (< 2^32); the group owns max_batch x 20 bytes of device scratch.
- * Tables built with PLANB_KERNEL_LEARNED cannot join a group.
+ * Tables built with PLANB_KERNEL_LEARNED cannot join a group. flags: 0, or PLANB_MULTI_NO_GRAPH.
  * Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ECUDA.
  */
+#define PLANB_MULTI_NO_GRAPH 1u /* flag: launch the pipeline directly instead of a captured graph */
 int planb_multi_create(planb_fib *const *fibs, uint32_t n_tables, size_t max_batch,
-                       planb_multi **out);
+                       uint32_t flags, planb_multi **out);
 
 /*
  * planb_multi_lookup — next hop of n addresses, address i looked up in table d_table[i]
@@ -317,6 +323,14 @@ uint64_t planb_child_index(uint32_t keys_per_node, uint32_t d, uint64_t j, uint3
  * Errors: PLANB_EINVAL for another point.
  */
 int planb_debug_inject(int point);
+
+/*
+ * planb_debug_kernel_info — test hook (the paper has no counterpart): the CUDA function attributes
+ * of the lookup kernel a table uses (multi != 0: its multi-table form), out6[0..5] = registers per
+ * thread, max threads per block, max dynamic shared bytes, local (spill) bytes per thread, static
+ * shared bytes, constant bytes. Errors: PLANB_EINVAL, PLANB_ECUDA.
+ */
+int planb_debug_kernel_info(const planb_fib *fib, int multi, int *out6);
 
 /* planb_version — library version, (major << 16) | minor. */
 uint32_t planb_version(void);

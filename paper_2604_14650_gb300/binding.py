@@ -26,7 +26,13 @@ KERNELS = {"auto": 0, "coop": 1, "hybrid": 2, "flat": 3, "learned": 4}
 class PlanbError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
-        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_strerror(code)})")
+        detail = ""
+        try:
+            detail = load().planb_last_error().decode()
+        except Exception:
+            pass
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_strerror(code)})"
+                         + (f" [{detail}]" if detail else ""))
 
 
 class Opts(C.Structure):
@@ -72,6 +78,7 @@ _sz = C.c_size_t
 _SIGS = {
     "planb_opts_default": (None, [_vp]),
     "planb_strerror": (C.c_char_p, [C.c_int]),
+    "planb_last_error": (C.c_char_p, []),
     "planb_version": (C.c_uint32, []),
     "planb_build": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, C.POINTER(_vp)]),
     "planb_lookup": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
@@ -85,9 +92,10 @@ _SIGS = {
     "planb_layout_info": (C.c_int, [C.c_uint32, C.c_uint64, C.c_uint32, _vp]),
     "planb_child_index": (C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32]),
     "planb_debug_inject": (C.c_int, [C.c_int]),
+    "planb_debug_kernel_info": (C.c_int, [_vp, C.c_int, _vp]),
     "planb_mlp_grad": (C.c_int, [_vp, _vp, _sz, _vp, _vp, C.POINTER(C.c_double), _vp]),
     "planb_mlp_forward": (C.c_int, [_vp, _sz, _vp, _vp, _vp]),
-    "planb_multi_create": (C.c_int, [_vp, C.c_uint32, _sz, C.POINTER(_vp)]),
+    "planb_multi_create": (C.c_int, [_vp, C.c_uint32, _sz, C.c_uint32, C.POINTER(_vp)]),
     "planb_multi_lookup": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_multi_destroy": (None, [_vp]),
 }
@@ -298,6 +306,11 @@ class Fib:
         _check(self._lib.planb_stats(self._h, C.byref(s)), "planb_stats")
         return {f: getattr(s, f) for f, _ in Stats._fields_}
 
+    def kernel_info(self, multi: bool = False) -> dict:
+        a = (C.c_int * 6)()
+        _check(self._lib.planb_debug_kernel_info(self._h, int(multi), a), "planb_debug_kernel_info")
+        return dict(zip(("regs", "max_threads", "max_dyn_smem", "local", "static_smem", "const"), a))
+
     def device_status(self):
         w = C.c_uint32(0)
         rc = self._lib.planb_device_status(self._h, C.byref(w))
@@ -337,13 +350,14 @@ def _host_ptrs(hi, lo):
 class MultiFib:
     """Several tables (VRFs) looked up by one captured graph; each address carries a table id."""
 
-    def __init__(self, fibs, max_batch: int):
+    def __init__(self, fibs, max_batch: int, graph: bool = True):
         self._lib = fibs[0]._lib
+        self._h = None
         self.fibs = list(fibs)                 # keep the tables alive while the group exists
         arr = (C.c_void_p * len(fibs))(*[f._h.value for f in fibs])
         h = C.c_void_p()
-        _check(self._lib.planb_multi_create(arr, len(fibs), max_batch, C.byref(h)),
-               "planb_multi_create")
+        _check(self._lib.planb_multi_create(arr, len(fibs), max_batch, 0 if graph else 1,
+                                            C.byref(h)), "planb_multi_create")
         self._h = h
 
     def lookup(self, addr_hi, addr_lo, table, out=None, stream=None):

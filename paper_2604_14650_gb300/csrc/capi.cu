@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -19,6 +20,17 @@ using planb::u128;
 namespace {
 
 std::atomic<int> g_inject{0};  // test hook: 1 = fail the next build on the host, 2 = on the device
+
+thread_local char g_detail[256] = "";  // detail of the last failure on this thread
+
+// records where a call failed (and the CUDA error, if any); returns code
+int fail_detail(int code, const char* where, cudaError_t e = cudaSuccess) {
+  if (e != cudaSuccess)
+    snprintf(g_detail, sizeof(g_detail), "%s: %s", where, cudaGetErrorString(e));
+  else
+    snprintf(g_detail, sizeof(g_detail), "%s", where);
+  return code;
+}
 
 double ms_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -331,6 +343,8 @@ void planb_opts_default(planb_opts* o) {
   o->model_leaves = 0;
   o->model_iters = -1;
 }
+
+const char* planb_last_error(void) { return g_detail; }
 
 const char* planb_strerror(int code) {
   switch (code) {
@@ -698,6 +712,18 @@ int planb_mlp_forward(const float* d_u, size_t n, const float* w, float* d_y,
   return planb::mlp_forward_host(d_u, n, w, d_y, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int planb_debug_kernel_info(const planb_fib* f, int multi, int* out6) {
+  if (!f || !out6) return PLANB_EINVAL;
+  std::shared_ptr<Table> t;
+  {
+    std::lock_guard<std::mutex> lk(const_cast<planb_fib*>(f)->cur_mu);
+    t = f->cur;
+  }
+  DeviceGuard g(f->device);
+  int rc = planb::kernel_attributes(t->dt, multi != 0, out6);
+  return rc ? rc : PLANB_OK;
+}
+
 int planb_debug_inject(int point) {
   if (point < 0 || point > 2) return PLANB_EINVAL;
   g_inject.store(point);
@@ -723,12 +749,34 @@ struct planb_multi {
   size_t g_n = 0;
   std::vector<std::shared_ptr<Table>> snap;  // the tables the captured graph reads
   std::mutex mu;
+  uint32_t flags = 0;
 };
+
+namespace {
+
+// the multi-table pipeline on one stream: bucketing, one lookup per table, invalid-id fill
+int multi_pipeline(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cur,
+                   const uint64_t* d_addr_hi, const uint64_t* d_addr_lo, const uint8_t* d_table,
+                   size_t n, uint16_t* d_out, cudaStream_t s) {
+  int rc = planb::launch_bucketing(d_addr_hi, d_addr_lo, d_table, n, m->T, m->G, m->counts,
+                                   m->range, m->bhi, m->blo, m->perm, s);
+  if (rc) return fail_detail(rc, "multi: bucketing", cudaGetLastError());
+  for (uint32_t t = 0; t < m->T; t++) {
+    rc = planb::launch_lookup(cur[t]->dt, cur[t]->cfg, m->bhi, m->blo, n, d_out,
+                              m->fibs[t]->d_status, s, m->range + t, m->perm);
+    if (rc) return fail_detail(rc, "multi: table lookup", cudaGetLastError());
+  }
+  rc = planb::launch_invalid_fill(m->range, m->T, m->perm, d_out, s);
+  if (rc) return fail_detail(rc, "multi: invalid-id fill", cudaGetLastError());
+  return PLANB_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
 int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_batch,
-                       planb_multi** out) {
+                       uint32_t flags, planb_multi** out) {
   if (!out) return PLANB_EINVAL;
   *out = nullptr;
   if (!fibs || n_tables == 0 || n_tables > 255 || max_batch == 0 ||
@@ -744,6 +792,7 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     m->fibs.assign(fibs, fibs + n_tables);
     m->T = n_tables;
     m->cap = max_batch;
+    m->flags = flags;
     DeviceGuard g(m->device);
     if (!g.ok) return PLANB_ECUDA;
     int sms = 0;
@@ -798,36 +847,35 @@ int planb_multi_lookup(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t
     note_stream(f, st);
     note_stream(f, m->cap_stream);
   }
+  if (m->flags & PLANB_MULTI_NO_GRAPH)
+    return multi_pipeline(m, cur, d_addr_hi, d_addr_lo, d_table, n, d_out, st);
   bool same = m->exec && m->g_hi == d_addr_hi && m->g_lo == d_addr_lo && m->g_tid == d_table &&
               m->g_out == d_out && m->g_n == n;
   for (uint32_t t = 0; same && t < m->T; t++) same = m->snap[t] == cur[t];
   if (!same) {
     // a table was swapped by an update, or the buffers changed: capture the pipeline again
     if (m->exec) {
-      if (cudaStreamSynchronize(st) != cudaSuccess) return PLANB_ECUDA;
+      const cudaError_t es = cudaStreamSynchronize(st);
+      if (es != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: wait for previous graph", es);
       cudaGraphExecDestroy(m->exec);
       m->exec = nullptr;
     }
-    if (cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-      return PLANB_ECUDA;
-    int rc = planb::launch_bucketing(d_addr_hi, d_addr_lo, d_table, n, m->T, m->G, m->counts,
-                                     m->range, m->bhi, m->blo, m->perm, m->cap_stream);
-    for (uint32_t t = 0; rc == PLANB_OK && t < m->T; t++)
-      rc = planb::launch_lookup(cur[t]->dt, cur[t]->cfg, m->bhi, m->blo, n, d_out,
-                                m->fibs[t]->d_status, m->cap_stream, m->range + t, m->perm);
-    if (rc == PLANB_OK) rc = planb::launch_invalid_fill(m->range, m->T, m->perm, d_out, m->cap_stream);
+    cudaGetLastError();   // start the capture with no stale launch error
+    const cudaError_t eb = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (eb != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: begin capture", eb);
+    const int rc = multi_pipeline(m, cur, d_addr_hi, d_addr_lo, d_table, n, d_out, m->cap_stream);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(m->cap_stream, &graph);
     if (rc != PLANB_OK || ec != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
-      return rc != PLANB_OK ? rc : PLANB_ECUDA;
+      return rc != PLANB_OK ? rc : fail_detail(PLANB_ECUDA, "multi: end capture", ec);
     }
     const cudaError_t ei = cudaGraphInstantiate(&m->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) {
       m->exec = nullptr;
-      return PLANB_ECUDA;
+      return fail_detail(PLANB_ECUDA, "multi: instantiate graph", ei);
     }
     m->g_hi = d_addr_hi;
     m->g_lo = d_addr_lo;
@@ -836,7 +884,9 @@ int planb_multi_lookup(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t
     m->g_n = n;
     m->snap = cur;
   }
-  return cudaGraphLaunch(m->exec, st) == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+  const cudaError_t eg = cudaGraphLaunch(m->exec, st);
+  if (eg != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: graph launch", eg);
+  return PLANB_OK;
 }
 
 void planb_multi_destroy(planb_multi* m) {

@@ -470,6 +470,20 @@ KernelFn kernel_for(const DevTable& t, bool multi = false) {
 
 }  // namespace
 
+int kernel_attributes(const DevTable& t, bool multi, int* out) {
+  KernelFn fn = kernel_for(t, multi);
+  if (!fn) return PLANB_EINVAL;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(fn)) != cudaSuccess) return PLANB_ECUDA;
+  out[0] = a.numRegs;
+  out[1] = a.maxThreadsPerBlock;
+  out[2] = a.maxDynamicSharedSizeBytes;
+  out[3] = static_cast<int>(a.localSizeBytes);
+  out[4] = static_cast<int>(a.sharedSizeBytes);
+  out[5] = static_cast<int>(a.constSizeBytes);
+  return PLANB_OK;
+}
+
 size_t smem_bytes_for(const Layout& L, uint32_t format, uint32_t levels) {
   (void)format;
   if (levels == 0) return 0;
@@ -493,15 +507,19 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
     cfg.smem_bytes = 0;
   else
     cfg.smem_bytes = static_cast<size_t>(t.smem_nodes) * 128u;
-  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(fn),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(cfg.smem_bytes)) != cudaSuccess)
+  // The dynamic shared-memory limit is a property of the kernel function, which tables of other
+  // sizes share: raise it once to the device's opt-in maximum rather than to this table's need
+  // (a later, smaller table would otherwise lower it under an earlier one).
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
     return PLANB_ECUDA;
-  if (KernelFn fm = (t.kernel == kHybrid) ? kernel_for(t, true) : nullptr)
-    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(fm),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(cfg.smem_bytes)) != cudaSuccess)
+  if (cfg.smem_bytes > static_cast<size_t>(optin)) return PLANB_EINVAL;
+  for (KernelFn f : {fn, (t.kernel == kHybrid) ? kernel_for(t, true) : nullptr}) {
+    if (!f) continue;
+    if (cudaFuncSetAttribute(reinterpret_cast<const void*>(f),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
       return PLANB_ECUDA;
+  }
   int sms = 0, per_sm = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
     return PLANB_ECUDA;

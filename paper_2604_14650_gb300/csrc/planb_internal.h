@@ -173,6 +173,11 @@ int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* 
 int launch_invalid_fill(const uint64_t* d_range, uint32_t T, const uint32_t* d_perm,
                         uint16_t* d_out, void* stream);
 
+// cudaFuncGetAttributes of the lookup kernel a table uses (multi: its multi-table form):
+// out[0..5] = registers, max threads per block, max dynamic shared bytes, local bytes, static shared
+// bytes, constant bytes.
+int kernel_attributes(const DevTable& t, bool multi, int* out);
+
 // Occupancy-derived launch configuration for a table on a device.
 int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, LaunchCfg& cfg);
 

@@ -221,3 +221,18 @@ def test_shared_high_halves(variant):
     xl = np.concatenate([bl, xl, np.array(el, np.uint64)])
     with make(g, variant) as fib:
         assert np.array_equal(gpu_lookup(fib, xh, xl), expected(g, xh, xl))
+
+
+def test_tables_sharing_a_kernel_with_different_shared_memory():
+    """Two live tables that use the same kernel instantiation but need different amounts of shared
+    memory (the whole key index of each sits in shared memory), the larger built first: lookups on
+    both stay correct (the kernel's shared-memory limit must not follow the last table built)."""
+    big = synth.gen_fib(5000, seed=401, nh_max=4095)
+    small = synth.gen_fib(1500, seed=402, nh_max=4095)
+    with pb.Fib(big.hi, big.lo, big.len, big.nh) as fb, \
+            pb.Fib(small.hi, small.lo, small.len, small.nh) as fs:
+        assert fb.stats()["smem_levels"] == fb.stats()["depth"]       # index holds every key
+        assert fb.stats()["smem_bytes"] > 48 * 1024 > fs.stats()["smem_bytes"]
+        for f, fib in ((big, fb), (small, fs)):
+            xh, xl = synth.gen_trace(f, 100_000, seed=403)
+            assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl))

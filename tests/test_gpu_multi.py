@@ -52,8 +52,9 @@ def expected(fibs, tid, xh, xl):
     return want
 
 
+@pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("kinds", [("f8x128", "hybrid"), ("f8v7", "hybrid"), ("mixed", None)])
-def test_multi_table_parity_and_replay(kinds):
+def test_multi_table_parity_and_replay(kinds, graph):
     sizes = [500, 3000, 20_000, 1000, 60_000, 7, 12_000, 2500]
     fibs_in, tid, xh, xl = workload(sizes, 600_000, seed=41)
     want = expected(fibs_in, tid, xh, xl)
@@ -63,7 +64,7 @@ def test_multi_table_parity_and_replay(kinds):
     for t, f in enumerate(fibs_in):
         fmt, ker = kinds if kinds[0] != "mixed" else choices[t % len(choices)]
         fibs.append(pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=ker))
-    with pb.MultiFib(fibs, max_batch=1 << 20) as mt:
+    with pb.MultiFib(fibs, max_batch=1 << 20, graph=graph) as mt:
         dh, dl, dt = dev(xh), dev(xl), dev(tid, np.uint8)
         out = torch.empty(tid.size, dtype=torch.int16, device="cuda")
         for _ in range(3):                     # first call captures the graph, the others replay
