@@ -332,6 +332,37 @@ int planb_debug_inject(int point);
  */
 int planb_debug_kernel_info(const planb_fib *fib, int multi, int *out6);
 
+/*
+ * planb_lookup_host_noalloc — the lookup of planb_lookup_host for callers that must not allocate
+ * device memory. The paper has no counterpart.
+ *
+ * Who needs it: a packet-forwarding thread (the data plane that hands bursts of destination
+ * addresses to the lookup) cannot call cudaMalloc, because an allocation can block for a long time
+ * (it may synchronise the device and takes the driver's allocator locks) while packets queue up
+ * behind it; the same holds for a process whose device memory is already handed out by another
+ * allocator's pool (a framework's caching allocator), where a private cudaMalloc can fail or
+ * fragment that pool. planb_lookup_host would allocate its staging buffers on first use.
+ *
+ * How: addresses and results are staged through one fixed array of PLANB_NOALLOC_MAX_KEYS x 18
+ * bytes (4.5 MiB) declared in the library as a __device__ variable, so every GPU that loads the
+ * library holds it until the process exits. The call allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine. Its first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.
+ *   addr_hi, addr_lo: host arrays of n uint64_t; out: host array of n uint16_t. The call copies
+ *   them in, runs the lookup kernel and copies the results out on `stream`, and returns after the
+ *   stream has finished them (synchronous). Pinned host buffers copy fastest.
+ *   The array keeps the previous call's contents; nothing in it needs to start at zero, since each
+ *   call writes the n entries it reads. Calls from any thread share the one array, so two calls
+ *   that overlapped on the GPU would race on it: the library serialises them with a process-wide
+ *   lock held until the call's copies are done.
+ * Errors: PLANB_EINVAL (null pointer with n > 0, n > PLANB_NOALLOC_MAX_KEYS), PLANB_ECUDA.
+ */
+#define PLANB_NOALLOC_MAX_KEYS 262144
+int planb_lookup_host_noalloc(const planb_fib *fib, const uint64_t *addr_hi,
+                              const uint64_t *addr_lo, size_t n, uint16_t *out,
+                              planb_stream_t stream);
+
 /* planb_version — library version, (major << 16) | minor. */
 uint32_t planb_version(void);
 

@@ -902,3 +902,72 @@ void planb_multi_destroy(planb_multi* m) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ lookups without device allocation
+//
+// planb_lookup_host_noalloc stages addresses and results through one fixed device array declared
+// below instead of buffers from cudaMalloc. The array lives in every GPU context that loads this
+// library, for the life of the process. Its device address comes from cudaGetSymbolAddress, taken
+// once per device on the first call with that device current (the array's name in host code is
+// only a host-side stand-in). Calls share the array, so a process-wide lock serialises them, and
+// each call waits for its own copies before it returns and releases the lock.
+namespace {
+
+constexpr size_t kNoAllocMaxKeys = PLANB_NOALLOC_MAX_KEYS;
+constexpr size_t kNoAllocBytes = kNoAllocMaxKeys * (8 + 8 + 2);  // hi, lo, next hop: 4.5 MiB
+
+__device__ __align__(256) unsigned char g_noalloc_stage[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};  // device address of g_noalloc_stage per device ordinal
+
+// with g_noalloc_mu held and `dev` current
+int noalloc_stage(int dev, void** out) {
+  if (dev < 0 || dev >= 256) return PLANB_EINVAL;
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_stage) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return PLANB_ECUDA;
+    }
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return PLANB_OK;
+}
+
+}  // namespace
+
+extern "C" int planb_lookup_host_noalloc(const planb_fib* fib_c, const uint64_t* addr_hi,
+                                         const uint64_t* addr_lo, size_t n, uint16_t* out,
+                                         planb_stream_t stream) {
+  if (!fib_c) return PLANB_EINVAL;
+  if (n == 0) return PLANB_OK;
+  if (!addr_hi || !addr_lo || !out) return PLANB_EINVAL;
+  if (n > kNoAllocMaxKeys) return PLANB_EINVAL;
+  planb_fib* f = const_cast<planb_fib*>(fib_c);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  DeviceGuard g(f->device);
+  if (!g.ok) return PLANB_ECUDA;
+  void* stage = nullptr;
+  int rc = noalloc_stage(f->device, &stage);
+  if (rc) return rc;
+  std::shared_ptr<Table> t;
+  {
+    std::lock_guard<std::mutex> lk2(f->cur_mu);
+    t = f->cur;
+    note_stream(f, reinterpret_cast<cudaStream_t>(stream));
+  }
+  uint64_t* dh = static_cast<uint64_t*>(stage);
+  uint64_t* dl = dh + kNoAllocMaxKeys;
+  uint16_t* dout = reinterpret_cast<uint16_t*>(dl + kNoAllocMaxKeys);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(dh, addr_hi, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dl, addr_lo, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return PLANB_ECUDA;
+  rc = planb::launch_lookup(t->dt, t->cfg, dh, dl, n, dout, f->d_status, stream);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(out, dout, n * 2, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return PLANB_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
