@@ -178,14 +178,19 @@ def recorded_traffic(kernel: str):
 
 # ----------------------------------------------------------------------------- workload
 
+def rank_shard(fib, n, seed, rank, traffic="uniform"):
+    """Rank r looks up draws r*n .. (r+1)*n - 1 of one seeded trace stream (weak scaling: every rank
+    has its own n addresses; the table is replicated)."""
+    import synth
+    if traffic == "zipf":
+        return synth.gen_trace_zipf(fib, n, seed=seed + 1 + rank)
+    return synth.gen_trace(fib, n, seed=seed + 1, start=rank * n)
+
+
 def workload(args, rank):
     import synth
     fib = synth.gen_fib(args.prefixes, seed=args.seed, nh_max=255 if args.prefixes <= 1000 else 4095)
-    n = args.lookups
-    if args.traffic == "zipf":
-        xh, xl = synth.gen_trace_zipf(fib, n, seed=args.seed + 1 + rank)
-    else:
-        xh, xl = synth.gen_trace(fib, n, seed=args.seed + 1, start=rank * n)
+    xh, xl = rank_shard(fib, args.lookups, args.seed, rank, args.traffic)
     return fib, xh, xl
 
 
