@@ -55,12 +55,19 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="backbone",
-                    choices=["backbone", "vrf64", "learned1m", "small"],
+                    choices=["backbone", "vrf64", "learned1m", "small", "serve", "build"],
                     help="backbone: 200k prefixes, 2^28 lookups (the headline); vrf64: 64 VRF "
                          "tables of 1k-300k prefixes, 2^27 tagged lookups, one graph per batch; "
                          "learned1m: 1M prefixes, 2^28 lookups, learned vs plain tree; small: "
-                         "1k prefixes, 10^6 lookups")
+                         "1k prefixes, 10^6 lookups; serve: the serving engine under Poisson "
+                         "arrivals and route updates; build: build and rebuild times, host "
+                         "builder against the device builder")
+    ap.add_argument("--builder", default="host", choices=["host", "device"],
+                    help="where tables are built (and rebuilt by updates) in serve")
     ap.add_argument("--tables", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=20000.0, help="serve: requests per second")
+    ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
+    ap.add_argument("--update-rate", type=float, default=1000.0, help="serve: route changes/s")
     ap.add_argument("--no-tune", action="store_true")
     return ap.parse_args()
 
@@ -605,6 +612,147 @@ def run_learned1m(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: Poisson arrivals of requests (32..65,536 addresses, log-uniform) over the 64 VRF
+    tables (table drawn proportional to size), route updates at --update-rate changes per second
+    applied while serving, latency from submit to results in place."""
+    import threading
+    import torch
+    import paper_2604_14650_gb300 as pb
+    import synth
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(args.seed)
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(3e5), args.tables)).astype(int)
+    fibs_in = [synth.gen_fib(int(sz), seed=args.seed + 1000 + t, nh_max=4095)
+               for t, sz in enumerate(sizes)]
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, builder=args.builder) for f in fibs_in]
+    pool = 1 << 17
+    pools = [synth.gen_trace(f, pool, seed=args.seed + 3000 + t) for t, f in enumerate(fibs_in)]
+    nreq = int(args.rate * args.duration)
+    p = sizes / sizes.sum()
+    tabs = rng.choice(args.tables, size=nreq, p=p)
+    lens = np.exp(rng.uniform(np.log(32), np.log(65536), nreq)).astype(int)
+    offs = rng.integers(0, pool - 65536, nreq)
+    gaps = rng.exponential(1.0 / args.rate, nreq)
+    out_pool = np.empty(1 << 26, np.uint16)
+    budget = int(sum(f.stats()["node_bytes"] + f.stats()["value_bytes"] for f in fibs) * 1.05)
+    srv = pb.Server(slots=4, max_batch=1 << 18, mem_budget=budget)
+    for f in fibs:
+        srv.add_table(f)
+    tickets = []
+    done = threading.Event()
+
+    def updater():
+        per = 10                                  # changes per 10 ms
+        k = 0
+        while not done.is_set():
+            t = int(rng.integers(args.tables))
+            upd = synth.gen_updates(fibs_in[t], per, seed=args.seed + 9, start=k * per)
+            srv.update(t, *upd)
+            k += 1
+            time.sleep(per / args.update_rate)
+
+    ut = threading.Thread(target=updater)
+    ut.start()
+    t0 = time.perf_counter()
+    nxt = t0
+    pos = 0
+    for i in range(nreq):
+        nxt += gaps[i]
+        while time.perf_counter() < nxt:
+            pass
+        n = int(lens[i])
+        if pos + n > out_pool.size:
+            pos = 0
+        h, l = pools[tabs[i]]
+        o = int(offs[i])
+        tickets.append((srv.submit(int(tabs[i]), h[o:o + n], l[o:o + n],
+                                   out_pool[pos:pos + n]), i))
+        pos += n
+    deadline = t0 + args.duration + 60.0           # the run never waits more than a minute past
+    failed = 0
+    for tk, _ in tickets:
+        left = max(0.0, deadline - time.perf_counter())
+        try:
+            srv.wait(tk, int(left * 1e6))
+        except pb.PlanbError:
+            failed += 1
+            if time.perf_counter() >= deadline:
+                break
+    wall = time.perf_counter() - t0
+    done.set()
+    ut.join()
+    st = srv.stats()
+    srv.close()
+    line = {"metric": "serving: lookups/s and p50/p99 request latency, 64 VRF tables",
+            "value": st["lookups"] / wall / 1e9, "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "u64", "data": "synthetic (seeded)",
+            "config": {"workload": f"Poisson arrivals at {args.rate:.0f} requests/s for "
+                                   f"{args.duration:.1f} s, 32..65,536 addresses per request "
+                                   f"(log-uniform), {args.tables} VRF tables, route updates at "
+                                   f"{args.update_rate:.0f}/s", "slots": 4,
+                       "builder": args.builder,
+                       "max_batch": 1 << 18, "mem_budget_bytes": budget},
+            "latency_us": {"p50": st["p50_us"], "p99": st["p99_us"], "max": st["max_us"]},
+            "requests": st["requests"], "requests_per_s": st["requests"] / wall,
+            "batches": st["batches"], "mean_batch": st["mean_batch"],
+            "updates_applied": st["updates"], "rebuilds": st["update_batches"],
+            "rebuild_ms_mean": st["rebuild_ms_mean"], "last_error": st["last_error"],
+            "requests_not_completed": failed}
+    print(json.dumps(line), flush=True)
+    for f in fibs:
+        f.close()
+    return 0
+
+
+def run_build(args):
+    """Build and rebuild latency (Section 3.6 rebuild-and-swap; the paper quotes a full rebuild of
+    a 1M-prefix table): planb_build, then planb_update with 1,000-change batches, by the host
+    builder and by the device builder, on 200k- and 1M-prefix FIBs. Both builders' tables are
+    checked to be identical."""
+    import torch
+    import paper_2604_14650_gb300 as pb
+    import synth
+    torch.cuda.set_device(0)
+    res = {}
+    for n in (200_000, 1_000_000):
+        f = synth.gen_fib(n, seed=args.seed, nh_max=4095)
+        row = {}
+        images = {}
+        for builder in ("host", "device"):
+            walls = []
+            for rep in range(3):
+                t0 = time.perf_counter()
+                fib = pb.Fib(f.hi, f.lo, f.len, f.nh, builder=builder)
+                walls.append((time.perf_counter() - t0) * 1e3)
+                if rep < 2:
+                    fib.close()
+            rebuild = []
+            for k in range(max(3, args.steps)):
+                upd = synth.gen_updates(f, 1000, seed=args.seed + 7, start=k * 1000)
+                t0 = time.perf_counter()
+                fib.update(*upd)
+                rebuild.append((time.perf_counter() - t0) * 1e3)
+            images[builder] = fib.table_dump()
+            st = fib.stats()
+            row[builder] = {"build_ms_median": float(np.median(walls)),
+                            "rebuild_ms_median": float(np.median(rebuild)),
+                            "rebuild_ms_p90": float(np.percentile(rebuild, 90)),
+                            "stats_build_ms": st["build_ms"], "n_intervals": st["n_intervals"]}
+            fib.close()
+        row["identical_tables"] = bool(np.array_equal(images["host"], images["device"]))
+        res[str(n)] = row
+    v = res["1000000"]["device"]["rebuild_ms_median"]
+    print(json.dumps({"metric": "rebuild latency, 1M-prefix FIB, 1,000-change batch",
+                      "value": v, "unit": "ms", "n_gpus": 1, "steps": max(3, args.steps),
+                      "warmup": 0, "higher_is_better": False, "dtype": "u64",
+                      "data": "synthetic (seeded)",
+                      "config": {"workload": "planb_build and planb_update (1,000 changes, half "
+                                             "withdraws) on 200k- and 1M-prefix FIBs"},
+                      "builders": res}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -613,6 +761,10 @@ def main():
         return run_vrf64(args)
     if args.workload == "learned1m":
         return run_learned1m(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    if args.workload == "build":
+        return run_build(args)
     if args.workload == "small":
         args.prefixes, args.lookups = 1000, 1_000_000
     return run_planb(args)

@@ -74,6 +74,17 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
  * has no learned component; this follows the learned-index idea on top of its tree. */
 #define PLANB_KERNEL_LEARNED 4
 
+/* Builders (planb_opts.builder). Both give the same table, word for word.
+ * host: the prefix sort and Algorithm 2's stack sweep run on the host (Section 3.6), then the
+ *   layout is filled on the host and uploaded.
+ * device: every build step runs on the GPU: radix sorts of the prefixes and of the range-end
+ *   events, the stack sweep replaced by a bracket-matching scan (nesting depth by a prefix sum,
+ *   then for every event the latest start at the same depth), and the node arrays, index and
+ *   next hops written in place by closed-form kernels. Device scratch is about 120 bytes per
+ *   prefix during the build. Rebuilds by planb_update use the same builder. */
+#define PLANB_BUILDER_HOST 0
+#define PLANB_BUILDER_DEVICE 1
+
 typedef struct planb_fib planb_fib; /* opaque; owns all host and device memory of one table */
 
 typedef struct {
@@ -90,7 +101,8 @@ typedef struct {
     int32_t kernel;         /* PLANB_KERNEL_*; default PLANB_KERNEL_AUTO                          */
     int32_t model_leaves;   /* learned: leaf models L; 0 = automatic                              */
     int32_t model_iters;    /* learned: Adam steps of the root's training; -1 = default (2000)    */
-    int32_t reserved[5];    /* zero                                                              */
+    int32_t builder;        /* PLANB_BUILDER_*: where the build steps run; default host          */
+    int32_t reserved[4];    /* zero                                                              */
 } planb_opts;
 
 /* Fills *o with the defaults. */
@@ -112,8 +124,10 @@ typedef struct {
     uint64_t value_bytes;      /* bytes of the next-hop array on the device                      */
     uint64_t version;          /* table generation: 1 after build, +1 per applied update         */
     uint64_t withdraw_absent;  /* withdraws of prefixes that were not in the table (no-ops)       */
-    double build_ms;           /* host time of the last build (canonicalise .. layout)           */
-    double upload_ms;          /* host time to allocate and upload the last table                */
+    double build_ms;           /* wall time of the last build: host builder, canonicalise ..
+                                  layout on the host; device builder, every step incl. the fill */
+    double upload_ms;          /* host builder: time to allocate and upload the last table;
+                                  device builder: 0 (the fill is part of build_ms)               */
     uint32_t kernel;           /* PLANB_KERNEL_* in use (never AUTO)                             */
     uint32_t threads;          /* threads per CTA of the lookup kernel                           */
     uint32_t ctas;             /* persistent grid size (CTAs)                                    */
@@ -121,7 +135,7 @@ typedef struct {
     uint32_t model_leaves;     /* learned: leaf models (0 for the other kernels)                 */
     uint32_t model_iters;      /* learned: Adam steps run                                        */
     uint32_t model_max_err;    /* learned: largest per-leaf bound, in ranks                      */
-    uint32_t reserved0;
+    uint32_t builder;          /* PLANB_BUILDER_* that made the current table                    */
     double model_loss0;        /* learned: root's mean squared CDF error before training         */
     double model_loss;         /* learned: ... and after                                         */
     double model_covered;      /* learned: share of keys in leaves within the window limit       */
@@ -195,6 +209,16 @@ typedef struct {
 int planb_update(planb_fib *fib, const planb_route *inserts, size_t n_ins,
                  const planb_prefix *withdraws, size_t n_wd, planb_stream_t stream);
 
+/*
+ * planb_forget_stream — the fib fences table retirement (planb_update) on every stream its
+ * lookups have used, so such a stream must stay valid while it is remembered. Before destroying a
+ * stream that was used with this fib (planb_lookup, planb_update, or a planb_multi_lookup over
+ * it), call this: it waits for the stream's queued work and removes the stream from the set. The
+ * paper has no counterpart (it frees the old table after its readers finish, Section 3.6).
+ * Errors: PLANB_EINVAL (null fib), PLANB_ECUDA.
+ */
+int planb_forget_stream(planb_fib *fib, planb_stream_t stream);
+
 /* planb_stats — copies the table's statistics into *out. Errors: PLANB_EINVAL. */
 int planb_stats(const planb_fib *fib, planb_stats_t *out);
 
@@ -248,8 +272,98 @@ int planb_multi_create(planb_fib *const *fibs, uint32_t n_tables, size_t max_bat
 int planb_multi_lookup(planb_multi *m, const uint64_t *d_addr_hi, const uint64_t *d_addr_lo,
                        const uint8_t *d_table, size_t n, uint16_t *d_out, planb_stream_t stream);
 
+/*
+ * planb_multi_lookup_devn — planb_multi_lookup with the batch size read from device memory
+ * (*d_n, a uint64_t written before the work runs, at most max_n <= max_batch): the captured graph
+ * depends on the buffers and max_n only, so batches of any size replay it without a new capture
+ * (a serving loop's slots do this). Errors as planb_multi_lookup.
+ */
+int planb_multi_lookup_devn(planb_multi *m, const uint64_t *d_addr_hi, const uint64_t *d_addr_lo,
+                            const uint8_t *d_table, const uint64_t *d_n, size_t max_n,
+                            uint16_t *d_out, planb_stream_t stream);
+
 /* planb_multi_destroy — waits for the device and frees the group (not its tables). */
 void planb_multi_destroy(planb_multi *m);
+
+/* ------------------------------------------------------------------------------ serving loop */
+
+typedef struct planb_server planb_server;
+
+typedef struct {
+    uint32_t struct_size;      /* sizeof(planb_server_opts)                                      */
+    uint32_t slots;            /* batches in flight at once, each on its own stream; default 4    */
+    uint32_t max_batch;        /* addresses per device batch; default 262,144                     */
+    uint32_t max_request;      /* addresses per request (<= max_batch); default 65,536            */
+    uint64_t mem_budget;       /* device bytes the admitted tables may hold; 0 = no limit         */
+    uint32_t update_period_us; /* how often queued route changes are applied; default 10,000      */
+    int32_t device;            /* CUDA device; -1 = current                                       */
+    uint32_t reserved[6];
+} planb_server_opts;
+
+typedef struct {
+    uint64_t requests, lookups, batches;  /* completed since start (or the last reset)          */
+    uint64_t updates, update_batches;     /* route changes applied, rebuilds run                 */
+    uint64_t tables, table_bytes, queued; /* admitted tables, their device bytes, queue depth    */
+    double p50_us, p99_us, max_us;        /* request latency, submit to results in place         */
+    double mean_batch;                    /* addresses per device batch                          */
+    double rebuild_ms_mean;               /* mean time of one table's rebuild-and-swap           */
+    int32_t last_error;                   /* last failure code inside the engine (0 = none)      */
+    int32_t reserved;
+} planb_server_stats_t;
+
+void planb_server_opts_default(planb_server_opts *o);
+
+/*
+ * planb_server_create — a serving engine: continuous batching of lookup requests over a set of
+ * tables (the paper's data plane batches NIC bursts, Section 3.4, and applies route changes by
+ * rebuild-and-swap, Section 3.6). Requests queue up; a dispatcher thread packs whatever is queued
+ * into the next free slot (pinned staging + device buffers of max_batch addresses on its own
+ * stream), so requests arriving while others run join the next batch, and the slots' copies and
+ * lookups overlap on the device. A slot runs one multi-table pipeline (planb_multi_lookup_devn) per
+ * batch. An updater thread applies queued route changes every update period; batches formed after
+ * a table's swap see the new table. Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ENODEV, PLANB_ECUDA.
+ */
+int planb_server_create(const planb_server_opts *opts, planb_server **out);
+
+/*
+ * planb_server_add_table — admits a built table (same device) if the tables' device bytes stay
+ * within mem_budget; *table_id receives its id (0, 1, ...). Not owned: it must outlive the server.
+ * Errors: PLANB_EINVAL (255 tables already, other device), PLANB_ENOMEM (over the budget: not
+ * admitted).
+ */
+int planb_server_add_table(planb_server *s, planb_fib *fib, uint32_t *table_id);
+
+/*
+ * planb_server_submit — queues a request: the next hops of n (1..max_request) addresses in table
+ * table_id. addr_hi, addr_lo, out: host arrays that must stay valid until planb_server_wait reports
+ * the request done. Returns at once; *ticket identifies the request.
+ * Errors: PLANB_EINVAL, PLANB_ENOMEM.
+ */
+int planb_server_submit(planb_server *s, uint32_t table_id, const uint64_t *addr_hi,
+                        const uint64_t *addr_lo, size_t n, uint16_t *out, uint64_t *ticket);
+
+/*
+ * planb_server_wait — waits up to timeout_us for a request; returns PLANB_OK when its results are
+ * in place (the ticket is then released), PLANB_ETIMEOUT if still running, else the failure code.
+ */
+int planb_server_wait(planb_server *s, uint64_t ticket, uint32_t timeout_us);
+
+/*
+ * planb_server_update — queues route changes for a table (applied by the updater thread at the
+ * next update period, all changes queued for the table in one rebuild). Errors: PLANB_EINVAL.
+ */
+int planb_server_update(planb_server *s, uint32_t table_id, const planb_route *inserts,
+                        size_t n_ins, const planb_prefix *withdraws, size_t n_wd);
+
+/* planb_server_stats — counters and latency percentiles (over the last 2^20 requests). */
+int planb_server_stats(planb_server *s, planb_server_stats_t *out);
+
+/* planb_server_reset_stats — zeroes the counters and the latency record. */
+void planb_server_reset_stats(planb_server *s);
+
+/* planb_server_destroy — stops the threads, finishes the batches in flight and frees the engine
+ * (not its tables); requests still queued fail with PLANB_EINVAL. */
+void planb_server_destroy(planb_server *s);
 
 /* ------------------------------------------------------ learned-model kernels (for checking) */
 
@@ -274,7 +388,8 @@ int planb_mlp_forward(const float *d_u, size_t n, const float *w, float *d_y,
                       planb_stream_t stream);
 
 /* ------------------------------------------------------------------ host-only entry points */
-/* These run on the host alone and need no GPU; they expose the build steps for inspection.  */
+/* These run on the host alone and need no GPU (except planb_intervals_device, the device
+ * builder's counterpart of planb_intervals); they expose the build steps for inspection.     */
 
 /*
  * planb_intervals — the elementary intervals of a prefix table (Section 3.1; Algorithm 2's event
@@ -287,6 +402,18 @@ int planb_mlp_forward(const float *d_u, size_t n, const float *w, float *d_y,
 int planb_intervals(const uint64_t *prefix_hi, const uint64_t *prefix_lo, const uint8_t *len,
                     const uint16_t *nexthop, size_t n, int merge_equal_nh, uint64_t *out_start_hi,
                     uint64_t *out_start_lo, uint16_t *out_nh, size_t cap, size_t *out_m);
+
+/*
+ * planb_intervals_device — planb_intervals computed by the device builder (PLANB_BUILDER_DEVICE:
+ * GPU radix sorts and the bracket-matching scan that replaces Algorithm 2's stack) on the current
+ * device; same arguments, same results. Host arrays in and out; device scratch is allocated and
+ * freed inside the call. Errors: as planb_intervals, plus PLANB_ENODEV (no sm_103 device current),
+ * PLANB_ENOMEM (device scratch), PLANB_ECUDA.
+ */
+int planb_intervals_device(const uint64_t *prefix_hi, const uint64_t *prefix_lo,
+                           const uint8_t *len, const uint16_t *nexthop, size_t n,
+                           int merge_equal_nh, uint64_t *out_start_hi, uint64_t *out_start_lo,
+                           uint16_t *out_nh, size_t cap, size_t *out_m);
 
 typedef struct {
     uint32_t keys_per_node;  /* k */
@@ -323,6 +450,16 @@ uint64_t planb_child_index(uint32_t keys_per_node, uint32_t d, uint64_t j, uint3
  * Errors: PLANB_EINVAL for another point.
  */
 int planb_debug_inject(int point);
+
+/*
+ * planb_debug_table_dump — test hook (the paper has no counterpart): copies the current table's
+ * device image to host memory `dst`: the node array(s) (F16HI: the high halves, then the low
+ * halves), the top-of-tree index of the hybrid and learned kernels (16 bytes per entry, zero-padded
+ * to 128 bytes) and the m next hops (u16). *out_bytes receives its size; with cap smaller (or dst
+ * NULL) nothing is copied and PLANB_EINVAL is returned. Tables made by the two builders from the
+ * same prefixes and options have identical images. Errors: PLANB_EINVAL, PLANB_ECUDA.
+ */
+int planb_debug_table_dump(const planb_fib *fib, void *dst, size_t cap, size_t *out_bytes);
 
 /*
  * planb_debug_kernel_info — test hook (the paper has no counterpart): the CUDA function attributes

@@ -21,6 +21,7 @@ PLANB_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EDEVICE", -5: "ENODEV", -6: "ETIMEOUT"}
 FORMATS = {"f8x128": 0, "f16hi": 1, "f8v7": 2}
 KERNELS = {"auto": 0, "coop": 1, "hybrid": 2, "flat": 3, "learned": 4}
+BUILDERS = {"host": 0, "device": 1}
 
 
 class PlanbError(RuntimeError):
@@ -39,7 +40,7 @@ class Opts(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("format", C.c_int32), ("merge_equal_nh", C.c_int32),
                 ("smem_levels", C.c_int32), ("device", C.c_int32), ("block_threads", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("kernel", C.c_int32), ("model_leaves", C.c_int32),
-                ("model_iters", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("model_iters", C.c_int32), ("builder", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class Stats(C.Structure):
@@ -52,7 +53,7 @@ class Stats(C.Structure):
                 ("upload_ms", C.c_double), ("kernel", C.c_uint32), ("threads", C.c_uint32),
                 ("ctas", C.c_uint32), ("smem_bytes", C.c_uint32), ("model_leaves", C.c_uint32),
                 ("model_iters", C.c_uint32), ("model_max_err", C.c_uint32),
-                ("reserved0", C.c_uint32), ("model_loss0", C.c_double), ("model_loss", C.c_double),
+                ("builder", C.c_uint32), ("model_loss0", C.c_double), ("model_loss", C.c_double),
                 ("model_covered", C.c_double), ("model_mean_err", C.c_double),
                 ("model_train_ms", C.c_double)]
 
@@ -84,6 +85,7 @@ _SIGS = {
     "planb_lookup": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_lookup_host": (C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     "planb_update": (C.c_int, [_vp, _vp, _sz, _vp, _sz, _vp]),
+    "planb_forget_stream": (C.c_int, [_vp, _vp]),
     "planb_stats": (C.c_int, [_vp, _vp]),
     "planb_device_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
     "planb_destroy": (None, [_vp]),
@@ -93,11 +95,25 @@ _SIGS = {
     "planb_child_index": (C.c_uint64, [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32]),
     "planb_debug_inject": (C.c_int, [C.c_int]),
     "planb_debug_kernel_info": (C.c_int, [_vp, C.c_int, _vp]),
+    "planb_debug_table_dump": (C.c_int, [_vp, _vp, _sz, C.POINTER(_sz)]),
+    "planb_intervals_device": (C.c_int, [_vp, _vp, _vp, _vp, _sz, C.c_int, _vp, _vp, _vp, _sz,
+                                         C.POINTER(_sz)]),
     "planb_mlp_grad": (C.c_int, [_vp, _vp, _sz, _vp, _vp, C.POINTER(C.c_double), _vp]),
     "planb_mlp_forward": (C.c_int, [_vp, _sz, _vp, _vp, _vp]),
     "planb_multi_create": (C.c_int, [_vp, C.c_uint32, _sz, C.c_uint32, C.POINTER(_vp)]),
     "planb_multi_lookup": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_multi_destroy": (None, [_vp]),
+    "planb_multi_lookup_devn": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "planb_server_opts_default": (None, [_vp]),
+    "planb_server_create": (C.c_int, [_vp, C.POINTER(_vp)]),
+    "planb_server_add_table": (C.c_int, [_vp, _vp, C.POINTER(C.c_uint32)]),
+    "planb_server_submit": (C.c_int, [_vp, C.c_uint32, _vp, _vp, _sz, _vp,
+                                      C.POINTER(C.c_uint64)]),
+    "planb_server_wait": (C.c_int, [_vp, C.c_uint64, C.c_uint32]),
+    "planb_server_update": (C.c_int, [_vp, C.c_uint32, _vp, _sz, _vp, _sz]),
+    "planb_server_stats": (C.c_int, [_vp, _vp]),
+    "planb_server_reset_stats": (None, [_vp]),
+    "planb_server_destroy": (None, [_vp]),
 }
 
 
@@ -160,9 +176,12 @@ def version() -> int:
     return int(load().planb_version())
 
 
-def intervals(hi, lo, ln, nh, merge: bool = False, variant: str = "libplanb.so"):
-    """Elementary intervals of a prefix table (host only): (start_hi, start_lo, nh) arrays."""
+def intervals(hi, lo, ln, nh, merge: bool = False, variant: str = "libplanb.so",
+              device: bool = False):
+    """Elementary intervals of a prefix table: (start_hi, start_lo, nh) arrays. device=False runs
+    the host builder (no GPU needed), device=True the GPU builder on the current device."""
     lib = load(variant)
+    entry = lib.planb_intervals_device if device else lib.planb_intervals
     hi, lo, ln, nh = _np(hi, np.uint64), _np(lo, np.uint64), _np(ln, np.uint8), _np(nh, np.uint16)
     n = hi.size
     m = _sz(0)
@@ -170,8 +189,9 @@ def intervals(hi, lo, ln, nh, merge: bool = False, variant: str = "libplanb.so")
     sh = np.empty(cap, np.uint64)
     sl = np.empty(cap, np.uint64)
     snh = np.empty(cap, np.uint16)
-    _check(lib.planb_intervals(_ptr(hi), _ptr(lo), _ptr(ln), _ptr(nh), n, int(merge), _ptr(sh),
-                               _ptr(sl), _ptr(snh), cap, C.byref(m)), "planb_intervals")
+    _check(entry(_ptr(hi), _ptr(lo), _ptr(ln), _ptr(nh), n, int(merge), _ptr(sh), _ptr(sl),
+                 _ptr(snh), cap, C.byref(m)),
+           "planb_intervals_device" if device else "planb_intervals")
     k = m.value
     return sh[:k].copy(), sl[:k].copy(), snh[:k].copy()
 
@@ -226,7 +246,7 @@ class Fib:
     def __init__(self, hi, lo, ln, nh, *, format: str = "f8x128", merge: bool = False,
                  smem_levels: int = -1, device: int | None = None, block_threads: int = 0,
                  ctas_per_sm: int = 0, kernel: str = "auto", model_leaves: int = 0,
-                 model_iters: int = -1, variant: str = "libplanb.so"):
+                 model_iters: int = -1, builder: str = "host", variant: str = "libplanb.so"):
         self._lib = load(variant)
         self._h = None
         hi, lo, ln, nh = _np(hi, np.uint64), _np(lo, np.uint64), _np(ln, np.uint8), _np(nh, np.uint16)
@@ -243,6 +263,7 @@ class Fib:
         o.kernel = KERNELS[kernel]
         o.model_leaves = model_leaves
         o.model_iters = model_iters
+        o.builder = BUILDERS[builder]
         h = C.c_void_p()
         _check(self._lib.planb_build(_ptr(hi), _ptr(lo), _ptr(ln), _ptr(nh), hi.size, C.byref(o),
                                      C.byref(h)), "planb_build")
@@ -310,6 +331,20 @@ class Fib:
         a = (C.c_int * 6)()
         _check(self._lib.planb_debug_kernel_info(self._h, int(multi), a), "planb_debug_kernel_info")
         return dict(zip(("regs", "max_threads", "max_dyn_smem", "local", "static_smem", "const"), a))
+
+    def forget_stream(self, stream):
+        """Before destroying a stream used with this table: waits for it and stops fencing on it."""
+        _check(self._lib.planb_forget_stream(self._h, _stream_handle(stream)),
+               "planb_forget_stream")
+
+    def table_dump(self) -> np.ndarray:
+        """The current table's device image (node arrays, index, next hops) as bytes."""
+        nb = _sz(0)
+        self._lib.planb_debug_table_dump(self._h, None, 0, C.byref(nb))
+        buf = np.empty(nb.value, dtype=np.uint8)
+        _check(self._lib.planb_debug_table_dump(self._h, _ptr(buf), buf.size, C.byref(nb)),
+               "planb_debug_table_dump")
+        return buf
 
     def device_status(self):
         w = C.c_uint32(0)
@@ -383,6 +418,92 @@ class MultiFib:
     def close(self):
         if self._h:
             self._lib.planb_multi_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("slots", C.c_uint32), ("max_batch", C.c_uint32),
+                ("max_request", C.c_uint32), ("mem_budget", C.c_uint64),
+                ("update_period_us", C.c_uint32), ("device", C.c_int32),
+                ("reserved", C.c_uint32 * 6)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("requests", C.c_uint64), ("lookups", C.c_uint64), ("batches", C.c_uint64),
+                ("updates", C.c_uint64), ("update_batches", C.c_uint64), ("tables", C.c_uint64),
+                ("table_bytes", C.c_uint64), ("queued", C.c_uint64), ("p50_us", C.c_double),
+                ("p99_us", C.c_double), ("max_us", C.c_double), ("mean_batch", C.c_double),
+                ("rebuild_ms_mean", C.c_double), ("last_error", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class Server:
+    """The serving engine (planb_server): continuous batching of host-buffer requests over tables."""
+
+    def __init__(self, slots: int = 4, max_batch: int = 1 << 18, max_request: int = 1 << 16,
+                 mem_budget: int = 0, update_period_us: int = 10_000, device: int | None = None):
+        self._lib = load()
+        self._h = None
+        o = ServerOpts()
+        self._lib.planb_server_opts_default(C.byref(o))
+        o.slots, o.max_batch, o.max_request = slots, max_batch, max_request
+        o.mem_budget, o.update_period_us = mem_budget, update_period_us
+        o.device = -1 if device is None else device
+        h = C.c_void_p()
+        _check(self._lib.planb_server_create(C.byref(o), C.byref(h)), "planb_server_create")
+        self._h = h
+        self.tables = []
+
+    def add_table(self, fib: Fib) -> int:
+        tid = C.c_uint32()
+        _check(self._lib.planb_server_add_table(self._h, fib._h, C.byref(tid)),
+               "planb_server_add_table")
+        self.tables.append(fib)
+        return tid.value
+
+    def submit(self, table: int, hi: np.ndarray, lo: np.ndarray, out: np.ndarray) -> int:
+        """Queues a request; the arrays must stay alive until wait() returns for its ticket."""
+        t = C.c_uint64()
+        _check(self._lib.planb_server_submit(self._h, table, hi.ctypes.data, lo.ctypes.data,
+                                             hi.size, out.ctypes.data, C.byref(t)),
+               "planb_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = 60_000_000):
+        _check(self._lib.planb_server_wait(self._h, ticket, timeout_us), "planb_server_wait")
+
+    def update(self, table: int, ins_hi=(), ins_lo=(), ins_len=(), ins_nh=(), wd_hi=(), wd_lo=(),
+               wd_len=()):
+        ins = np.zeros(len(ins_hi), dtype=ROUTE_DTYPE)
+        ins["hi"], ins["lo"], ins["len"], ins["nexthop"] = ins_hi, ins_lo, ins_len, ins_nh
+        wd = np.zeros(len(wd_hi), dtype=PREFIX_DTYPE)
+        wd["hi"], wd["lo"], wd["len"] = wd_hi, wd_lo, wd_len
+        _check(self._lib.planb_server_update(self._h, table, _ptr(ins), ins.size, _ptr(wd),
+                                             wd.size), "planb_server_update")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(self._lib.planb_server_stats(self._h, C.byref(s)), "planb_server_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_ if f != "reserved"}
+
+    def reset_stats(self):
+        self._lib.planb_server_reset_stats(self._h)
+
+    def close(self):
+        if self._h:
+            self._lib.planb_server_destroy(self._h)
             self._h = None
 
     def __enter__(self):

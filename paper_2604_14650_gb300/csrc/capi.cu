@@ -49,6 +49,19 @@ struct DeviceGuard {
   }
 };
 
+// A non-blocking stream for the GPU builder; declared before the buffers ordered on it, so that it
+// outlives them.
+struct BuildStream {
+  cudaStream_t s = nullptr;
+  bool make() { return cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess; }
+  ~BuildStream() {
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  }
+};
+
 // One built, uploaded, immutable table.
 struct Table {
   int device = 0;
@@ -59,6 +72,8 @@ struct Table {
   planb::LaunchCfg cfg;
   uint64_t n_input = 0, n_prefixes = 0;
   double build_ms = 0, upload_ms = 0;
+  uint32_t builder = 0;       // PLANB_BUILDER_* that made it
+  size_t dump_bytes = 0;      // node array(s), index and next hops: the deterministic prefix of mem
   planb::LearnedBuild model;  // learned kernel only
   ~Table() {
     if (mem) {
@@ -131,24 +146,59 @@ uint32_t auto_index_levels(const planb::Layout& L, size_t budget) {
   return s;
 }
 
-// Builds and uploads a table from a canonical prefix list.
+// Builds and uploads a table from a canonical prefix list. With the device builder the intervals
+// and the node arrays are made on the GPU (gpu_builder.cu) from d_canon when it is given (the
+// same list, already on the device, ordered on bs) or from an upload of canon.
 int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const planb_opts& o,
-               int device, std::shared_ptr<Table>& out) {
+               int device, std::shared_ptr<Table>& out, BuildStream* bs = nullptr,
+               const planb::DevBuf* d_canon = nullptr) {
   auto t0 = std::chrono::steady_clock::now();
   if (g_inject.load() == 1) {
     g_inject.store(0);
     return PLANB_ENOMEM;
   }
-  planb::Intervals iv;
-  planb::sweep(canon, o.merge_equal_nh != 0, iv);
+  const bool on_dev = o.builder == PLANB_BUILDER_DEVICE;
+  DeviceGuard gd(device);      // current for the whole build (outlives the stream and buffers)
+  if (!gd.ok) return PLANB_ECUDA;
+  BuildStream own;
+  if (on_dev && !bs) {
+    bs = &own;
+    if (!own.make()) return fail_detail(PLANB_ECUDA, "build stream");
+  }
+  planb::DevBuf up;            // the canonical list, uploaded (after bs: freed on it first)
+  planb::GpuIntervals giv;     // device builder: the intervals
+  planb::Intervals iv;         // host builder (and the learned model): the intervals
+  uint64_t m = 0;
+  if (on_dev) {
+    void* st = bs->s;
+    const planb::Prefix* dc = d_canon ? d_canon->as<planb::Prefix>() : nullptr;
+    if (!dc) {
+      if (!up.alloc(canon.size() * sizeof(planb::Prefix), st)) return PLANB_ENOMEM;
+      if (!canon.empty() &&
+          cudaMemcpyAsync(up.p, canon.data(), canon.size() * sizeof(planb::Prefix),
+                          cudaMemcpyHostToDevice, bs->s) != cudaSuccess)
+        return fail_detail(PLANB_ECUDA, "builder upload");
+      dc = up.as<planb::Prefix>();
+    }
+    int rc = planb::gpu_sweep(dc, canon.size(), o.merge_equal_nh != 0, st, giv);
+    if (rc) return fail_detail(rc, "device interval sweep", cudaGetLastError());
+    m = giv.m;
+  } else {
+    planb::sweep(canon, o.merge_equal_nh != 0, iv);
+    m = iv.size();
+  }
   const uint32_t format = static_cast<uint32_t>(o.format);
   const uint32_t k = format == PLANB_FMT_F16HI ? 16 : 8;
   uint32_t kernel = static_cast<uint32_t>(o.kernel);
   if (format == PLANB_FMT_F16HI) kernel = planb::kCoop;
   else if (kernel == PLANB_KERNEL_AUTO) kernel = planb::kHybrid;
   const bool learned = kernel == planb::kLearned;
-  const uint64_t m = iv.size();
+  if (on_dev && learned) {  // the model is fitted from the host copy of the intervals
+    int rc = planb::gpu_download(giv, bs->s, iv);
+    if (rc) return rc;
+  }
   auto t = std::make_shared<Table>();
+  t->builder = on_dev ? PLANB_BUILDER_DEVICE : PLANB_BUILDER_HOST;
   t->device = device;
   t->n_input = n_input;
   t->n_prefixes = canon.size();
@@ -192,14 +242,17 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   const size_t val_bytes = ((static_cast<size_t>(m) * 2 + 255) / 256) * 256;
   const size_t model_bytes =
       learned ? ((static_cast<size_t>(model_leaves) * 18 + 255) / 256) * 256 : 0;
-  std::vector<uint64_t> host((node_bytes + lo_bytes + sidx_bytes) / 8);
-  if (format == PLANB_FMT_F16HI)
-    planb::fill_f16hi(iv, t->L, host.data(), host.data() + node_bytes / 8);
-  else if (format == PLANB_FMT_F8V7)
-    planb::fill_f8v7(iv, t->L, host.data());
-  else
-    planb::fill_f8x128(iv, t->L, host.data());
-  if (sidx_n) planb::fill_sidx(iv, t->L, s, host.data() + (node_bytes + lo_bytes) / 8);
+  std::vector<uint64_t> host;
+  if (!on_dev) {
+    host.resize((node_bytes + lo_bytes + sidx_bytes) / 8);
+    if (format == PLANB_FMT_F16HI)
+      planb::fill_f16hi(iv, t->L, host.data(), host.data() + node_bytes / 8);
+    else if (format == PLANB_FMT_F8V7)
+      planb::fill_f8v7(iv, t->L, host.data());
+    else
+      planb::fill_f8x128(iv, t->L, host.data());
+    if (sidx_n) planb::fill_sidx(iv, t->L, s, host.data() + (node_bytes + lo_bytes) / 8);
+  }
   t->build_ms = ms_since(t0);
 
   auto t1 = std::chrono::steady_clock::now();
@@ -229,9 +282,26 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   }
   char* base = static_cast<char*>(t->mem);
   const size_t head = node_bytes + lo_bytes + sidx_bytes;
-  if (cudaMemcpy(base, host.data(), head, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(base + head, iv.nh.data(), m * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+  t->dump_bytes = head + m * 2;
+  if (on_dev) {
+    // the index region's rounding tail is zero, as in the host-filled image
+    const size_t sidx_used = static_cast<size_t>(sidx_n) * 16;
+    if ((sidx_bytes > sidx_used &&
+         cudaMemsetAsync(base + node_bytes + lo_bytes + sidx_used, 0, sidx_bytes - sidx_used,
+                         bs->s) != cudaSuccess))
+      return PLANB_ECUDA;
+    rc = planb::gpu_fill(giv, t->L, format, s, sidx_n, base,
+                         lo_bytes ? reinterpret_cast<uint64_t*>(base + node_bytes) : nullptr,
+                         reinterpret_cast<uint64_t*>(base + node_bytes + lo_bytes),
+                         reinterpret_cast<uint16_t*>(base + head), bs->s);
+    if (rc) return fail_detail(rc, "device layout fill", cudaGetLastError());
+    if (cudaStreamSynchronize(bs->s) != cudaSuccess)
+      return fail_detail(PLANB_ECUDA, "device layout fill", cudaGetLastError());
+  } else if (cudaMemcpy(base, host.data(), head, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(base + head, iv.nh.data(), m * 2, cudaMemcpyHostToDevice) !=
+                 cudaSuccess) {
     return PLANB_ECUDA;
+  }
   if (learned) {
     char* mb = base + head + val_bytes;
     const size_t lb = static_cast<size_t>(model_leaves) * sizeof(planb::LeafModel);
@@ -262,6 +332,10 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   rc = planb::plan_launch(t->dt, device, o.block_threads, o.ctas_per_sm, t->cfg);
   if (rc) return rc;
   t->upload_ms = ms_since(t1);
+  if (on_dev) {  // one device build: intervals, layout and fill together
+    t->build_ms = ms_since(t0);
+    t->upload_ms = 0;
+  }
   out = std::move(t);
   return PLANB_OK;
 }
@@ -381,6 +455,7 @@ int planb_build(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint
   if (o.kernel < PLANB_KERNEL_AUTO || o.kernel > PLANB_KERNEL_LEARNED) return PLANB_EINVAL;
   if (o.format == PLANB_FMT_F16HI && o.kernel > PLANB_KERNEL_COOP) return PLANB_EINVAL;
   if (o.model_leaves < 0 || o.model_leaves > 8192 || o.model_iters < -1) return PLANB_EINVAL;
+  if (o.builder != PLANB_BUILDER_HOST && o.builder != PLANB_BUILDER_DEVICE) return PLANB_EINVAL;
   try {
     int dev = o.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return PLANB_ENODEV;
@@ -390,11 +465,28 @@ int planb_build(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint
     std::unique_ptr<planb_fib> f(new planb_fib());
     f->opts = o;
     f->device = dev;
-    rc = planb::canonicalise(prefix_hi, prefix_lo, len, nexthop, n, f->rib);
-    if (rc) return rc;
+    DeviceGuard gdev(dev);  // declared first: outlives the stream and buffers below
+    if (!gdev.ok) return PLANB_ECUDA;
+    BuildStream bs;
+    planb::DevBuf d_canon;  // device builder: the canonical list, made on the GPU
+    if (o.builder == PLANB_BUILDER_DEVICE) {
+      if (!bs.make()) return fail_detail(PLANB_ECUDA, "build stream");
+      uint64_t N = 0;
+      rc = planb::gpu_canonicalise(prefix_hi, prefix_lo, len, nexthop, n, bs.s, d_canon, N);
+      if (rc) return fail_detail(rc, "device canonicalise", cudaGetLastError());
+      f->rib.resize(N);
+      if (N && cudaMemcpyAsync(f->rib.data(), d_canon.p, N * sizeof(planb::Prefix),
+                               cudaMemcpyDeviceToHost, bs.s) != cudaSuccess)
+        return PLANB_ECUDA;
+      if (cudaStreamSynchronize(bs.s) != cudaSuccess) return PLANB_ECUDA;
+    } else {
+      rc = planb::canonicalise(prefix_hi, prefix_lo, len, nexthop, n, f->rib);
+      if (rc) return rc;
+    }
     double canon_ms = ms_since(t0);
     std::shared_ptr<Table> t;
-    rc = make_table(f->rib, n, o, dev, t);
+    rc = make_table(f->rib, n, o, dev, t, o.builder == PLANB_BUILDER_DEVICE ? &bs : nullptr,
+                    o.builder == PLANB_BUILDER_DEVICE ? &d_canon : nullptr);
     if (rc) return rc;
     t->build_ms += canon_ms;
     DeviceGuard g(dev);
@@ -570,6 +662,18 @@ int planb_update(planb_fib* f, const planb_route* inserts, size_t n_ins,
   }
 }
 
+int planb_forget_stream(planb_fib* f, planb_stream_t stream) {
+  if (!f) return PLANB_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  DeviceGuard g(f->device);
+  if (!g.ok) return PLANB_ECUDA;
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_detail(PLANB_ECUDA, "forget stream: synchronize", e);
+  std::lock_guard<std::mutex> lk(f->cur_mu);
+  f->streams.erase(std::remove(f->streams.begin(), f->streams.end(), s), f->streams.end());
+  return PLANB_OK;
+}
+
 int planb_stats(const planb_fib* fib_c, planb_stats_t* out) {
   if (!fib_c || !out) return PLANB_EINVAL;
   planb_fib* f = const_cast<planb_fib*>(fib_c);
@@ -596,6 +700,7 @@ int planb_stats(const planb_fib* fib_c, planb_stats_t* out) {
   out->withdraw_absent = f->withdraw_absent;
   out->build_ms = t->build_ms;
   out->upload_ms = t->upload_ms;
+  out->builder = t->builder;
   out->kernel = t->dt.kernel;
   out->threads = static_cast<uint32_t>(t->cfg.threads);
   out->ctas = static_cast<uint32_t>(t->cfg.blocks);
@@ -665,6 +770,58 @@ int planb_intervals(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const 
   } catch (const std::bad_alloc&) {
     return PLANB_ENOMEM;
   }
+}
+
+int planb_intervals_device(const uint64_t* prefix_hi, const uint64_t* prefix_lo,
+                           const uint8_t* len, const uint16_t* nexthop, size_t n,
+                           int merge_equal_nh, uint64_t* out_start_hi, uint64_t* out_start_lo,
+                           uint16_t* out_nh, size_t cap, size_t* out_m) {
+  if (!out_m) return PLANB_EINVAL;
+  try {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PLANB_ENODEV;
+    int rc = check_device(dev);
+    if (rc) return rc;
+    BuildStream bs;
+    if (!bs.make()) return PLANB_ECUDA;
+    planb::DevBuf d_canon;
+    planb::GpuIntervals giv;
+    uint64_t N = 0;
+    rc = planb::gpu_canonicalise(prefix_hi, prefix_lo, len, nexthop, n, bs.s, d_canon, N);
+    if (rc) return fail_detail(rc, "device canonicalise", cudaGetLastError());
+    rc = planb::gpu_sweep(d_canon.as<planb::Prefix>(), N, merge_equal_nh != 0, bs.s, giv);
+    if (rc) return fail_detail(rc, "device interval sweep", cudaGetLastError());
+    *out_m = giv.m;
+    if (cap < giv.m || !out_start_hi || !out_start_lo || !out_nh) return PLANB_EINVAL;
+    if (giv.m &&
+        (cudaMemcpyAsync(out_start_hi, giv.hi.p, giv.m * 8, cudaMemcpyDeviceToHost, bs.s) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(out_start_lo, giv.lo.p, giv.m * 8, cudaMemcpyDeviceToHost, bs.s) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(out_nh, giv.nh.p, giv.m * 2, cudaMemcpyDeviceToHost, bs.s) !=
+             cudaSuccess))
+      return PLANB_ECUDA;
+    return cudaStreamSynchronize(bs.s) == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+  } catch (const std::bad_alloc&) {
+    return PLANB_ENOMEM;
+  }
+}
+
+int planb_debug_table_dump(const planb_fib* fib_c, void* dst, size_t cap, size_t* out_bytes) {
+  if (!fib_c || !out_bytes) return PLANB_EINVAL;
+  planb_fib* f = const_cast<planb_fib*>(fib_c);
+  std::shared_ptr<Table> t;
+  {
+    std::lock_guard<std::mutex> lk(f->cur_mu);
+    t = f->cur;
+  }
+  *out_bytes = t->dump_bytes;
+  if (!dst || cap < t->dump_bytes) return PLANB_EINVAL;
+  DeviceGuard g(t->device);
+  if (!g.ok) return PLANB_ECUDA;
+  return cudaMemcpy(dst, t->mem, t->dump_bytes, cudaMemcpyDeviceToHost) == cudaSuccess
+             ? PLANB_OK
+             : PLANB_ECUDA;
 }
 
 int planb_layout_info(uint32_t keys_per_node, uint64_t n_keys, uint32_t depth_override,
@@ -742,10 +899,15 @@ struct planb_multi {
   uint32_t G = 0;                // bucketing chunks
   void* mem = nullptr;
   uint64_t *bhi = nullptr, *blo = nullptr, *range = nullptr;
-  uint32_t *perm = nullptr, *counts = nullptr;
+  uint32_t *where = nullptr, *counts = nullptr;
+  uint16_t* bres = nullptr;      // results in bucketed order
   cudaStream_t cap_stream = nullptr;
+  static constexpr int kBranches = 4;          // per-table lookups run on this many streams
+  cudaStream_t side[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
   cudaGraphExec_t exec = nullptr;
-  const void *g_hi = nullptr, *g_lo = nullptr, *g_tid = nullptr, *g_out = nullptr;
+  const void *g_hi = nullptr, *g_lo = nullptr, *g_tid = nullptr, *g_out = nullptr,
+             *g_dn = nullptr;
   size_t g_n = 0;
   std::vector<std::shared_ptr<Table>> snap;  // the tables the captured graph reads
   std::mutex mu;
@@ -754,20 +916,37 @@ struct planb_multi {
 
 namespace {
 
-// the multi-table pipeline on one stream: bucketing, one lookup per table, invalid-id fill
+// The multi-table pipeline on stream s: bucketing; the per-table lookups, which read and write
+// disjoint segments; the gather. When captured (fork), the lookups are forked over the side
+// streams and joined back on s: parallel branches of the graph, so one table's tail overlaps the
+// next table's start, while the graph still runs on s alone. Direct launches stay on s (a table
+// swap between forked launches would fence only s).
 int multi_pipeline(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cur,
                    const uint64_t* d_addr_hi, const uint64_t* d_addr_lo, const uint8_t* d_table,
-                   size_t n, uint16_t* d_out, cudaStream_t s) {
+                   size_t n, uint16_t* d_out, cudaStream_t s, const uint64_t* d_n, bool fork) {
   int rc = planb::launch_bucketing(d_addr_hi, d_addr_lo, d_table, n, m->T, m->G, m->counts,
-                                   m->range, m->bhi, m->blo, m->perm, s);
+                                   m->range, m->bhi, m->blo, m->where, s, d_n);
   if (rc) return fail_detail(rc, "multi: bucketing", cudaGetLastError());
+  cudaError_t e = cudaSuccess;
+  if (fork) {
+    e = cudaEventRecord(m->fork, s);
+    for (int k = 0; e == cudaSuccess && k < planb_multi::kBranches; k++)
+      e = cudaStreamWaitEvent(m->side[k], m->fork, 0);
+    if (e != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: fork", e);
+  }
   for (uint32_t t = 0; t < m->T; t++) {
-    rc = planb::launch_lookup(cur[t]->dt, cur[t]->cfg, m->bhi, m->blo, n, d_out,
-                              m->fibs[t]->d_status, s, m->range + t, m->perm);
+    rc = planb::launch_lookup(cur[t]->dt, cur[t]->cfg, m->bhi, m->blo, n, m->bres,
+                              m->fibs[t]->d_status,
+                              fork ? m->side[t % planb_multi::kBranches] : s, m->range + t);
     if (rc) return fail_detail(rc, "multi: table lookup", cudaGetLastError());
   }
-  rc = planb::launch_invalid_fill(m->range, m->T, m->perm, d_out, s);
-  if (rc) return fail_detail(rc, "multi: invalid-id fill", cudaGetLastError());
+  for (int k = 0; fork && e == cudaSuccess && k < planb_multi::kBranches; k++) {
+    e = cudaEventRecord(m->join[k], m->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->join[k], 0);
+  }
+  if (e != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: join", e);
+  rc = planb::launch_gather(d_table, m->where, m->bres, n, m->T, m->G, d_out, s, d_n);
+  if (rc) return fail_detail(rc, "multi: gather", cudaGetLastError());
   return PLANB_OK;
 }
 
@@ -800,9 +979,11 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
       return PLANB_ECUDA;
     m->G = static_cast<uint32_t>(sms) * 8u;
     const size_t cap = max_batch;
-    const size_t bytes = cap * 8 * 2 + ((cap * 4 + 255) / 256) * 256 +
-                         ((static_cast<size_t>(m->T + 1) * m->G * 4 + 255) / 256) * 256 +
-                         (m->T + 2) * 8;
+    auto up = [](size_t x) { return ((x + 255) / 256) * 256; };
+    const size_t where_off = cap * 16, bres_off = where_off + up(cap * 4),
+                 counts_off = bres_off + up(cap * 2),
+                 range_off = counts_off + up(static_cast<size_t>(m->T + 1) * m->G * 4);
+    const size_t bytes = range_off + (m->T + 2) * 8;
     if (cudaMalloc(&m->mem, bytes) != cudaSuccess) {
       m->mem = nullptr;
       cudaGetLastError();
@@ -811,13 +992,18 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     char* b = static_cast<char*>(m->mem);
     m->bhi = reinterpret_cast<uint64_t*>(b);
     m->blo = m->bhi + cap;
-    m->perm = reinterpret_cast<uint32_t*>(m->blo + cap);
-    m->counts = reinterpret_cast<uint32_t*>(b + cap * 16 + ((cap * 4 + 255) / 256) * 256);
-    m->range = reinterpret_cast<uint64_t*>(
-        reinterpret_cast<char*>(m->counts) +
-        ((static_cast<size_t>(m->T + 1) * m->G * 4 + 255) / 256) * 256);
-    if (cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-      cudaFree(m->mem);
+    m->where = reinterpret_cast<uint32_t*>(b + where_off);
+    m->bres = reinterpret_cast<uint16_t*>(b + bres_off);
+    m->counts = reinterpret_cast<uint32_t*>(b + counts_off);
+    m->range = reinterpret_cast<uint64_t*>(b + range_off);
+    bool ok = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < planb_multi::kBranches; k++)
+      ok = cudaStreamCreateWithFlags(&m->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&m->join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      planb_multi_destroy(m.release());
       return PLANB_ECUDA;
     }
     *out = m.release();
@@ -827,8 +1013,30 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
   }
 }
 
+namespace {
+int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t* d_addr_lo,
+                      const uint8_t* d_table, size_t n, uint16_t* d_out, planb_stream_t stream,
+                      const uint64_t* d_n);
+}
+
 int planb_multi_lookup(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t* d_addr_lo,
                        const uint8_t* d_table, size_t n, uint16_t* d_out, planb_stream_t stream) {
+  return multi_lookup_impl(m, d_addr_hi, d_addr_lo, d_table, n, d_out, stream, nullptr);
+}
+
+int planb_multi_lookup_devn(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t* d_addr_lo,
+                            const uint8_t* d_table, const uint64_t* d_n, size_t max_n,
+                            uint16_t* d_out, planb_stream_t stream) {
+  if (!d_n) return PLANB_EINVAL;
+  return multi_lookup_impl(m, d_addr_hi, d_addr_lo, d_table, max_n, d_out, stream, d_n);
+}
+
+}  // extern "C"
+
+namespace {
+int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t* d_addr_lo,
+                      const uint8_t* d_table, size_t n, uint16_t* d_out, planb_stream_t stream,
+                      const uint64_t* d_n) {
   if (!m) return PLANB_EINVAL;
   if (n == 0) return PLANB_OK;
   if (!d_addr_hi || !d_addr_lo || !d_table || !d_out || n > m->cap) return PLANB_EINVAL;
@@ -844,13 +1052,12 @@ int planb_multi_lookup(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t
     planb_fib* f = m->fibs[t];
     std::lock_guard<std::mutex> lk2(f->cur_mu);
     cur[t] = f->cur;
-    note_stream(f, st);
-    note_stream(f, m->cap_stream);
+    note_stream(f, st);   // the graph runs on st; capture streams never execute work
   }
   if (m->flags & PLANB_MULTI_NO_GRAPH)
-    return multi_pipeline(m, cur, d_addr_hi, d_addr_lo, d_table, n, d_out, st);
+    return multi_pipeline(m, cur, d_addr_hi, d_addr_lo, d_table, n, d_out, st, d_n, false);
   bool same = m->exec && m->g_hi == d_addr_hi && m->g_lo == d_addr_lo && m->g_tid == d_table &&
-              m->g_out == d_out && m->g_n == n;
+              m->g_out == d_out && m->g_n == n && m->g_dn == d_n;
   for (uint32_t t = 0; same && t < m->T; t++) same = m->snap[t] == cur[t];
   if (!same) {
     // a table was swapped by an update, or the buffers changed: capture the pipeline again
@@ -863,7 +1070,8 @@ int planb_multi_lookup(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t
     cudaGetLastError();   // start the capture with no stale launch error
     const cudaError_t eb = cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (eb != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: begin capture", eb);
-    const int rc = multi_pipeline(m, cur, d_addr_hi, d_addr_lo, d_table, n, d_out, m->cap_stream);
+    const int rc =
+        multi_pipeline(m, cur, d_addr_hi, d_addr_lo, d_table, n, d_out, m->cap_stream, d_n, true);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(m->cap_stream, &graph);
     if (rc != PLANB_OK || ec != cudaSuccess) {
@@ -882,12 +1090,16 @@ int planb_multi_lookup(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t
     m->g_tid = d_table;
     m->g_out = d_out;
     m->g_n = n;
+    m->g_dn = d_n;
     m->snap = cur;
   }
   const cudaError_t eg = cudaGraphLaunch(m->exec, st);
   if (eg != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: graph launch", eg);
   return PLANB_OK;
 }
+}  // namespace
+
+extern "C" {
 
 void planb_multi_destroy(planb_multi* m) {
   if (!m) return;
@@ -896,6 +1108,11 @@ void planb_multi_destroy(planb_multi* m) {
     cudaDeviceSynchronize();
     if (m->exec) cudaGraphExecDestroy(m->exec);
     if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    for (int k = 0; k < planb_multi::kBranches; k++) {
+      if (m->side[k]) cudaStreamDestroy(m->side[k]);
+      if (m->join[k]) cudaEventDestroy(m->join[k]);
+    }
+    if (m->fork) cudaEventDestroy(m->fork);
     if (m->mem) cudaFree(m->mem);
   }
   delete m;

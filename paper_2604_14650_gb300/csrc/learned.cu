@@ -186,24 +186,15 @@ void init_weights(MlpWeights& w) {
   w.b2 = 0.0f;
 }
 
-struct DevBuf {
-  void* p = nullptr;
-  ~DevBuf() {
-    if (p) cudaFree(p);
-  }
-  bool alloc(size_t bytes) { return cudaMalloc(&p, bytes) == cudaSuccess; }
-  template <class T>
-  T* as() { return static_cast<T*>(p); }
-};
-
 }  // namespace
 
 int mlp_grad_host(const float* d_u, const float* d_t, size_t n, const float* w_host,
                   float* grad_host, double* loss_host, cudaStream_t st) {
   if (n >= (size_t(1) << 32)) return PLANB_EINVAL;
   DevBuf part, wb, gb, lb;
-  if (!part.alloc(kGradBlocks * kRow * sizeof(float)) || !wb.alloc(kMlpWeights * sizeof(float)) ||
-      !gb.alloc(kMlpParams * sizeof(float)) || !lb.alloc(sizeof(double))) {
+  if (!part.alloc(kGradBlocks * kRow * sizeof(float), nullptr) ||
+      !wb.alloc(kMlpWeights * sizeof(float), nullptr) ||
+      !gb.alloc(kMlpParams * sizeof(float), nullptr) || !lb.alloc(sizeof(double), nullptr)) {
     cudaGetLastError();
     return PLANB_ENOMEM;
   }
@@ -292,12 +283,14 @@ int build_learned(const Intervals& iv, uint32_t span, uint32_t leaves, uint32_t 
     P.mlp.b2 = v0[0];
   }
   DevBuf dk, du, dl, dt, dpart, dw, dm, dq, dv, dc, dstep, dloss, dleaf, dleaves, derr;
-  if (!dk.alloc(n * 8ull) || !du.alloc(n * 4ull) || !dl.alloc(n * 4ull) ||
-      !dt.alloc(n * 4ull) || !dpart.alloc(kGradBlocks * kRow * 4ull) ||
-      !dw.alloc(kMlpWeights * 4) || !dm.alloc(kRow * 4) || !dq.alloc(kRow * 4) ||
-      !dv.alloc(kRow * 4) || !dc.alloc(kRow * 4) || !dstep.alloc(sizeof(int)) ||
-      !dloss.alloc(sizeof(double)) || !dleaf.alloc(n * 4ull) ||
-      !dleaves.alloc(P.leaves * sizeof(LeafModel)) || !derr.alloc(P.leaves * 4ull)) {
+  if (!dk.alloc(n * 8ull, nullptr) || !du.alloc(n * 4ull, nullptr) ||
+      !dl.alloc(n * 4ull, nullptr) || !dt.alloc(n * 4ull, nullptr) ||
+      !dpart.alloc(kGradBlocks * kRow * 4ull, nullptr) || !dw.alloc(kMlpWeights * 4, nullptr) ||
+      !dm.alloc(kRow * 4, nullptr) || !dq.alloc(kRow * 4, nullptr) ||
+      !dv.alloc(kRow * 4, nullptr) || !dc.alloc(kRow * 4, nullptr) ||
+      !dstep.alloc(sizeof(int), nullptr) || !dloss.alloc(sizeof(double), nullptr) ||
+      !dleaf.alloc(n * 4ull, nullptr) || !dleaves.alloc(P.leaves * sizeof(LeafModel), nullptr) ||
+      !derr.alloc(P.leaves * 4ull, nullptr)) {
     cudaGetLastError();
     return PLANB_ENOMEM;
   }

@@ -86,6 +86,47 @@ int canonicalise(const uint64_t* hi, const uint64_t* lo, const uint8_t* len, con
 // sweep) on a canonical, sorted prefix list.
 void sweep(const std::vector<Prefix>& canon, bool merge_equal_nh, Intervals& out);
 
+// Device memory owned by the host code that allocated it; with a stream the allocation and the
+// free are stream-ordered (cudaMallocAsync / cudaFreeAsync), so the stream must outlive the buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void* stream = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf();
+  bool alloc(size_t n, void* stream);
+  void release();
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+// Elementary intervals on the device (the GPU builder's a1-a3 result): first address (hi, lo) and
+// next hop of each of the m intervals.
+struct GpuIntervals {
+  DevBuf hi, lo, nh;
+  uint64_t m = 0;
+};
+
+// GPU builder (gpu_builder.cu), all on `stream`:
+//   gpu_canonicalise  step a1 of host arrays: the canonical prefix list on the device (N entries,
+//                     the same list and order as canonicalise()).
+//   gpu_sweep         steps a2-a3 of a canonical device list: the intervals sweep() would give.
+//   gpu_fill          step a4 into a table's device allocation: the node array(s) (fill_f8x128,
+//                     fill_f8v7 or fill_f16hi), the top-of-tree index of level S (fill_sidx, when
+//                     sidx_n > 0) and the m next hops.
+//   gpu_download      the intervals back to the host.
+struct Layout;
+int gpu_canonicalise(const uint64_t* hi, const uint64_t* lo, const uint8_t* len,
+                     const uint16_t* nh, size_t n, void* stream, DevBuf& d_canon, uint64_t& N);
+int gpu_sweep(const Prefix* d_canon, uint64_t N, bool merge_equal_nh, void* stream,
+              GpuIntervals& out);
+int gpu_fill(const GpuIntervals& iv, const Layout& L, uint32_t format, uint32_t S,
+             uint64_t sidx_n, void* nodes, uint64_t* nodes_lo, uint64_t* sidx, uint16_t* values,
+             void* stream);
+int gpu_download(const GpuIntervals& iv, void* stream, Intervals& out);
+
 // Linearized B+-tree arithmetic (Section 3.2).
 struct Layout {
   uint32_t k = 0, b = 0, D = 0;        // keys per internal node, fanout, levels incl. leaves
@@ -164,14 +205,17 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   const uint32_t* d_perm = nullptr);
 
 // Multi-table bucketing (multi.cu): groups n addresses by their u8 table id (ids >= T form one
-// extra segment) into d_bhi/d_blo, table-major, with d_perm[j] = original index; d_range[t] ..
-// d_range[t+1] bound table t's segment. d_counts holds (T+1) x G words. n < 2^32.
+// extra segment) into d_bhi/d_blo, table-major, with d_where[i] = the bucketed position of address
+// i; d_range[t] .. d_range[t+1] bound table t's segment. d_counts holds (T+1) x G words. n < 2^32.
+// With d_n the kernels read the batch size from device memory (n then only bounds it).
 int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
                      uint32_t T, uint32_t G, uint32_t* d_counts, uint64_t* d_range,
-                     uint64_t* d_bhi, uint64_t* d_blo, uint32_t* d_perm, void* stream);
-// Writes next hop 0 for the addresses of the invalid-id segment.
-int launch_invalid_fill(const uint64_t* d_range, uint32_t T, const uint32_t* d_perm,
-                        uint16_t* d_out, void* stream);
+                     uint64_t* d_bhi, uint64_t* d_blo, uint32_t* d_where, void* stream,
+                     const uint64_t* d_n = nullptr);
+// d_out[i] = d_bres[d_where[i]] for ids below T, else 0 (at most G blocks; d_n as above).
+int launch_gather(const uint8_t* d_tid, const uint32_t* d_where, const uint16_t* d_bres, size_t n,
+                  uint32_t T, uint32_t G, uint16_t* d_out, void* stream,
+                  const uint64_t* d_n = nullptr);
 
 // cudaFuncGetAttributes of the lookup kernel a table uses (multi: its multi-table form):
 // out[0..5] = registers, max threads per block, max dynamic shared bytes, local bytes, static shared

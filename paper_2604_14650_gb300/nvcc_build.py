@@ -18,8 +18,11 @@ OUT = os.path.join(HERE, "_build", platform.machine())
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["builder.cpp", "lookup.cu", "learned.cu", "multi.cu", "capi.cu"]
+SOURCES = ["builder.cpp", "lookup.cu", "learned.cu", "multi.cu", "capi.cu", "server.cu",
+           "gpu_builder.cu"]
 LIBS = {"libplanb.so": [], "libplanb_checked.so": ["-DPLANB_BOUNDS_CHECK"]}
+# the only translation unit the bounds-checking define changes; the others are compiled once
+CHECKED_SOURCES = {"lookup.cu"}
 
 
 def nvcc() -> str:
@@ -49,14 +52,15 @@ def build(force: bool = False, verbose: bool = False) -> dict:
                os.path.join(INCLUDE, "planb.h")]
     jobs, links = [], {}
     for lib, defines in LIBS.items():
-        tag = "chk" if defines else "rel"
         objs = []
         for src in SOURCES:
+            own = defines if src in CHECKED_SOURCES else []
+            tag = "chk" if own else "rel"
             s = os.path.join(CSRC, src)
             o = os.path.join(OUT, f"{os.path.splitext(src)[0]}.{tag}.o")
             objs.append(o)
-            if force or _stale(o, [s, *headers]):
-                jobs.append([cc, *_flags(defines), "-c", s, "-o", o])
+            if (force or _stale(o, [s, *headers])) and not any(j[-1] == o for j in jobs):
+                jobs.append([cc, *_flags(own), "-c", s, "-o", o])
         links[lib] = objs
 
     def run(cmd):

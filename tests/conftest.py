@@ -8,3 +8,5 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    # without pytest-timeout installed, a timeout mark is inert
+    config.addinivalue_line("markers", "timeout(seconds): per-test time limit (pytest-timeout)")
