@@ -250,11 +250,13 @@ typedef struct planb_multi planb_multi; /* several tables (VRFs) served by one c
  * addresses each carry a u8 table id. The paper serves one table; many tables per box are the
  * same lookup applied per table. fibs: n_tables table handles (1..255), not owned: they must
  * outlive the group; updates to them are picked up by later lookups. max_batch: most addresses per
- * planb_multi_lookup call (< 2^32); the group owns max_batch x 20 bytes of device scratch.
- * Tables built with PLANB_KERNEL_LEARNED cannot join a group. flags: 0, or PLANB_MULTI_NO_GRAPH.
- * Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ECUDA.
+ * planb_multi_lookup call (< 2^32); the group owns max_batch x 22 bytes of device scratch.
+ * Tables built with PLANB_KERNEL_LEARNED cannot join a group. flags: 0, or an OR of the
+ * PLANB_MULTI_* flags below. Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ECUDA.
  */
-#define PLANB_MULTI_NO_GRAPH 1u /* flag: launch the pipeline directly instead of a captured graph */
+#define PLANB_MULTI_NO_GRAPH 1u  /* flag: launch the pipeline directly instead of a captured graph */
+#define PLANB_MULTI_PER_TABLE 2u /* flag: one lookup launch per table even where every table could
+                                    share the single persistent launch (for comparison)          */
 int planb_multi_create(planb_fib *const *fibs, uint32_t n_tables, size_t max_batch,
                        uint32_t flags, planb_multi **out);
 
@@ -262,11 +264,14 @@ int planb_multi_create(planb_fib *const *fibs, uint32_t n_tables, size_t max_bat
  * planb_multi_lookup — next hop of n addresses, address i looked up in table d_table[i]
  * (ids >= n_tables give 0). d_addr_hi, d_addr_lo: device u64 arrays; d_table: device u8 array;
  * d_out: device u16 array; all of n entries. The batch is grouped by table (a counting sort on the
- * device), each table's group is looked up by its own kernel (the tables' shared-memory index and
- * nodes stay hot while it runs), and results are written back in the input order. The whole
+ * device); when every table uses the hybrid kernel (F8X128 or F8V7) one persistent launch looks
+ * up all groups — each CTA takes a contiguous piece of the grouped batch and stages the index of
+ * each table it meets — else each table's group gets its own launch; results are gathered back
+ * into the input order. The whole
  * pipeline is captured once as a CUDA graph and replayed while the buffers, n and the tables stay
  * the same; a table swapped by planb_update, or new buffers, cause one new capture. Enqueued on
- * `stream`; calls on one group are serialised.
+ * `stream`; calls on one group are serialised on the host, and since the group's device scratch
+ * is reused by every call, all calls on one group must use the same stream.
  * Errors: PLANB_EINVAL (null pointer, misalignment, n > max_batch), PLANB_ECUDA.
  */
 int planb_multi_lookup(planb_multi *m, const uint64_t *d_addr_hi, const uint64_t *d_addr_lo,
@@ -357,6 +362,11 @@ int planb_server_update(planb_server *s, uint32_t table_id, const planb_route *i
 
 /* planb_server_stats — counters and latency percentiles (over the last 2^20 requests). */
 int planb_server_stats(planb_server *s, planb_server_stats_t *out);
+
+/* planb_server_error_detail — copies (NUL-terminated, truncated to cap) where and why the engine
+ * last failed: the failing step and the CUDA error, or "" when nothing failed. Errors:
+ * PLANB_EINVAL. */
+int planb_server_error_detail(planb_server *s, char *buf, size_t cap);
 
 /* planb_server_reset_stats — zeroes the counters and the latency record. */
 void planb_server_reset_stats(planb_server *s);

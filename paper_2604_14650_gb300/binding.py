@@ -8,9 +8,11 @@ or CPU fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 import platform
+import weakref
 
 import numpy as np
 
@@ -113,6 +115,7 @@ _SIGS = {
     "planb_server_update": (C.c_int, [_vp, C.c_uint32, _vp, _sz, _vp, _sz]),
     "planb_server_stats": (C.c_int, [_vp, _vp]),
     "planb_server_reset_stats": (None, [_vp]),
+    "planb_server_error_detail": (C.c_int, [_vp, C.c_char_p, _sz]),
     "planb_server_destroy": (None, [_vp]),
 }
 
@@ -385,14 +388,15 @@ def _host_ptrs(hi, lo):
 class MultiFib:
     """Several tables (VRFs) looked up by one captured graph; each address carries a table id."""
 
-    def __init__(self, fibs, max_batch: int, graph: bool = True):
+    def __init__(self, fibs, max_batch: int, graph: bool = True, per_table: bool = False):
         self._lib = fibs[0]._lib
         self._h = None
         self.fibs = list(fibs)                 # keep the tables alive while the group exists
         arr = (C.c_void_p * len(fibs))(*[f._h.value for f in fibs])
         h = C.c_void_p()
-        _check(self._lib.planb_multi_create(arr, len(fibs), max_batch, 0 if graph else 1,
-                                            C.byref(h)), "planb_multi_create")
+        flags = (0 if graph else 1) | (2 if per_table else 0)
+        _check(self._lib.planb_multi_create(arr, len(fibs), max_batch, flags, C.byref(h)),
+               "planb_multi_create")
         self._h = h
 
     def lookup(self, addr_hi, addr_lo, table, out=None, stream=None):
@@ -449,6 +453,19 @@ class ServerStats(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+_live_servers = weakref.WeakSet()
+
+
+@atexit.register
+def _close_live_servers():
+    # an engine's threads must stop before the CUDA runtime is torn down at process exit
+    for srv in list(_live_servers):
+        try:
+            srv.close()
+        except Exception:
+            pass
+
+
 class Server:
     """The serving engine (planb_server): continuous batching of host-buffer requests over tables."""
 
@@ -465,6 +482,7 @@ class Server:
         _check(self._lib.planb_server_create(C.byref(o), C.byref(h)), "planb_server_create")
         self._h = h
         self.tables = []
+        _live_servers.add(self)
 
     def add_table(self, fib: Fib) -> int:
         tid = C.c_uint32()
@@ -497,6 +515,11 @@ class Server:
         s = ServerStats()
         _check(self._lib.planb_server_stats(self._h, C.byref(s)), "planb_server_stats")
         return {f: getattr(s, f) for f, _ in ServerStats._fields_ if f != "reserved"}
+
+    def error_detail(self) -> str:
+        buf = C.create_string_buffer(256)
+        _check(self._lib.planb_server_error_detail(self._h, buf, 256), "planb_server_error_detail")
+        return buf.value.decode(errors="replace")
 
     def reset_stats(self):
         self._lib.planb_server_reset_stats(self._h)

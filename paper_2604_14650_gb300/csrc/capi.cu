@@ -901,6 +901,10 @@ struct planb_multi {
   uint64_t *bhi = nullptr, *blo = nullptr, *range = nullptr;
   uint32_t *where = nullptr, *counts = nullptr;
   uint16_t* bres = nullptr;      // results in bucketed order
+  planb::MultiDesc* desc = nullptr;  // per-table descriptors of the single persistent launch
+  bool persist = false;          // the current tables all fit the single persistent launch
+  int persist_ctas = 0;
+  size_t persist_smem = 0;
   cudaStream_t cap_stream = nullptr;
   static constexpr int kBranches = 4;          // per-table lookups run on this many streams
   cudaStream_t side[kBranches] = {};
@@ -928,17 +932,24 @@ int multi_pipeline(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cu
                                    m->range, m->bhi, m->blo, m->where, s, d_n);
   if (rc) return fail_detail(rc, "multi: bucketing", cudaGetLastError());
   cudaError_t e = cudaSuccess;
+  fork = fork && !m->persist;
   if (fork) {
     e = cudaEventRecord(m->fork, s);
     for (int k = 0; e == cudaSuccess && k < planb_multi::kBranches; k++)
       e = cudaStreamWaitEvent(m->side[k], m->fork, 0);
     if (e != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: fork", e);
   }
-  for (uint32_t t = 0; t < m->T; t++) {
-    rc = planb::launch_lookup(cur[t]->dt, cur[t]->cfg, m->bhi, m->blo, n, m->bres,
-                              m->fibs[t]->d_status,
-                              fork ? m->side[t % planb_multi::kBranches] : s, m->range + t);
-    if (rc) return fail_detail(rc, "multi: table lookup", cudaGetLastError());
+  if (m->persist) {
+    rc = planb::launch_multi_persistent(m->desc, m->T, m->range, m->bhi, m->blo, m->bres,
+                                        m->fibs[0]->d_status, m->persist_ctas, m->persist_smem, s);
+    if (rc) return fail_detail(rc, "multi: persistent lookup", cudaGetLastError());
+  } else {
+    for (uint32_t t = 0; t < m->T; t++) {
+      rc = planb::launch_lookup(cur[t]->dt, cur[t]->cfg, m->bhi, m->blo, n, m->bres,
+                                m->fibs[t]->d_status,
+                                fork ? m->side[t % planb_multi::kBranches] : s, m->range + t);
+      if (rc) return fail_detail(rc, "multi: table lookup", cudaGetLastError());
+    }
   }
   for (int k = 0; fork && e == cudaSuccess && k < planb_multi::kBranches; k++) {
     e = cudaEventRecord(m->join[k], m->side[k]);
@@ -983,7 +994,8 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     const size_t where_off = cap * 16, bres_off = where_off + up(cap * 4),
                  counts_off = bres_off + up(cap * 2),
                  range_off = counts_off + up(static_cast<size_t>(m->T + 1) * m->G * 4);
-    const size_t bytes = range_off + (m->T + 2) * 8;
+    const size_t desc_off = range_off + up((2 * m->T + 3) * 8);
+    const size_t bytes = desc_off + m->T * sizeof(planb::MultiDesc);
     if (cudaMalloc(&m->mem, bytes) != cudaSuccess) {
       m->mem = nullptr;
       cudaGetLastError();
@@ -996,6 +1008,7 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     m->bres = reinterpret_cast<uint16_t*>(b + bres_off);
     m->counts = reinterpret_cast<uint32_t*>(b + counts_off);
     m->range = reinterpret_cast<uint64_t*>(b + range_off);
+    m->desc = reinterpret_cast<planb::MultiDesc*>(b + desc_off);
     bool ok = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) == cudaSuccess;
     for (int k = 0; ok && k < planb_multi::kBranches; k++)
@@ -1034,6 +1047,49 @@ int planb_multi_lookup_devn(planb_multi* m, const uint64_t* d_addr_hi, const uin
 }  // extern "C"
 
 namespace {
+// Decides whether the current tables can share the single persistent launch (every one a hybrid
+// F8X128 or F8V7 table whose index fits the shared memory) and writes their descriptors.
+int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cur,
+                        cudaStream_t st) {
+  m->persist = false;
+  if (m->flags & PLANB_MULTI_PER_TABLE) return PLANB_OK;
+  std::vector<planb::MultiDesc> hd(m->T);
+  uint64_t max_n = 0;
+  for (uint32_t t = 0; t < m->T; t++) {
+    const planb::DevTable& d = cur[t]->dt;
+    if (d.kernel != planb::kHybrid ||
+        (d.format != PLANB_FMT_F8X128 && d.format != PLANB_FMT_F8V7) || d.depth < d.smem_levels)
+      return PLANB_OK;
+    planb::MultiDesc& x = hd[t];
+    x.nodes = d.nodes;
+    x.sidx = d.sidx;
+    x.values = d.values;
+    x.sidx_n = static_cast<uint32_t>(d.sidx_n);
+    x.sidx_node = static_cast<uint32_t>(d.sidx_node);
+    x.internal_nodes = static_cast<uint32_t>(d.internal_nodes);
+    x.db = d.depth - d.smem_levels;
+    x.packed = d.format == PLANB_FMT_F8V7 ? 1u : 0u;
+    x.pad = 0;
+    x.n_intervals = d.n_intervals;
+    max_n = std::max<uint64_t>(max_n, d.sidx_n);
+  }
+  const size_t smem = ((m->T + 3u) & ~1u) * 8u + max_n * 8u;
+  int ctas = 0;
+  if (planb::multi_persistent_setup(m->device, smem, &ctas) != PLANB_OK) {
+    cudaGetLastError();
+    return PLANB_OK;   // too large for one CTA: per-table launches
+  }
+  const cudaError_t e = cudaMemcpyAsync(m->desc, hd.data(), hd.size() * sizeof(planb::MultiDesc),
+                                        cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: descriptors", e);
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (es != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: descriptors", es);
+  m->persist = true;
+  m->persist_ctas = ctas;
+  m->persist_smem = smem;
+  return PLANB_OK;
+}
+
 int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t* d_addr_lo,
                       const uint8_t* d_table, size_t n, uint16_t* d_out, planb_stream_t stream,
                       const uint64_t* d_n) {
@@ -1054,11 +1110,22 @@ int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t*
     cur[t] = f->cur;
     note_stream(f, st);   // the graph runs on st; capture streams never execute work
   }
-  if (m->flags & PLANB_MULTI_NO_GRAPH)
+  bool changed = m->snap.size() != m->T;
+  for (uint32_t t = 0; !changed && t < m->T; t++) changed = m->snap[t] != cur[t];
+  if (changed) {
+    // new tables: the per-table descriptors of the persistent launch are rewritten once the
+    // work already queued on st (which reads them) is done
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (es != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: wait for previous work", es);
+    int rc = refresh_descriptors(m, cur, st);
+    if (rc) return rc;
+  }
+  if (m->flags & PLANB_MULTI_NO_GRAPH) {
+    if (changed) m->snap = cur;
     return multi_pipeline(m, cur, d_addr_hi, d_addr_lo, d_table, n, d_out, st, d_n, false);
-  bool same = m->exec && m->g_hi == d_addr_hi && m->g_lo == d_addr_lo && m->g_tid == d_table &&
-              m->g_out == d_out && m->g_n == n && m->g_dn == d_n;
-  for (uint32_t t = 0; same && t < m->T; t++) same = m->snap[t] == cur[t];
+  }
+  const bool same = !changed && m->exec && m->g_hi == d_addr_hi && m->g_lo == d_addr_lo &&
+                    m->g_tid == d_table && m->g_out == d_out && m->g_n == n && m->g_dn == d_n;
   if (!same) {
     // a table was swapped by an update, or the buffers changed: capture the pipeline again
     if (m->exec) {

@@ -343,6 +343,7 @@ int sort_by_address(Ctx& cx, const uint64_t* hi, const uint64_t* lo, const uint3
                     int key_bits, uint64_t n, uint32_t* ord, uint32_t* w32a, uint32_t* w32b,
                     uint64_t* w64a, uint64_t* w64b) {
   if (n == 0) return PLANB_OK;
+  cudaGetLastError();   // the check at the end is about these launches only
   uint32_t* a = ord;
   uint32_t* b = w32a;
   k_gather<uint32_t><<<blocks_for(n), 256, 0, cx.st>>>(key, a, n, w32b);
@@ -375,6 +376,7 @@ int gpu_canonicalise(const uint64_t* hi, const uint64_t* lo, const uint8_t* len,
     if (len[i] > 128) return PLANB_EINVAL;
   Ctx cx;
   cx.st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
   const uint64_t n = n_in;
   if (n == 0) return d_canon.alloc(16, stream) ? PLANB_OK : PLANB_ENOMEM;
   DevBuf d_hi, d_lo, d_len, d_nh, mhi, mlo, key, ord, w32a, w32b, w64a, w64b, keep, sel, cnt;
@@ -417,6 +419,7 @@ int gpu_sweep(const Prefix* d_canon, uint64_t N, bool merge, void* stream, GpuIn
   out.m = 0;
   Ctx cx;
   cx.st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
   if (N >= (uint64_t(1) << 30)) return PLANB_EINVAL;
   const uint64_t E2 = N ? 2 * N : 1;
   DevBuf ehi, elo, ekey, evalid, slot, eord, w32a, w32b, w64a, w64b, cnt;
@@ -536,6 +539,7 @@ int gpu_fill(const GpuIntervals& iv, const Layout& L, uint32_t format, uint32_t 
              uint64_t sidx_n, void* nodes, uint64_t* nodes_lo, uint64_t* sidx, uint16_t* values,
              void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
   FillGeom g{};
   for (uint32_t l = 0; l <= L.D && l < 17; l++) g.level_node[l] = L.level_node[l];
   // child_span[l] = kl * b^(D-2-l) for the internal levels l = 0 .. D-2

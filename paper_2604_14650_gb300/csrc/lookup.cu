@@ -426,6 +426,182 @@ __global__ void __launch_bounds__(256) lookup_flat(const KParams p) {
   }
 }
 
+// ------------------------------------------------------------------------------- multi, one launch
+// All tables of a bucketed multi-table batch in one persistent launch. CTA b takes the b-th
+// contiguous chunk of the bucketed addresses (a multiple of 32), so it meets only the few tables
+// whose segments overlap its chunk; for each it stages that table's top-of-tree index (high halves)
+// in shared memory and runs the hybrid descent of lookup_hybrid — phase A over the index, then the
+// table's remaining DB levels from L2 by 8-lane groups — writing each result at its bucketed
+// position. The tile code is instantiated per (DB, packed) and picked per table; depths beyond
+// kMultiMaxDb take a run-time level loop. Addresses with an id beyond the tables (after range[T])
+// are left to the gather that follows.
+constexpr int kMultiMaxDb = 4;
+
+template <int DB, bool PACKED>   // DB < 0: run-time depth d.db
+__device__ __forceinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh, uint64_t s0,
+                                            uint64_t s1, const uint64_t* __restrict__ xhi,
+                                            const uint64_t* __restrict__ xlo,
+                                            uint16_t* __restrict__ out, uint32_t* status) {
+  const ulonglong2* nodes = static_cast<const ulonglong2*>(d.nodes);
+  const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
+  const uint32_t N = d.sidx_n;
+  const uint32_t db = DB >= 0 ? static_cast<uint32_t>(DB) : d.db;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t g = lane >> 3;
+  const uint32_t j = lane & 7u;
+  const uint32_t gshift = g * 8u;
+  const uint32_t gmask = 0xFFu << gshift;
+  const uint32_t wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint64_t base = s0 + static_cast<uint64_t>(wid) * 32u; base < s1; base += nw * 32u) {
+    const uint64_t mine = base + lane;
+    const bool ok = mine < s1;
+    const uint64_t my_hi = ok ? xhi[mine] : 0ull;
+    const uint64_t my_lo = ok ? xlo[mine] : 0ull;
+    uint32_t cnt = 0;
+    if (N) {
+      uint32_t b = 0, n = N;
+      while (n > 1) {
+        const uint32_t half = n >> 1;
+        b = Uh[b + half] < my_hi ? b + half : b;
+        n -= half;
+      }
+      cnt = b + (Uh[b] < my_hi ? 1u : 0u);
+      while (cnt < N && Uh[cnt] == my_hi && __ldg(&sidx[cnt].y) < my_lo) cnt++;
+    }
+    uint32_t result = 0;
+    if (db == 0) {
+      uint32_t rank = cnt;
+#ifdef PLANB_BOUNDS_CHECK
+      if (rank >= d.n_intervals) {
+        report(status, 2u);
+        rank = 0;
+      }
+#endif
+      result = __ldg(d.values + rank);
+    } else {
+      const uint32_t my_node = d.sidx_node + cnt;
+#pragma unroll
+      for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
+        uint64_t qh[kRounds];
+        uint32_t nd[kRounds], c[kRounds];
+        ulonglong2 key[kRounds];
+#pragma unroll
+        for (int i = 0; i < kRounds; i++) {
+          const uint32_t src = gshift + r0 + i;
+          qh[i] = __shfl_sync(kFull, my_hi, src);
+          nd[i] = __shfl_sync(kFull, my_node, src);
+        }
+#pragma unroll
+        for (uint32_t l = 0; l < (DB >= 0 ? static_cast<uint32_t>(DB) : db); l++) {
+#pragma unroll
+          for (int i = 0; i < kRounds; i++)
+            key[i] = __ldg(nodes + static_cast<uint64_t>(nd[i]) * 8u + j);
+          const bool last = l + 1 == db;
+          const bool keylane = !(PACKED && last) || j < 7u;
+          bool lt[kRounds], eq[kRounds];
+          bool anyeq = false;
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            lt[i] = keylane & (key[i].x < qh[i]);
+            eq[i] = keylane & (key[i].x == qh[i]);
+            anyeq |= eq[i];
+          }
+          if (__any_sync(kFull, anyeq)) {
+#pragma unroll
+            for (int i = 0; i < kRounds; i++) {
+              const uint64_t ql = __shfl_sync(kFull, my_lo, gshift + r0 + i);
+              lt[i] = lt[i] | (eq[i] & (key[i].y < ql));
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            c[i] = __popc(__ballot_sync(kFull, lt[i]) & gmask);
+            if (!last) nd[i] = nd[i] * 9u + 1u + c[i];
+          }
+        }
+        if (PACKED) {
+          // the next hop of slot c sits in slot 7 of the same leaf line (lane 7 of the group)
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+#ifdef PLANB_BOUNDS_CHECK
+            if (c[i] > 6u) report(status, 4u);
+#endif
+            const uint32_t ci = c[i] & 7u;
+            const uint64_t w = ci < 4u ? key[i].x : key[i].y;
+            const uint32_t f = static_cast<uint32_t>(w >> (16u * (ci & 3u))) & 0xFFFFu;
+            const uint32_t v = __shfl_sync(kFull, f, gshift + 7u);
+            if (j == r0 + i) result = v;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            uint64_t rank = static_cast<uint64_t>(nd[i] - d.internal_nodes) * 8u + c[i];
+#ifdef PLANB_BOUNDS_CHECK
+            if (rank >= d.n_intervals) {
+              report(status, 4u);
+              rank = 0;
+            }
+#endif
+            const uint32_t v = __ldg(d.values + rank);
+            if (j == r0 + i) result = v;
+          }
+        }
+      }
+    }
+    if (ok) out[mine] = static_cast<uint16_t>(result);
+  }
+}
+
+__global__ void __launch_bounds__(512, 2)
+    lookup_multi_persistent(const MultiDesc* __restrict__ desc, uint32_t T,
+                            const uint64_t* __restrict__ range, const uint64_t* __restrict__ xhi,
+                            const uint64_t* __restrict__ xlo, uint16_t* __restrict__ out,
+                            uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* R = reinterpret_cast<uint64_t*>(smem_raw);           // range[0 .. T+1]
+  uint64_t* Uh = R + ((T + 3u) & ~1u);                           // the staged index
+  for (uint32_t i = threadIdx.x; i <= T + 1u; i += blockDim.x) R[i] = range[i];
+  __syncthreads();
+  const uint64_t nreal = R[T];
+  const uint64_t chunk = ((nreal + gridDim.x - 1) / gridDim.x + 31u) & ~31ull;
+  const uint64_t c0 = min(static_cast<uint64_t>(blockIdx.x) * chunk, nreal);
+  const uint64_t c1 = min(c0 + chunk, nreal);
+  if (c0 >= c1) return;   // the whole CTA leaves together
+  uint32_t t = 0;
+  while (t + 1u < T && R[t + 1] <= c0) t++;
+  for (; t < T && R[t] < c1; t++) {
+    const uint64_t s0 = max(R[t], c0), s1 = min(R[t + 1], c1);
+    if (s0 >= s1) continue;
+    __shared__ MultiDesc d;   // kept in shared memory: the tile loop is short of registers
+    __syncthreads();          // the previous table's readers are done with Uh and d
+    if (threadIdx.x == 0) d = desc[t];
+    __syncthreads();
+    const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
+    for (uint32_t i = threadIdx.x; i < d.sidx_n; i += blockDim.x) Uh[i] = __ldg(&sidx[i].x);
+    __syncthreads();
+    const uint32_t sel = d.db <= static_cast<uint32_t>(kMultiMaxDb) ? d.db : 15u;
+    if (d.packed) {
+      switch (sel) {
+        case 0: multi_tiles<0, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 1: multi_tiles<1, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 2: multi_tiles<2, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 3: multi_tiles<3, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 4: multi_tiles<4, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        default: multi_tiles<-1, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+      }
+    } else {
+      switch (sel) {
+        case 0: multi_tiles<0, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 1: multi_tiles<1, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 2: multi_tiles<2, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 3: multi_tiles<3, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 4: multi_tiles<4, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        default: multi_tiles<-1, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+      }
+    }
+  }
+}
+
 typedef void (*KernelFn)(const KParams);
 
 constexpr int kMaxDepth = 10;
@@ -540,6 +716,7 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   if (multi && t.kernel == kLearned) return PLANB_EINVAL;   // no multi-table form
   KernelFn fn = kernel_for(t, multi);
   if (!fn) return PLANB_EINVAL;
+  cudaGetLastError();   // the check below is about this launch, not an earlier call's leftover
   KParams p;
   p.nodes = static_cast<const ulonglong2*>(t.nodes);
   p.nodes_hi = static_cast<const uint64_t*>(t.nodes);
@@ -574,6 +751,34 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   if (cfg.blocks > 0 && blocks > static_cast<uint64_t>(cfg.blocks)) blocks = cfg.blocks;
   fn<<<static_cast<unsigned>(blocks), cfg.threads, cfg.smem_bytes,
        static_cast<cudaStream_t>(stream)>>>(p);
+  return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+int multi_persistent_setup(int device, size_t smem_bytes, int* ctas) {
+  int optin = 0, sms = 0, per_sm = 0;
+  const void* fn = reinterpret_cast<const void*>(lookup_multi_persistent);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return PLANB_ECUDA;
+  if (smem_bytes > static_cast<size_t>(optin)) return PLANB_EINVAL;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+    return PLANB_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, smem_bytes) != cudaSuccess)
+    return PLANB_ECUDA;
+  if (per_sm < 1) return PLANB_EINVAL;
+  *ctas = sms * per_sm;
+  return PLANB_OK;
+}
+
+int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t* d_range,
+                            const uint64_t* d_hi, const uint64_t* d_lo, uint16_t* d_out,
+                            uint32_t* d_status, int ctas, size_t smem_bytes, void* stream) {
+  if (T == 0 || T > 255 || ctas < 1) return PLANB_EINVAL;
+  cudaGetLastError();
+  lookup_multi_persistent<<<static_cast<unsigned>(ctas), 512, smem_bytes,
+                            static_cast<cudaStream_t>(stream)>>>(d_desc, T, d_range, d_hi, d_lo,
+                                                                 d_out, d_status);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

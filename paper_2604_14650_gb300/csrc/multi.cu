@@ -11,6 +11,8 @@
 // Ids at or above the table count get next hop 0 from the gather.
 #include <cuda_runtime.h>
 
+#include <cub/cub.cuh>
+
 #include "planb_internal.h"
 
 namespace planb {
@@ -44,46 +46,61 @@ __global__ void mt_hist_kernel(const uint8_t* __restrict__ tid, uint64_t n, uint
   for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) counts[t * gridDim.x + blockIdx.x] = h[t];
 }
 
-// One block: row t (table t's counts over the G chunks) becomes the chunks' output offsets;
-// range[t], range[t+1] bound table t's segment (range[T], range[T+1] the invalid-id segment).
-__global__ void mt_scan_kernel(uint32_t* __restrict__ counts, uint32_t G, uint32_t T,
-                               uint64_t* __restrict__ range) {
-  __shared__ uint64_t total[257];
+// Block t scans row t of the (T+1) x G chunk counts in place into exclusive offsets within the row
+// and writes the row's total.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+
+__global__ void __launch_bounds__(kScanThreads) mt_rowscan_kernel(uint32_t* __restrict__ counts,
+                                                                  uint32_t G,
+                                                                  uint64_t* __restrict__ totals) {
+  typedef cub::BlockScan<uint32_t, kScanThreads> Scan;
+  __shared__ typename Scan::TempStorage tmp;
+  uint32_t* row = counts + static_cast<uint64_t>(blockIdx.x) * G;
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < G; base += kScanThreads * kScanItems) {
+    uint32_t v[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+      const uint32_t i = base + threadIdx.x * kScanItems + k;
+      v[k] = i < G ? row[i] : 0u;
+    }
+    uint32_t tile_total = 0;
+    Scan(tmp).ExclusiveSum(v, v, tile_total);
+    __syncthreads();   // tmp is reused by the next tile
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+      const uint32_t i = base + threadIdx.x * kScanItems + k;
+      if (i < G) row[i] = v[k] + carry;
+    }
+    carry += tile_total;
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+// One block: range[t] = sum of the totals of rows before t (range[T] starts the invalid-id
+// segment, range[T+1] = the batch size).
+__global__ void mt_tablescan_kernel(const uint64_t* __restrict__ totals, uint32_t T,
+                                    uint64_t* __restrict__ range) {
+  typedef cub::BlockScan<uint64_t, 256> Scan;
+  __shared__ typename Scan::TempStorage tmp;
   const uint32_t t = threadIdx.x;
-  if (t <= T) {
-    uint64_t s = 0;
-    for (uint32_t b = 0; b < G; b++) {
-      const uint32_t c = counts[t * G + b];
-      counts[t * G + b] = static_cast<uint32_t>(s);
-      s += c;
-    }
-    total[t] = s;
-  }
-  __syncthreads();
-  if (t == 0) {
-    uint64_t run = 0;
-    for (uint32_t u = 0; u <= T; u++) {
-      range[u] = run;
-      run += total[u];
-    }
-    range[T + 1] = run;
-  }
-  __syncthreads();
-  if (t <= T) {
-    const uint32_t base = static_cast<uint32_t>(range[t]);
-    for (uint32_t b = 0; b < G; b++) counts[t * G + b] += base;
-  }
+  uint64_t v = t <= T ? totals[t] : 0ull, excl = 0, all = 0;
+  Scan(tmp).ExclusiveSum(v, excl, all);
+  if (t <= T) range[t] = excl;
+  if (t == 0) range[T + 1] = all;
 }
 
 __global__ void mt_scatter_kernel(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo,
                                   const uint8_t* __restrict__ tid, uint64_t n, uint32_t T,
                                   uint64_t chunk, const uint32_t* __restrict__ offsets,
+                                  const uint64_t* __restrict__ range,
                                   uint64_t* __restrict__ bhi, uint64_t* __restrict__ blo,
                                   uint32_t* __restrict__ where, const uint64_t* __restrict__ d_n) {
   extern __shared__ uint32_t cur[];
   batch_shape(d_n, n, chunk);
   for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x)
-    cur[t] = offsets[t * gridDim.x + blockIdx.x];
+    cur[t] = static_cast<uint32_t>(range[t]) + offsets[t * gridDim.x + blockIdx.x];
   __syncthreads();
   const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * chunk;
   const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
@@ -117,12 +134,15 @@ int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* 
                      const uint64_t* d_n) {
   if (T == 0 || T > 255 || G == 0 || n >= (uint64_t(1) << 32)) return PLANB_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();   // the check below is about these launches only
   const uint64_t chunk = n ? (n + G - 1) / G : 1;
   const size_t sh = (T + 1) * sizeof(uint32_t);
+  uint64_t* totals = d_range + (T + 2);   // T + 1 words of scratch after the range
   mt_hist_kernel<<<G, 256, sh, st>>>(d_tid, n, T, chunk, d_counts, d_n);
-  mt_scan_kernel<<<1, 256, 0, st>>>(d_counts, G, T, d_range);
-  mt_scatter_kernel<<<G, 256, sh, st>>>(d_hi, d_lo, d_tid, n, T, chunk, d_counts, d_bhi, d_blo,
-                                        d_where, d_n);
+  mt_rowscan_kernel<<<T + 1, kScanThreads, 0, st>>>(d_counts, G, totals);
+  mt_tablescan_kernel<<<1, 256, 0, st>>>(totals, T, d_range);
+  mt_scatter_kernel<<<G, 256, sh, st>>>(d_hi, d_lo, d_tid, n, T, chunk, d_counts, d_range, d_bhi,
+                                        d_blo, d_where, d_n);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 
@@ -130,6 +150,7 @@ int launch_gather(const uint8_t* d_tid, const uint32_t* d_where, const uint16_t*
                   uint32_t T, uint32_t G, uint16_t* d_out, void* stream, const uint64_t* d_n) {
   const uint64_t want = (static_cast<uint64_t>(n) + 255) / 256;
   const unsigned blocks = static_cast<unsigned>(want < G ? (want ? want : 1) : G);
+  cudaGetLastError();
   mt_gather_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_tid, d_where, d_bres,
                                                                           n, T, d_out, d_n);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;

@@ -204,9 +204,34 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   void* stream, const uint64_t* d_range = nullptr,
                   const uint32_t* d_perm = nullptr);
 
+// One table of the single-launch multi-table kernel (F8X128 or F8V7 tables of the hybrid kernel).
+struct MultiDesc {
+  const void* nodes;         // node array
+  const uint64_t* sidx;      // top-of-tree index, (hi, lo) per entry
+  const uint16_t* values;    // next hop per interval
+  uint32_t sidx_n;           // index entries
+  uint32_t sidx_node;        // first node of level S
+  uint32_t internal_nodes;
+  uint32_t db;               // levels below the index, read from L2 (D - S)
+  uint32_t packed;           // F8V7: next hops in the leaf line
+  uint32_t pad;
+  uint64_t n_intervals;
+};
+
+// The single-launch multi-table kernel: raises its shared-memory limit to the device maximum and
+// returns the persistent grid size for smem_bytes of dynamic shared memory per CTA.
+int multi_persistent_setup(int device, size_t smem_bytes, int* ctas);
+// Looks up the bucketed addresses [0, range[T]) of d_hi/d_lo against table t of d_desc for the
+// addresses in [range[t], range[t+1]), writing each result at its bucketed position in d_out.
+// smem_bytes: 8 * (T + 3 rounded to even) + 8 * (largest sidx_n), at most the device maximum.
+int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t* d_range,
+                            const uint64_t* d_hi, const uint64_t* d_lo, uint16_t* d_out,
+                            uint32_t* d_status, int ctas, size_t smem_bytes, void* stream);
+
 // Multi-table bucketing (multi.cu): groups n addresses by their u8 table id (ids >= T form one
 // extra segment) into d_bhi/d_blo, table-major, with d_where[i] = the bucketed position of address
-// i; d_range[t] .. d_range[t+1] bound table t's segment. d_counts holds (T+1) x G words. n < 2^32.
+// i; d_range[t] .. d_range[t+1] bound table t's segment; d_range has room for 2T + 3 words (the
+// last T + 1 are scratch). d_counts holds (T+1) x G words. n < 2^32.
 // With d_n the kernels read the batch size from device memory (n then only bounds it).
 int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
                      uint32_t T, uint32_t G, uint32_t* d_counts, uint64_t* d_range,

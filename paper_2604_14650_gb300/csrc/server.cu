@@ -17,6 +17,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -88,11 +89,18 @@ struct planb_server {
   std::vector<float> lat_us;           // ring of recent request latencies
   size_t lat_pos = 0, lat_count = 0;
   int last_error = PLANB_OK;
+  char last_detail[512] = "";
 };
 
 namespace {
 
 constexpr size_t kLatRing = size_t(1) << 20;
+
+// with m->mu held: remember a failure and where it happened
+void note_error(planb_server* m, int rc, const char* where, const char* why) {
+  m->last_error = rc;
+  snprintf(m->last_detail, sizeof(m->last_detail), "%s: %s", where, why ? why : "");
+}
 
 void free_slot(Slot& s) {
   if (s.mt) planb_multi_destroy(s.mt);
@@ -158,6 +166,7 @@ void dispatcher_main(planb_server* m) {
     for (Slot& s : m->slots)
       if (s.busy && cudaEventQuery(s.ev) != cudaErrorNotReady) {
         const cudaError_t e = cudaEventSynchronize(s.ev);
+        if (e != cudaSuccess) note_error(m, PLANB_ECUDA, "batch completion", cudaGetErrorString(e));
         complete_slot(m, s, e == cudaSuccess ? PLANB_OK : PLANB_ECUDA);
       }
     if (m->queue.empty()) {
@@ -190,7 +199,7 @@ void dispatcher_main(planb_server* m) {
       const int rc = planb_multi_create(m->tables.data(), static_cast<uint32_t>(m->tables.size()),
                                         m->o.max_batch, 0, &slot->mt);
       if (rc) {
-        m->last_error = rc;
+        note_error(m, rc, "slot table group", planb_last_error());
         while (!m->queue.empty()) {
           m->queue.front()->status = rc;
           m->queue.pop_front();
@@ -232,11 +241,14 @@ void dispatcher_main(planb_server* m) {
              cudaSuccess ||
          cudaEventRecord(slot->ev, st) != cudaSuccess))
       rc = PLANB_ECUDA;
+    const char* why = rc == PLANB_OK ? "" : (ok ? planb_last_error() : "staging copy");
+    char why_copy[256];
+    snprintf(why_copy, sizeof(why_copy), "%s", why);
     lk.lock();
     m->batches++;
     slot->busy = true;
     if (rc != PLANB_OK) {
-      m->last_error = rc;
+      note_error(m, rc, "batch launch", why_copy);
       cudaStreamSynchronize(st);
       complete_slot(m, *slot, rc);
     }
@@ -267,9 +279,11 @@ void updater_main(planb_server* m) {
       const int rc = planb_update(tabs[w.first], w.second.ins.data(), w.second.ins.size(),
                                   w.second.wd.data(), w.second.wd.size(), nullptr);
       const double ms = std::chrono::duration<double, std::milli>(clock_t_::now() - t0).count();
+      char why[256];
+      snprintf(why, sizeof(why), "%s", rc ? planb_last_error() : "");
       std::lock_guard<std::mutex> lk(m->mu);
       if (rc) {
-        m->last_error = rc;
+        note_error(m, rc, "route update", why);
       } else {
         m->updates += w.second.ins.size() + w.second.wd.size();
         m->update_batches++;
@@ -438,6 +452,13 @@ int planb_server_stats(planb_server* m, planb_server_stats_t* out) {
     out->p99_us = pct(0.99);
     out->max_us = *std::max_element(lat.begin(), lat.end());
   }
+  return PLANB_OK;
+}
+
+int planb_server_error_detail(planb_server* m, char* buf, size_t cap) {
+  if (!m || !buf || cap == 0) return PLANB_EINVAL;
+  std::lock_guard<std::mutex> lk(m->mu);
+  snprintf(buf, cap, "%s", m->last_detail);
   return PLANB_OK;
 }
 

@@ -1,6 +1,7 @@
 """Multi-table (VRF) lookups: each address carries a u8 table id; one captured graph buckets the
-batch by table, runs one lookup per table and writes results back in input order. Checked
-bit-exactly against the oracle of each table."""
+batch by table, looks every group up — in one persistent launch when every table uses the hybrid
+kernel, else one launch per table — and gathers results back into input order. Checked bit-exactly
+against the oracle of each table, in both launch modes, captured and direct."""
 import numpy as np
 import pytest
 
@@ -52,9 +53,11 @@ def expected(fibs, tid, xh, xl):
     return want
 
 
+@pytest.mark.parametrize("per_table", [False, True])
 @pytest.mark.parametrize("graph", [False, True])
-@pytest.mark.parametrize("kinds", [("f8x128", "hybrid"), ("f8v7", "hybrid"), ("mixed", None)])
-def test_multi_table_parity_and_replay(kinds, graph):
+@pytest.mark.parametrize("kinds", [("f8x128", "hybrid"), ("f8v7", "hybrid"), ("mixed_hybrid", None),
+                                   ("mixed", None)])
+def test_multi_table_parity_and_replay(kinds, graph, per_table):
     sizes = [500, 3000, 20_000, 1000, 60_000, 7, 12_000, 2500]
     fibs_in, tid, xh, xl = workload(sizes, 600_000, seed=41)
     want = expected(fibs_in, tid, xh, xl)
@@ -62,9 +65,15 @@ def test_multi_table_parity_and_replay(kinds, graph):
                ("f16hi", "coop")]
     fibs = []
     for t, f in enumerate(fibs_in):
-        fmt, ker = kinds if kinds[0] != "mixed" else choices[t % len(choices)]
-        fibs.append(pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=ker))
-    with pb.MultiFib(fibs, max_batch=1 << 20, graph=graph) as mt:
+        if kinds[0] == "mixed":
+            fmt, ker = choices[t % len(choices)]
+        elif kinds[0] == "mixed_hybrid":          # both hybrid formats, several index depths
+            fmt, ker = choices[t % 2]
+        else:
+            fmt, ker = kinds
+        smem = {2: 0, 5: 1}.get(t, -1) if kinds[0] == "mixed_hybrid" else -1
+        fibs.append(pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=ker, smem_levels=smem))
+    with pb.MultiFib(fibs, max_batch=1 << 20, graph=graph, per_table=per_table) as mt:
         dh, dl, dt = dev(xh), dev(xl), dev(tid, np.uint8)
         out = torch.empty(tid.size, dtype=torch.int16, device="cuda")
         for _ in range(3):                     # first call captures the graph, the others replay
@@ -82,11 +91,12 @@ def test_multi_table_parity_and_replay(kinds, graph):
         f.close()
 
 
-def test_multi_table_sees_updates():
+@pytest.mark.parametrize("per_table", [False, True])
+def test_multi_table_sees_updates(per_table):
     sizes = [5000, 20_000, 800]
     fibs_in, tid, xh, xl = workload(sizes, 300_000, seed=51)
     fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh) for f in fibs_in]
-    with pb.MultiFib(fibs, max_batch=300_000) as mt:
+    with pb.MultiFib(fibs, max_batch=300_000, per_table=per_table) as mt:
         dh, dl, dt = dev(xh), dev(xl), dev(tid, np.uint8)
         out = mt.lookup(dh, dl, dt)
         torch.cuda.synchronize()
@@ -110,3 +120,17 @@ def test_learned_tables_cannot_join():
     with pb.Fib(f.hi, f.lo, f.len, f.nh, kernel="learned") as fib:
         with pytest.raises(pb.PlanbError):
             pb.MultiFib([fib], max_batch=1000)
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 1000])
+def test_multi_table_tiny_batches(n):
+    """Batches smaller than the persistent grid: most CTAs get no addresses."""
+    sizes = [3000, 40_000, 100]
+    fibs_in, tid, xh, xl = workload(sizes, n, seed=61)
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh) for f in fibs_in]
+    with pb.MultiFib(fibs, max_batch=4096) as mt:
+        out = mt.lookup(dev(xh), dev(xl), dev(tid, np.uint8))
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
+    for f in fibs:
+        f.close()
