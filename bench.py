@@ -539,7 +539,10 @@ def run_vrf64(args):
             mt.lookup_ptr(*args_ptr, stream)
         b.record(stream)
         stream.synchronize()
+        mode = mt.persistent
         mt.close()
+        if mode == per_table:
+            raise SystemExit(f"multi-table launch mode is not the one asked for (per_table={per_table})")
         return a.elapsed_time(b) / args.steps
 
     ms = timed(False)

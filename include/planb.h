@@ -287,6 +287,12 @@ int planb_multi_lookup_devn(planb_multi *m, const uint64_t *d_addr_hi, const uin
                             const uint8_t *d_table, const uint64_t *d_n, size_t max_n,
                             uint16_t *d_out, planb_stream_t stream);
 
+/* planb_multi_persistent — 1 when the group's lookups run as the single persistent launch (every
+ * table a hybrid F8X128/F8V7 table whose index fits one CTA's shared memory, and no
+ * PLANB_MULTI_PER_TABLE flag), 0 when each table gets its own launch. Decided at the first lookup
+ * and again whenever a table is swapped; 0 before the first lookup. Errors: PLANB_EINVAL. */
+int planb_multi_persistent(const planb_multi *m);
+
 /* planb_multi_destroy — waits for the device and frees the group (not its tables). */
 void planb_multi_destroy(planb_multi *m);
 

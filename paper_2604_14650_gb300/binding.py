@@ -105,6 +105,7 @@ _SIGS = {
     "planb_multi_create": (C.c_int, [_vp, C.c_uint32, _sz, C.c_uint32, C.POINTER(_vp)]),
     "planb_multi_lookup": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_multi_destroy": (None, [_vp]),
+    "planb_multi_persistent": (C.c_int, [_vp]),
     "planb_multi_lookup_devn": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_server_opts_default": (None, [_vp]),
     "planb_server_create": (C.c_int, [_vp, C.POINTER(_vp)]),
@@ -413,6 +414,14 @@ class MultiFib:
                                             C.c_void_p(out.data_ptr()), _stream_handle(stream)),
                "planb_multi_lookup")
         return out
+
+    @property
+    def persistent(self) -> bool:
+        """True when the lookups run as the single persistent launch over all tables."""
+        rc = self._lib.planb_multi_persistent(self._h)
+        if rc < 0:
+            _check(rc, "planb_multi_persistent")
+        return rc == 1
 
     def lookup_ptr(self, hi_ptr: int, lo_ptr: int, tid_ptr: int, n: int, out_ptr: int, stream=None):
         _check(self._lib.planb_multi_lookup(self._h, C.c_void_p(hi_ptr), C.c_void_p(lo_ptr),

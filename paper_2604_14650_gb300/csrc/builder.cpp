@@ -297,4 +297,31 @@ void fill_sidx(const Intervals& iv, const Layout& L, uint32_t S, uint64_t* out) 
   }
 }
 
+uint32_t dir_bits_for(uint64_t n) {
+  if (n == 0 || n >= 65536) return 0;
+  uint32_t lg = 0;
+  while ((uint64_t(1) << lg) < n) lg++;
+  return std::min<uint32_t>(13, std::max<uint32_t>(4, lg + 1));   // about two buckets per entry
+}
+
+DirParams dir_params(const uint64_t* sidx, uint64_t n) {
+  DirParams p;
+  p.bits = dir_bits_for(n);
+  if (!p.bits) return p;
+  const uint64_t lo = sidx[0], hi = sidx[2 * (n - 1)];
+  const uint64_t cap = uint64_t(1) << p.bits;
+  while (p.shift < 63 && (hi >> p.shift) - (lo >> p.shift) >= cap) p.shift++;
+  p.base = lo >> p.shift;
+  return p;
+}
+
+void fill_dir(const uint64_t* sidx, uint64_t n, const DirParams& p, uint16_t* dir) {
+  const uint64_t buckets = uint64_t(1) << p.bits;
+  uint64_t q = 0;
+  for (uint64_t b = 0; b <= buckets; b++) {
+    while (q < n && (sidx[2 * q] >> p.shift) - p.base < b) q++;
+    dir[b] = static_cast<uint16_t>(q);
+  }
+}
+
 }  // namespace planb

@@ -128,6 +128,7 @@ int check_device(int dev) {
 }
 
 constexpr size_t kSmemBudget = 96 * 1024;   // per CTA; two hybrid CTAs fit one SM
+constexpr size_t kDirBudget = 16 * 1024;     // the hybrid index's radix directory (2^13 + 1 u16)
 
 uint32_t auto_smem_levels(const planb::Layout& L, uint32_t format) {
   // whole tree when it is small, else the deepest prefix of levels within 64 KiB
@@ -224,7 +225,8 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                           : std::min<uint32_t>(o.smem_levels, t->L.D);
     while (s > 0 && planb::sidx_entries(t->L, s) * 8 + leaf_bytes > 200 * 1024) s--;
   } else if (kernel == planb::kHybrid) {
-    s = o.smem_levels < 0 ? auto_index_levels(t->L, kSmemBudget)
+    // the index shares the budget with its radix directory (at most 16 KB)
+    s = o.smem_levels < 0 ? auto_index_levels(t->L, kSmemBudget - kDirBudget)
                           : std::min<uint32_t>(o.smem_levels, t->L.D);
     while (s > 0 && planb::sidx_entries(t->L, s) * 8 > 200 * 1024) s--;
   } else if (kernel == planb::kFlat) {
@@ -239,12 +241,16 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   const size_t node_bytes = static_cast<size_t>(total) * 128;
   const size_t lo_bytes = format == PLANB_FMT_F16HI ? node_bytes : 0;
   const size_t sidx_bytes = ((sidx_n * 16 + 127) / 128) * 128;
+  // radix directory of the hybrid index: its size depends on the entry count only
+  planb::DirParams dp;
+  if (kernel == planb::kHybrid) dp.bits = planb::dir_bits_for(sidx_n);
+  const size_t dirb = planb::dir_bytes(dp);
   const size_t val_bytes = ((static_cast<size_t>(m) * 2 + 255) / 256) * 256;
   const size_t model_bytes =
       learned ? ((static_cast<size_t>(model_leaves) * 18 + 255) / 256) * 256 : 0;
   std::vector<uint64_t> host;
   if (!on_dev) {
-    host.resize((node_bytes + lo_bytes + sidx_bytes) / 8);
+    host.resize((node_bytes + lo_bytes + sidx_bytes + dirb) / 8);
     if (format == PLANB_FMT_F16HI)
       planb::fill_f16hi(iv, t->L, host.data(), host.data() + node_bytes / 8);
     else if (format == PLANB_FMT_F8V7)
@@ -252,6 +258,14 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
     else
       planb::fill_f8x128(iv, t->L, host.data());
     if (sidx_n) planb::fill_sidx(iv, t->L, s, host.data() + (node_bytes + lo_bytes) / 8);
+    if (dp.bits) {
+      const uint64_t* sx = host.data() + (node_bytes + lo_bytes) / 8;
+      const uint32_t bits = dp.bits;
+      dp = planb::dir_params(sx, sidx_n);
+      if (dp.bits != bits) return fail_detail(PLANB_EINVAL, "radix directory size");
+      planb::fill_dir(sx, sidx_n, dp, reinterpret_cast<uint16_t*>(
+                                          host.data() + (node_bytes + lo_bytes + sidx_bytes) / 8));
+    }
   }
   t->build_ms = ms_since(t0);
 
@@ -270,7 +284,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                               model_leaves, iters, 0.01f, 64u, t->model);
     if (rc) return rc;
   }
-  t->bytes = node_bytes + lo_bytes + sidx_bytes + val_bytes + model_bytes;
+  t->bytes = node_bytes + lo_bytes + sidx_bytes + dirb + val_bytes + model_bytes;
   if (g_inject.load() == 2) {
     g_inject.store(0);
     return PLANB_ENOMEM;
@@ -281,7 +295,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
     return PLANB_ENOMEM;
   }
   char* base = static_cast<char*>(t->mem);
-  const size_t head = node_bytes + lo_bytes + sidx_bytes;
+  const size_t head = node_bytes + lo_bytes + sidx_bytes + dirb;
   t->dump_bytes = head + m * 2;
   if (on_dev) {
     // the index region's rounding tail is zero, as in the host-filled image
@@ -297,6 +311,19 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
     if (rc) return fail_detail(rc, "device layout fill", cudaGetLastError());
     if (cudaStreamSynchronize(bs->s) != cudaSuccess)
       return fail_detail(PLANB_ECUDA, "device layout fill", cudaGetLastError());
+    if (dp.bits) {   // the directory comes from the index the device just wrote
+      std::vector<uint64_t> sx(sidx_n * 2), dh(dirb / 8, 0);
+      if (cudaMemcpy(sx.data(), base + node_bytes + lo_bytes, sidx_n * 16,
+                     cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PLANB_ECUDA;
+      const uint32_t bits = dp.bits;
+      dp = planb::dir_params(sx.data(), sidx_n);
+      if (dp.bits != bits) return fail_detail(PLANB_EINVAL, "radix directory size");
+      planb::fill_dir(sx.data(), sidx_n, dp, reinterpret_cast<uint16_t*>(dh.data()));
+      if (cudaMemcpy(base + node_bytes + lo_bytes + sidx_bytes, dh.data(), dirb,
+                     cudaMemcpyHostToDevice) != cudaSuccess)
+        return PLANB_ECUDA;
+    }
   } else if (cudaMemcpy(base, host.data(), head, cudaMemcpyHostToDevice) != cudaSuccess ||
              cudaMemcpy(base + head, iv.nh.data(), m * 2, cudaMemcpyHostToDevice) !=
                  cudaSuccess) {
@@ -318,6 +345,11 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   t->dt.sidx = sidx_n ? reinterpret_cast<const uint64_t*>(base + node_bytes + lo_bytes) : nullptr;
   t->dt.sidx_n = sidx_n;
   t->dt.sidx_node = s < t->L.D ? t->L.level_node[s] : 0;
+  t->dt.dir = dp.bits ? reinterpret_cast<const uint16_t*>(base + node_bytes + lo_bytes + sidx_bytes)
+                      : nullptr;
+  t->dt.dir_bits = dp.bits;
+  t->dt.dir_shift = dp.shift;
+  t->dt.dir_base = dp.base;
   t->dt.kernel = kernel;
   t->dt.values = reinterpret_cast<const uint16_t*>(base + head);
   t->dt.n_intervals = m;
@@ -1069,11 +1101,17 @@ int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>
     x.internal_nodes = static_cast<uint32_t>(d.internal_nodes);
     x.db = d.depth - d.smem_levels;
     x.packed = d.format == PLANB_FMT_F8V7 ? 1u : 0u;
-    x.pad = 0;
     x.n_intervals = d.n_intervals;
-    max_n = std::max<uint64_t>(max_n, d.sidx_n);
+    x.dir = d.dir;
+    x.dir_bits = d.dir_bits;
+    x.dir_shift = d.dir_shift;
+    x.dir_base = d.dir_base;
+    x.pad = 0;
+    const uint64_t need = ((d.sidx_n + 1) & ~1ull) * 8u +
+                          (d.dir_bits ? ((((1ull << d.dir_bits) + 1) + 7) & ~7ull) * 2u : 0u);
+    max_n = std::max<uint64_t>(max_n, need);
   }
-  const size_t smem = ((m->T + 3u) & ~1u) * 8u + max_n * 8u;
+  const size_t smem = ((m->T + 3u) & ~1u) * 8u + max_n;
   int ctas = 0;
   if (planb::multi_persistent_setup(m->device, smem, &ctas) != PLANB_OK) {
     cudaGetLastError();
@@ -1167,6 +1205,12 @@ int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t*
 }  // namespace
 
 extern "C" {
+
+int planb_multi_persistent(const planb_multi* m) {
+  if (!m) return PLANB_EINVAL;
+  std::lock_guard<std::mutex> lk(const_cast<planb_multi*>(m)->mu);
+  return m->persist ? 1 : 0;
+}
 
 void planb_multi_destroy(planb_multi* m) {
   if (!m) return;

@@ -64,6 +64,9 @@ struct KParams {
   const LeafModel* leaves;    // learned: leaf models (copied to shared memory)
   const uint16_t* leaf_err;   // learned: per-leaf window half-width or kLeafFallback
   LearnedParams lp;           // learned: root weights and range reduction
+  const uint16_t* dir;        // hybrid: radix directory over the index (dir_bits = 0: none)
+  uint32_t dir_bits, dir_shift;
+  uint64_t dir_base;
   const uint64_t* range;      // multi-table: device [begin, end) of this launch's addresses
   const uint32_t* perm;       // multi-table: result of address j goes to out[perm[j]]
 };
@@ -109,6 +112,38 @@ __device__ __forceinline__ uint32_t count_below(Load load, uint32_t n, uint64_t 
   }
   const ulonglong2 u = load(b);
   return b + (less128(u.x, u.y, xh, xl) ? 1u : 0u);
+}
+
+// Entries of the staged index Uh[0..N) (ascending high halves) below the address, counting an
+// entry with an equal high half by its low half (read from the global index). With a radix
+// directory the search starts in the entries of the address's bucket: entries of lower buckets
+// have smaller high halves, entries of higher buckets larger ones.
+__device__ __forceinline__ uint32_t index_count(const uint64_t* Uh, uint32_t N,
+                                                const uint16_t* Dir, uint32_t dir_bits,
+                                                uint32_t dir_shift, uint64_t dir_base,
+                                                const ulonglong2* sidx, uint64_t my_hi,
+                                                uint64_t my_lo) {
+  uint32_t lo = 0, n = N;
+  if (dir_bits) {
+    const uint64_t v = my_hi >> dir_shift;
+    uint64_t bk = v > dir_base ? v - dir_base : 0ull;
+    const uint64_t last = (1ull << dir_bits) - 1ull;
+    bk = bk < last ? bk : last;
+    lo = Dir[bk];
+    n = Dir[bk + 1] - lo;
+  }
+  uint32_t cnt = lo;
+  if (n) {
+    uint32_t b = lo;
+    while (n > 1) {
+      const uint32_t half = n >> 1;
+      b = Uh[b + half] < my_hi ? b + half : b;
+      n -= half;
+    }
+    cnt = b + (Uh[b] < my_hi ? 1u : 0u);
+  }
+  while (cnt < N && Uh[cnt] == my_hi && __ldg(&sidx[cnt].y) < my_lo) cnt++;
+  return cnt;
 }
 
 // ------------------------------------------------------------------------------- coop F8X128
@@ -250,7 +285,10 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   const uint32_t N = p.sidx_n;
   uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
   for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
-  LeafModel* Lm = reinterpret_cast<LeafModel*>(Uh + ((N + 1u) & ~1u));
+  uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((N + 1u) & ~1u));
+  const uint32_t dn = p.dir_bits ? (1u << p.dir_bits) + 1u : 0u;
+  for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(p.dir + i);
+  LeafModel* Lm = reinterpret_cast<LeafModel*>(Dir + ((dn + 7u) & ~7u));
   uint16_t* Le = reinterpret_cast<uint16_t*>(Lm + (LEARNED ? p.lp.leaves : 0u));
   if (LEARNED) {
     for (uint32_t i = threadIdx.x; i < p.lp.leaves; i += blockDim.x) {
@@ -306,16 +344,8 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
         have = ok;
       }
     }
-    if (N && !have) {
-      uint32_t b = 0, n = N;
-      while (n > 1) {
-        const uint32_t half = n >> 1;
-        b = Uh[b + half] < my_hi ? b + half : b;
-        n -= half;
-      }
-      cnt = b + (Uh[b] < my_hi ? 1u : 0u);
-      while (cnt < N && Uh[cnt] == my_hi && __ldg(&p.sidx[cnt].y) < my_lo) cnt++;
-    }
+    if (N && !have)
+      cnt = index_count(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, p.sidx, my_hi, my_lo);
     if constexpr (DB == 0) {
       uint32_t rank = cnt;
 #ifdef PLANB_BOUNDS_CHECK
@@ -329,6 +359,7 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
     } else {
       const uint32_t my_node = p.sidx_node + cnt;
       uint32_t result = 0;
+      uint64_t my_rank = 0;   // the interval index of this lane's own address
       // phase B: the last DB levels from L2, 8-lane groups, kRounds addresses per group at once
 #pragma unroll
       for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
@@ -395,11 +426,12 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
               rank = 0;
             }
 #endif
-            const uint32_t v = __ldg(p.values + rank);
-            if (j == r0 + i) result = v;
+            if (j == r0 + i) my_rank = rank;
           }
         }
       }
+      // each lane fetches its own next hop: one load per lane rather than one per group lane
+      if (!PACKED) result = __ldg(p.values + my_rank);
       if (ok) store_out<MULTI>(p, seg.off + mine, static_cast<uint16_t>(result));
     }
   }
@@ -438,7 +470,8 @@ __global__ void __launch_bounds__(256) lookup_flat(const KParams p) {
 constexpr int kMultiMaxDb = 4;
 
 template <int DB, bool PACKED>   // DB < 0: run-time depth d.db
-__device__ __forceinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh, uint64_t s0,
+__device__ __forceinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
+                                            const uint16_t* Dir, uint64_t s0,
                                             uint64_t s1, const uint64_t* __restrict__ xhi,
                                             const uint64_t* __restrict__ xlo,
                                             uint16_t* __restrict__ out, uint32_t* status) {
@@ -457,17 +490,8 @@ __device__ __forceinline__ void multi_tiles(const MultiDesc& d, const uint64_t* 
     const bool ok = mine < s1;
     const uint64_t my_hi = ok ? xhi[mine] : 0ull;
     const uint64_t my_lo = ok ? xlo[mine] : 0ull;
-    uint32_t cnt = 0;
-    if (N) {
-      uint32_t b = 0, n = N;
-      while (n > 1) {
-        const uint32_t half = n >> 1;
-        b = Uh[b + half] < my_hi ? b + half : b;
-        n -= half;
-      }
-      cnt = b + (Uh[b] < my_hi ? 1u : 0u);
-      while (cnt < N && Uh[cnt] == my_hi && __ldg(&sidx[cnt].y) < my_lo) cnt++;
-    }
+    const uint32_t cnt =
+        N ? index_count(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, sidx, my_hi, my_lo) : 0u;
     uint32_t result = 0;
     if (db == 0) {
       uint32_t rank = cnt;
@@ -480,6 +504,7 @@ __device__ __forceinline__ void multi_tiles(const MultiDesc& d, const uint64_t* 
       result = __ldg(d.values + rank);
     } else {
       const uint32_t my_node = d.sidx_node + cnt;
+      uint64_t my_rank = 0;
 #pragma unroll
       for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
         uint64_t qh[kRounds];
@@ -492,7 +517,7 @@ __device__ __forceinline__ void multi_tiles(const MultiDesc& d, const uint64_t* 
           nd[i] = __shfl_sync(kFull, my_node, src);
         }
 #pragma unroll
-        for (uint32_t l = 0; l < (DB >= 0 ? static_cast<uint32_t>(DB) : db); l++) {
+        for (uint32_t l = 0; l < db; l++) {
 #pragma unroll
           for (int i = 0; i < kRounds; i++)
             key[i] = __ldg(nodes + static_cast<uint64_t>(nd[i]) * 8u + j);
@@ -542,11 +567,11 @@ __device__ __forceinline__ void multi_tiles(const MultiDesc& d, const uint64_t* 
               rank = 0;
             }
 #endif
-            const uint32_t v = __ldg(d.values + rank);
-            if (j == r0 + i) result = v;
+            if (j == r0 + i) my_rank = rank;
           }
         }
       }
+      if (!PACKED) result = __ldg(d.values + my_rank);
     }
     if (ok) out[mine] = static_cast<uint16_t>(result);
   }
@@ -578,25 +603,28 @@ __global__ void __launch_bounds__(512, 2)
     __syncthreads();
     const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
     for (uint32_t i = threadIdx.x; i < d.sidx_n; i += blockDim.x) Uh[i] = __ldg(&sidx[i].x);
+    uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((d.sidx_n + 1u) & ~1u));
+    const uint32_t dn = d.dir_bits ? (1u << d.dir_bits) + 1u : 0u;
+    for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(d.dir + i);
     __syncthreads();
     const uint32_t sel = d.db <= static_cast<uint32_t>(kMultiMaxDb) ? d.db : 15u;
     if (d.packed) {
       switch (sel) {
-        case 0: multi_tiles<0, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        case 1: multi_tiles<1, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        case 2: multi_tiles<2, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        case 3: multi_tiles<3, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        case 4: multi_tiles<4, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        default: multi_tiles<-1, true>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 0: multi_tiles<0, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        case 1: multi_tiles<1, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        case 2: multi_tiles<2, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        case 3: multi_tiles<3, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        case 4: multi_tiles<4, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        default: multi_tiles<-1, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
       }
     } else {
       switch (sel) {
-        case 0: multi_tiles<0, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        case 1: multi_tiles<1, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        case 2: multi_tiles<2, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        case 3: multi_tiles<3, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        case 4: multi_tiles<4, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
-        default: multi_tiles<-1, false>(d, Uh, s0, s1, xhi, xlo, out, status); break;
+        case 0: multi_tiles<0, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        case 1: multi_tiles<1, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        case 2: multi_tiles<2, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        case 3: multi_tiles<3, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        case 4: multi_tiles<4, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        default: multi_tiles<-1, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
       }
     }
   }
@@ -667,6 +695,19 @@ size_t smem_bytes_for(const Layout& L, uint32_t format, uint32_t levels) {
   return static_cast<size_t>(nodes) * 128u;  // both formats: 128-byte nodes
 }
 
+// Room for dynamic shared memory of a kernel: the device's opt-in maximum per block less the
+// kernel's static shared memory.
+int dynamic_smem_limit(const void* fn, int device, int* limit) {
+  int optin = 0;
+  cudaFuncAttributes a{};
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+          cudaSuccess ||
+      cudaFuncGetAttributes(&a, fn) != cudaSuccess)
+    return PLANB_ECUDA;
+  *limit = optin - static_cast<int>(a.sharedSizeBytes);
+  return *limit > 0 ? PLANB_OK : PLANB_EINVAL;
+}
+
 int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, LaunchCfg& cfg) {
   KernelFn fn = kernel_for(t);
   if (!fn) return PLANB_EINVAL;
@@ -678,6 +719,7 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
   cfg.threads = threads;
   if (hyb)
     cfg.smem_bytes = static_cast<size_t>((t.sidx_n + 1) & ~1ull) * 8u +
+                     (t.dir_bits ? ((((1u << t.dir_bits) + 1u) + 7u) & ~7u) * 2u : 0u) +
                      (t.kernel == kLearned ? static_cast<size_t>(t.lp.leaves) * 18u : 0u);
   else if (t.kernel == kFlat && f8)
     cfg.smem_bytes = 0;
@@ -686,14 +728,13 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
   // The dynamic shared-memory limit is a property of the kernel function, which tables of other
   // sizes share: raise it once to the device's opt-in maximum rather than to this table's need
   // (a later, smaller table would otherwise lower it under an earlier one).
-  int optin = 0;
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
-    return PLANB_ECUDA;
-  if (cfg.smem_bytes > static_cast<size_t>(optin)) return PLANB_EINVAL;
   for (KernelFn f : {fn, (t.kernel == kHybrid) ? kernel_for(t, true) : nullptr}) {
     if (!f) continue;
+    int limit = 0;
+    if (int rc = dynamic_smem_limit(reinterpret_cast<const void*>(f), device, &limit)) return rc;
+    if (cfg.smem_bytes > static_cast<size_t>(limit)) return PLANB_EINVAL;
     if (cudaFuncSetAttribute(reinterpret_cast<const void*>(f),
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess)
       return PLANB_ECUDA;
   }
   int sms = 0, per_sm = 0;
@@ -738,6 +779,10 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   p.leaves = t.leaves;
   p.leaf_err = t.leaf_err;
   p.lp = t.lp;
+  p.dir = t.dir;
+  p.dir_bits = t.dir_bits;
+  p.dir_shift = t.dir_shift;
+  p.dir_base = t.dir_base;
   p.range = d_range;
   p.perm = d_perm;
   uint64_t blocks;
@@ -755,14 +800,13 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
 }
 
 int multi_persistent_setup(int device, size_t smem_bytes, int* ctas) {
-  int optin = 0, sms = 0, per_sm = 0;
+  int limit = 0, sms = 0, per_sm = 0;
   const void* fn = reinterpret_cast<const void*>(lookup_multi_persistent);
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
-          cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+  if (int rc = dynamic_smem_limit(fn, device, &limit)) return rc;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
     return PLANB_ECUDA;
-  if (smem_bytes > static_cast<size_t>(optin)) return PLANB_EINVAL;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess)
+  if (smem_bytes > static_cast<size_t>(limit)) return PLANB_EINVAL;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess)
     return PLANB_ECUDA;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, smem_bytes) != cudaSuccess)
     return PLANB_ECUDA;

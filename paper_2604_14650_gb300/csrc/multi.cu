@@ -38,9 +38,17 @@ __global__ void mt_hist_kernel(const uint8_t* __restrict__ tid, uint64_t n, uint
   __syncthreads();
   const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * chunk;
   const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
-  for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-    const uint32_t t = tid[i];
-    atomicAdd(&h[t < T ? t : T], 1u);
+  const uint32_t lane = threadIdx.x & 31u;
+  // every lane of the block runs the same trip count so the warp match sees the whole warp
+  for (uint64_t i0 = b0; i0 < b1; i0 += blockDim.x) {
+    const uint64_t i = i0 + threadIdx.x;
+    uint32_t t = 0xFFFFu;
+    if (i < b1) {
+      const uint32_t t0 = tid[i];
+      t = t0 < T ? t0 : T;
+    }
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, t);
+    if (i < b1 && lane == __ffs(peers) - 1u) atomicAdd(&h[t], __popc(peers));
   }
   __syncthreads();
   for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) counts[t * gridDim.x + blockIdx.x] = h[t];
@@ -91,25 +99,88 @@ __global__ void mt_tablescan_kernel(const uint64_t* __restrict__ totals, uint32_
   if (t == 0) range[T + 1] = all;
 }
 
-__global__ void mt_scatter_kernel(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo,
-                                  const uint8_t* __restrict__ tid, uint64_t n, uint32_t T,
-                                  uint64_t chunk, const uint32_t* __restrict__ offsets,
-                                  const uint64_t* __restrict__ range,
-                                  uint64_t* __restrict__ bhi, uint64_t* __restrict__ blo,
-                                  uint32_t* __restrict__ where, const uint64_t* __restrict__ d_n) {
-  extern __shared__ uint32_t cur[];
+// The scatter works through its chunk in tiles of kTile addresses: the tile is ranked per table
+// in shared memory (lanes with the same table are grouped by a warp match, so one shared atomic
+// serves the group), staged in table order, and written out as one contiguous run per table, so
+// the global writes are coalesced; each address's bucketed position goes to where[i] in input
+// order. Positions within one table's run follow the atomics' order, not the input order: the
+// recorded positions make the order immaterial.
+constexpr int kScatterThreads = 256;
+constexpr int kScatterItems = 8;
+constexpr int kTile = kScatterThreads * kScatterItems;
+
+__global__ void __launch_bounds__(kScatterThreads)
+    mt_scatter_kernel(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo,
+                      const uint8_t* __restrict__ tid, uint64_t n, uint32_t T, uint64_t chunk,
+                      const uint32_t* __restrict__ offsets, const uint64_t* __restrict__ range,
+                      uint64_t* __restrict__ bhi, uint64_t* __restrict__ blo,
+                      uint32_t* __restrict__ where, const uint64_t* __restrict__ d_n) {
+  typedef cub::BlockScan<uint32_t, kScatterThreads> Scan;
+  __shared__ typename Scan::TempStorage scan_tmp;
+  __shared__ uint32_t cur[256], cnt[256], base[256];
+  __shared__ uint64_t s_hi[kTile], s_lo[kTile];
+  __shared__ uint8_t s_t[kTile];
   batch_shape(d_n, n, chunk);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt_mask = (1u << lane) - 1u;
   for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x)
     cur[t] = static_cast<uint32_t>(range[t]) + offsets[t * gridDim.x + blockIdx.x];
-  __syncthreads();
   const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * chunk;
   const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
-  for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-    const uint32_t t0 = tid[i];
-    const uint32_t pos = atomicAdd(&cur[t0 < T ? t0 : T], 1u);
-    bhi[pos] = hi[i];
-    blo[pos] = lo[i];
-    where[i] = pos;
+  for (uint64_t tb = b0; tb < b1; tb += kTile) {
+    for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) cnt[t] = 0;
+    __syncthreads();
+    uint32_t tt[kScatterItems], rank[kScatterItems];
+    uint64_t vh[kScatterItems], vl[kScatterItems];
+#pragma unroll
+    for (int k = 0; k < kScatterItems; k++) {
+      const uint64_t e = tb + static_cast<uint64_t>(k) * kScatterThreads + threadIdx.x;
+      const bool ok = e < b1;
+      uint32_t t = 0xFFFFu;   // no address: a group of its own that takes no slot
+      if (ok) {
+        const uint32_t t0 = tid[e];
+        t = t0 < T ? t0 : T;
+        vh[k] = hi[e];
+        vl[k] = lo[e];
+      }
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, t);
+      const uint32_t leader = __ffs(peers) - 1u;
+      uint32_t first = 0;
+      if (ok && lane == leader) first = atomicAdd(&cnt[t], __popc(peers));
+      first = __shfl_sync(0xFFFFFFFFu, first, leader);
+      tt[k] = t;
+      rank[k] = first + __popc(peers & lt_mask);
+    }
+    __syncthreads();
+    {
+      uint32_t v = threadIdx.x <= T ? cnt[threadIdx.x] : 0u, excl = 0;
+      Scan(scan_tmp).ExclusiveSum(v, excl);
+      if (threadIdx.x <= T) base[threadIdx.x] = excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScatterItems; k++) {
+      const uint64_t e = tb + static_cast<uint64_t>(k) * kScatterThreads + threadIdx.x;
+      if (e < b1) {
+        const uint32_t t = tt[k];
+        const uint32_t slot = base[t] + rank[k];
+        s_hi[slot] = vh[k];
+        s_lo[slot] = vl[k];
+        s_t[slot] = static_cast<uint8_t>(t);
+        where[e] = cur[t] + rank[k];
+      }
+    }
+    __syncthreads();
+    const uint32_t m = static_cast<uint32_t>(b1 - tb < kTile ? b1 - tb : kTile);
+    for (uint32_t slot = threadIdx.x; slot < m; slot += blockDim.x) {
+      const uint32_t t = s_t[slot];
+      const uint32_t pos = cur[t] + (slot - base[t]);
+      bhi[pos] = s_hi[slot];
+      blo[pos] = s_lo[slot];
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) cur[t] += cnt[t];
+    // the next tile's first barrier orders these updates before their next use
   }
 }
 
@@ -141,8 +212,8 @@ int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* 
   mt_hist_kernel<<<G, 256, sh, st>>>(d_tid, n, T, chunk, d_counts, d_n);
   mt_rowscan_kernel<<<T + 1, kScanThreads, 0, st>>>(d_counts, G, totals);
   mt_tablescan_kernel<<<1, 256, 0, st>>>(totals, T, d_range);
-  mt_scatter_kernel<<<G, 256, sh, st>>>(d_hi, d_lo, d_tid, n, T, chunk, d_counts, d_range, d_bhi,
-                                        d_blo, d_where, d_n);
+  mt_scatter_kernel<<<G, kScatterThreads, 0, st>>>(d_hi, d_lo, d_tid, n, T, chunk, d_counts,
+                                                    d_range, d_bhi, d_blo, d_where, d_n);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

@@ -165,6 +165,22 @@ void fill_f16hi(const Intervals& iv, const Layout& L, uint64_t* node_hi, uint64_
 uint64_t sidx_entries(const Layout& L, uint32_t S);
 void fill_sidx(const Intervals& iv, const Layout& L, uint32_t S, uint64_t* out /* 2 per entry */);
 
+// Radix directory over the high halves of the top-of-tree index, so that a lookup's search of
+// the index starts inside the few entries that share its leading bits: entry q falls in bucket
+// (hi_q >> shift) - base, and dir[b] (b = 0 .. 2^bits) is the number of entries in buckets below
+// b. shift is the smallest that puts every entry in one of 2^bits buckets; bits = 0 means no
+// directory (an empty index, or one too long for 16-bit positions).
+struct DirParams {
+  uint32_t bits = 0, shift = 0;
+  uint64_t base = 0;
+};
+uint32_t dir_bits_for(uint64_t n);   // the directory size for an index of n entries
+DirParams dir_params(const uint64_t* sidx /* 2 per entry, ascending */, uint64_t n);
+void fill_dir(const uint64_t* sidx, uint64_t n, const DirParams& p, uint16_t* dir);
+inline size_t dir_bytes(const DirParams& p) {
+  return p.bits ? ((((size_t(1) << p.bits) + 1) * 2 + 127) / 128) * 128 : 0;
+}
+
 // ------------------------------------------------------------------------- device side
 
 // Everything a lookup kernel needs about one table (device pointers).
@@ -175,6 +191,9 @@ struct DevTable {
   const uint64_t* sidx;     // hybrid: top-of-tree index, (hi, lo) per entry
   uint64_t sidx_n;          // entries in sidx
   uint64_t sidx_node;       // first node of level S (where the hybrid's per-group phase starts)
+  const uint16_t* dir;      // hybrid: radix directory over the index (dir_bits = 0: none)
+  uint32_t dir_bits, dir_shift;
+  uint64_t dir_base;
   uint32_t kernel;          // Kernel
   const uint64_t* nodes_lo; // F16HI: low halves, same shape; else null
   const uint16_t* values;   // next hop per interval, n_intervals entries
@@ -214,8 +233,12 @@ struct MultiDesc {
   uint32_t internal_nodes;
   uint32_t db;               // levels below the index, read from L2 (D - S)
   uint32_t packed;           // F8V7: next hops in the leaf line
-  uint32_t pad;
+  uint32_t dir_bits;         // radix directory over the index (0: none)
   uint64_t n_intervals;
+  const uint16_t* dir;
+  uint64_t dir_base;
+  uint32_t dir_shift;
+  uint32_t pad;
 };
 
 // The single-launch multi-table kernel: raises its shared-memory limit to the device maximum and
@@ -223,7 +246,8 @@ struct MultiDesc {
 int multi_persistent_setup(int device, size_t smem_bytes, int* ctas);
 // Looks up the bucketed addresses [0, range[T]) of d_hi/d_lo against table t of d_desc for the
 // addresses in [range[t], range[t+1]), writing each result at its bucketed position in d_out.
-// smem_bytes: 8 * (T + 3 rounded to even) + 8 * (largest sidx_n), at most the device maximum.
+// smem_bytes: 8 * (T + 3 rounded to even) + the largest over the tables of 8 * sidx_n rounded up
+// to 16 bytes plus 2 * (2^dir_bits + 1), at most the device maximum.
 int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t* d_range,
                             const uint64_t* d_hi, const uint64_t* d_lo, uint16_t* d_out,
                             uint32_t* d_status, int ctas, size_t smem_bytes, void* stream);

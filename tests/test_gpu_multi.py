@@ -81,6 +81,8 @@ def test_multi_table_parity_and_replay(kinds, graph, per_table):
             mt.lookup(dh, dl, dt, out=out)
             torch.cuda.synchronize()
             assert np.array_equal(out.cpu().numpy().view(np.uint16), want)
+        # every table on the hybrid kernel shares the single persistent launch unless asked not to
+        assert mt.persistent == (kinds[0] != "mixed" and not per_table)
         # a smaller batch (new capture) and an empty one
         k = 12_345
         small = mt.lookup(dh[:k], dl[:k], dt[:k])
@@ -131,6 +133,7 @@ def test_multi_table_tiny_batches(n):
     with pb.MultiFib(fibs, max_batch=4096) as mt:
         out = mt.lookup(dev(xh), dev(xl), dev(tid, np.uint8))
         torch.cuda.synchronize()
+        assert mt.persistent
         assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
     for f in fibs:
         f.close()
