@@ -62,6 +62,10 @@ def parse():
                          "1k prefixes, 10^6 lookups; serve: the serving engine under Poisson "
                          "arrivals and route updates; build: build and rebuild times, host "
                          "builder against the device builder")
+    ap.add_argument("--serve-warmup", type=float, default=1.0,
+                    help="serve: seconds of the same load before the measured phase")
+    ap.add_argument("--per-table", action="store_true",
+                    help="serve: one lookup launch per table instead of the single persistent one")
     ap.add_argument("--builder", default="host", choices=["host", "device"],
                     help="where tables are built (and rebuilt by updates) in serve")
     ap.add_argument("--tables", type=int, default=64)
@@ -164,11 +168,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from an ncu capture committed under profiles/, if the kernel source
-    has not changed since."""
+def recorded_counters(kernel: str):
+    """Per-lookup counters of a kernel from the ncu capture summarised in profiles/traffic.json,
+    if the kernel's source has not changed since the capture (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2604_14650_gb300", "csrc", "lookup.cu")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -176,11 +179,11 @@ def recorded_traffic(kernel: str):
     e = rec.get(kernel)
     if not e:
         return None
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
-    if e.get("source_sha256") != sha:
-        return None
-    return e.get("dram_bytes_per_launch")
+    h = hashlib.sha256()
+    for src in e["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    return e if e.get("sources_sha256") == h.hexdigest() else None
 
 
 # ----------------------------------------------------------------------------- workload
@@ -425,15 +428,33 @@ def run_planb(args):
 
     peak, peak_kind = measured_peaks()
     kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
-    kernel = {"hybrid": f"lookup_hybrid<{st['depth'] - st['smem_levels']}>",
-              "flat": "lookup_flat"}.get(kname, f"lookup_coop_{'f16' if args.format == 'f16hi' else 'f8'}<{st['depth']}>")
+    # the kernel's name as ncu prints it
     if kname == "hybrid":
-        kernel = f"lookup_hybrid<{st['depth'] - st['smem_levels']},{'true' if args.format == 'f8v7' else 'false'}>"
+        kernel = (f"lookup_hybrid<{st['depth'] - st['smem_levels']}, "
+                  f"{1 if args.format == 'f8v7' else 0}, 0, 0>")
+    elif kname == "flat":
+        kernel = "lookup_flat"
+    else:
+        kernel = f"lookup_coop_{'f16' if args.format == 'f16hi' else 'f8'}<{st['depth']}>"
     achieved = HBM_BYTES_PER_LOOKUP * n / avg_launch_s / 1e9
+    rec = recorded_counters(kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(kernel),
+                "frac": achieved / peak,
+                "traffic": rec["dram_bytes_per_lookup"] * n if rec else None,
                 "kernel": kernel, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": HBM_BYTES_PER_LOOKUP * n}
+    # the other roofs of the descent: L2 -> SM bytes and the L1/LSU data pipe, per lookup from the
+    # ncu capture in profiles/ (same kernel source), at this run's lookup rate
+    roofs = None
+    if rec:
+        rate = n / avg_launch_s
+        l2 = rec["l2_bytes_per_lookup"] * rate / 1e9
+        roofs = {"l2": {"achieved": l2, "peak": rec["l2_peak_gbs"], "unit": "GB/s",
+                        "frac": l2 / rec["l2_peak_gbs"] if rec["l2_peak_gbs"] else None,
+                        "bytes_per_lookup": rec["l2_bytes_per_lookup"]},
+                 "l1_lsu_pipe": {"frac_at_capture": rec["l1_lsu_wavefronts_pct_of_peak"] / 100,
+                                 "smem_wavefronts_per_lookup": rec["smem_wavefronts_per_lookup"]},
+                 "source": "profiles/traffic.json (ncu --set full capture of this kernel)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -447,6 +468,7 @@ def run_planb(args):
                    "l2": "inputs (16 B x lookups) larger than L2; no flush", "seed": args.seed,
                    "parallelism": f"dp{world} (table replicated, addresses sharded)"},
         "roofline": roofline,
+        "roofs": roofs,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "latency": lat,
@@ -500,7 +522,8 @@ def run_vrf64(args):
     d_lo = torch.from_numpy(xl.view(np.int64)).cuda()
     d_t = torch.from_numpy(tid).cuda()
     d_out = torch.empty(n, dtype=torch.int16, device="cuda")
-    tuner = Autotuner(cache_path=os.path.join(ROOT, "gpurun_out", "autotune.json"))
+    # tuned within the configurations the single persistent launch runs
+    tuner = Autotuner(cache_path=os.path.join(ROOT, "gpurun_out", "autotune.json"), persistent=True)
     choices, fibs = [], []
     t0 = time.perf_counter()
     for t, f in enumerate(fibs_in):
@@ -645,7 +668,7 @@ def run_serve(args):
     offs = rng.integers(0, pool - 65536, nreq)
     gaps = rng.exponential(1.0 / args.rate, nreq)
     budget = int(sum(f.stats()["node_bytes"] + f.stats()["value_bytes"] for f in fibs) * 1.05)
-    srv = pb.Server(slots=4, max_batch=1 << 18, mem_budget=budget)
+    srv = pb.Server(slots=4, max_batch=1 << 18, mem_budget=budget, per_table=args.per_table)
     try:
         return _serve_loop(args, srv, fibs, fibs_in, pools, nreq, tabs, lens, offs, gaps, rng,
                            budget)
@@ -677,32 +700,43 @@ def _serve_loop(args, srv, fibs, fibs_in, pools, nreq, tabs, lens, offs, gaps, r
 
     ut = threading.Thread(target=updater, daemon=True)
     ut.start()
-    t0 = time.perf_counter()
-    nxt = t0
-    pos = 0
-    for i in range(nreq):
-        nxt += gaps[i]
-        while time.perf_counter() < nxt:
-            pass
-        n = int(lens[i])
-        if pos + n > out_pool.size:
-            pos = 0
-        h, l = pools[tabs[i]]
-        o = int(offs[i])
-        tickets.append((srv.submit(int(tabs[i]), h[o:o + n], l[o:o + n],
-                                   out_pool[pos:pos + n]), i))
-        pos += n
-    deadline = t0 + args.duration + 60.0           # the run never waits more than a minute past
-    failed = 0
-    for tk, _ in tickets:
-        left = max(0.0, deadline - time.perf_counter())
-        try:
-            srv.wait(tk, int(left * 1e6))
-        except pb.PlanbError:
-            failed += 1
-            if time.perf_counter() >= deadline:
-                break
-    wall = time.perf_counter() - t0
+
+    def phase(count):
+        """Submits `count` requests on the Poisson schedule, then waits for them; returns
+        (wall seconds, requests not completed)."""
+        tickets.clear()
+        t0 = time.perf_counter()
+        nxt = t0
+        pos = 0
+        for i in range(count):
+            nxt += gaps[i]
+            while time.perf_counter() < nxt:
+                pass
+            n = int(lens[i])
+            if pos + n > out_pool.size:
+                pos = 0
+            h, l = pools[tabs[i]]
+            o = int(offs[i])
+            tickets.append((srv.submit(int(tabs[i]), h[o:o + n], l[o:o + n],
+                                       out_pool[pos:pos + n]), i))
+            pos += n
+        deadline = t0 + count / args.rate + 60.0    # never waits more than a minute past
+        failed = 0
+        for tk, _ in tickets:
+            left = max(0.0, deadline - time.perf_counter())
+            try:
+                srv.wait(tk, int(left * 1e6))
+            except pb.PlanbError:
+                failed += 1
+                if time.perf_counter() >= deadline:
+                    break
+        return time.perf_counter() - t0, failed
+
+    # warm-up under the same load (first launches, graph captures, memory pools), then the
+    # measured phase from zeroed statistics
+    phase(min(nreq, int(args.rate * args.serve_warmup)))
+    srv.reset_stats()
+    wall, failed = phase(nreq)
     done.set()
     ut.join()
     st = srv.stats()
@@ -713,10 +747,15 @@ def _serve_loop(args, srv, fibs, fibs_in, pools, nreq, tabs, lens, offs, gaps, r
             "config": {"workload": f"Poisson arrivals at {args.rate:.0f} requests/s for "
                                    f"{args.duration:.1f} s, 32..65,536 addresses per request "
                                    f"(log-uniform), {args.tables} VRF tables, route updates at "
-                                   f"{args.update_rate:.0f}/s", "slots": 4,
+                                   f"{args.update_rate:.0f}/s, after {args.serve_warmup:.1f} s "
+                                   "of the same load", "slots": 4,
                        "builder": args.builder,
+                       "lookup_launch": "per table" if args.per_table else "single persistent",
                        "max_batch": 1 << 18, "mem_budget_bytes": budget},
             "latency_us": {"p50": st["p50_us"], "p99": st["p99_us"], "max": st["max_us"]},
+            "batch_us": {"p50": st["batch_p50_us"], "p99": st["batch_p99_us"],
+                         "max": st["batch_max_us"]},
+            "graph_captures": st["recaptures"],
             "requests": st["requests"], "requests_per_s": st["requests"] / wall,
             "batches": st["batches"], "mean_batch": st["mean_batch"],
             "updates_applied": st["updates"], "rebuilds": st["update_batches"],

@@ -293,6 +293,10 @@ int planb_multi_lookup_devn(planb_multi *m, const uint64_t *d_addr_hi, const uin
  * and again whenever a table is swapped; 0 before the first lookup. Errors: PLANB_EINVAL. */
 int planb_multi_persistent(const planb_multi *m);
 
+/* planb_multi_captures — how many times the group has captured its graph (the first lookup,
+ * then once per table swap or buffer change seen by a lookup); 0 for NULL. */
+uint64_t planb_multi_captures(const planb_multi *m);
+
 /* planb_multi_destroy — waits for the device and frees the group (not its tables). */
 void planb_multi_destroy(planb_multi *m);
 
@@ -308,7 +312,8 @@ typedef struct {
     uint64_t mem_budget;       /* device bytes the admitted tables may hold; 0 = no limit         */
     uint32_t update_period_us; /* how often queued route changes are applied; default 10,000      */
     int32_t device;            /* CUDA device; -1 = current                                       */
-    uint32_t reserved[6];
+    uint32_t multi_flags;      /* flags of the slots' table groups (PLANB_MULTI_*); default 0     */
+    uint32_t reserved[5];
 } planb_server_opts;
 
 typedef struct {
@@ -320,6 +325,8 @@ typedef struct {
     double rebuild_ms_mean;               /* mean time of one table's rebuild-and-swap           */
     int32_t last_error;                   /* last failure code inside the engine (0 = none)      */
     int32_t reserved;
+    double batch_p50_us, batch_p99_us, batch_max_us; /* device batches, launch to results seen  */
+    uint64_t recaptures;                  /* slot graph captures after a table swap              */
 } planb_server_stats_t;
 
 void planb_server_opts_default(planb_server_opts *o);

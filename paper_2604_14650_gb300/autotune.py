@@ -25,9 +25,16 @@ def size_class(n_intervals: int) -> float:
     return round(math.log2(max(int(n_intervals), 2)) * 2) / 2
 
 
-def candidates(depth: int, auto_levels: int) -> list[dict]:
-    """Candidate option sets around the library's automatic choice."""
+def candidates(depth: int, auto_levels: int, persistent: bool = False) -> list[dict]:
+    """Candidate option sets around the library's automatic choice. persistent=True keeps to the
+    configurations a multi-table group can run in its single persistent launch (hybrid F8X128 or
+    F8V7; that launch fixes threads and CTAs per SM, so only the format and the index depth vary)."""
     out = []
+    if persistent:
+        for fmt in ("f8x128", "f8v7"):
+            for s in sorted({auto_levels, max(auto_levels - 1, 0)}):
+                out.append(dict(format=fmt, kernel="hybrid", smem_levels=s))
+        return out
     for fmt in ("f8x128", "f8v7"):
         for s in sorted({auto_levels, max(auto_levels - 1, 0)}):
             for threads, ctas in ((512, 0), (256, 0), (512, 1)):
@@ -41,7 +48,9 @@ def candidates(depth: int, auto_levels: int) -> list[dict]:
 
 
 class Autotuner:
-    def __init__(self, cache_path: str | None = DEFAULT_CACHE, warmup: int = 2, reps: int = 5):
+    def __init__(self, cache_path: str | None = DEFAULT_CACHE, warmup: int = 2, reps: int = 5,
+                 persistent: bool = False):
+        self.persistent = persistent
         self.cache_path = cache_path
         self.warmup = warmup
         self.reps = reps
@@ -55,7 +64,8 @@ class Autotuner:
 
     def _key(self, n_intervals: int) -> str:
         import torch
-        return f"{torch.cuda.get_device_name()}|{size_class(n_intervals)}"
+        mode = "|persistent" if self.persistent else ""
+        return f"{torch.cuda.get_device_name()}|{size_class(n_intervals)}{mode}"
 
     def _time(self, fib: Fib, hi, lo, out) -> float:
         import torch
@@ -79,7 +89,7 @@ class Autotuner:
         with Fib(hi, lo, ln, nh, device=device) as probe:
             st = probe.stats()
         results = []
-        for opts in candidates(st["depth"], st["smem_levels"]):
+        for opts in candidates(st["depth"], st["smem_levels"], self.persistent):
             try:
                 with Fib(hi, lo, ln, nh, device=device, **opts) as fib:
                     t = self._time(fib, sample_hi, sample_lo, out)

@@ -106,6 +106,7 @@ _SIGS = {
     "planb_multi_lookup": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_multi_destroy": (None, [_vp]),
     "planb_multi_persistent": (C.c_int, [_vp]),
+    "planb_multi_captures": (C.c_uint64, [_vp]),
     "planb_multi_lookup_devn": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_server_opts_default": (None, [_vp]),
     "planb_server_create": (C.c_int, [_vp, C.POINTER(_vp)]),
@@ -450,7 +451,7 @@ class ServerOpts(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("slots", C.c_uint32), ("max_batch", C.c_uint32),
                 ("max_request", C.c_uint32), ("mem_budget", C.c_uint64),
                 ("update_period_us", C.c_uint32), ("device", C.c_int32),
-                ("reserved", C.c_uint32 * 6)]
+                ("multi_flags", C.c_uint32), ("reserved", C.c_uint32 * 5)]
 
 
 class ServerStats(C.Structure):
@@ -459,7 +460,9 @@ class ServerStats(C.Structure):
                 ("table_bytes", C.c_uint64), ("queued", C.c_uint64), ("p50_us", C.c_double),
                 ("p99_us", C.c_double), ("max_us", C.c_double), ("mean_batch", C.c_double),
                 ("rebuild_ms_mean", C.c_double), ("last_error", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("batch_p50_us", C.c_double),
+                ("batch_p99_us", C.c_double), ("batch_max_us", C.c_double),
+                ("recaptures", C.c_uint64)]
 
 
 _live_servers = weakref.WeakSet()
@@ -479,7 +482,8 @@ class Server:
     """The serving engine (planb_server): continuous batching of host-buffer requests over tables."""
 
     def __init__(self, slots: int = 4, max_batch: int = 1 << 18, max_request: int = 1 << 16,
-                 mem_budget: int = 0, update_period_us: int = 10_000, device: int | None = None):
+                 mem_budget: int = 0, update_period_us: int = 10_000, device: int | None = None,
+                 per_table: bool = False):
         self._lib = load()
         self._h = None
         o = ServerOpts()
@@ -487,6 +491,7 @@ class Server:
         o.slots, o.max_batch, o.max_request = slots, max_batch, max_request
         o.mem_budget, o.update_period_us = mem_budget, update_period_us
         o.device = -1 if device is None else device
+        o.multi_flags = 2 if per_table else 0
         h = C.c_void_p()
         _check(self._lib.planb_server_create(C.byref(o), C.byref(h)), "planb_server_create")
         self._h = h

@@ -948,6 +948,7 @@ struct planb_multi {
   std::vector<std::shared_ptr<Table>> snap;  // the tables the captured graph reads
   std::mutex mu;
   uint32_t flags = 0;
+  uint64_t captures = 0;         // graph captures so far
 };
 
 namespace {
@@ -972,8 +973,10 @@ int multi_pipeline(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cu
     if (e != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: fork", e);
   }
   if (m->persist) {
-    rc = planb::launch_multi_persistent(m->desc, m->T, m->range, m->bhi, m->blo, m->bres,
-                                        m->fibs[0]->d_status, m->persist_ctas, m->persist_smem, s);
+    rc = planb::launch_multi_persistent(
+        m->desc, m->T, m->range, m->bhi, m->blo, m->bres,
+        reinterpret_cast<unsigned long long*>(m->range + 2 * m->T + 3), m->fibs[0]->d_status,
+        m->persist_ctas, m->persist_smem, s);
     if (rc) return fail_detail(rc, "multi: persistent lookup", cudaGetLastError());
   } else {
     for (uint32_t t = 0; t < m->T; t++) {
@@ -1026,7 +1029,7 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     const size_t where_off = cap * 16, bres_off = where_off + up(cap * 4),
                  counts_off = bres_off + up(cap * 2),
                  range_off = counts_off + up(static_cast<size_t>(m->T + 1) * m->G * 4);
-    const size_t desc_off = range_off + up((2 * m->T + 3) * 8);
+    const size_t desc_off = range_off + up((2 * m->T + 4) * 8);
     const size_t bytes = desc_off + m->T * sizeof(planb::MultiDesc);
     if (cudaMalloc(&m->mem, bytes) != cudaSuccess) {
       m->mem = nullptr;
@@ -1184,6 +1187,7 @@ int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t*
       cudaGetLastError();
       return rc != PLANB_OK ? rc : fail_detail(PLANB_ECUDA, "multi: end capture", ec);
     }
+    m->captures++;
     const cudaError_t ei = cudaGraphInstantiate(&m->exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) {
@@ -1205,6 +1209,12 @@ int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t*
 }  // namespace
 
 extern "C" {
+
+uint64_t planb_multi_captures(const planb_multi* m) {
+  if (!m) return 0;
+  std::lock_guard<std::mutex> lk(const_cast<planb_multi*>(m)->mu);
+  return m->captures;
+}
 
 int planb_multi_persistent(const planb_multi* m) {
   if (!m) return PLANB_EINVAL;

@@ -1,0 +1,74 @@
+// Device helpers shared by the lookup kernels (lookup.cu, multi_lookup.cu): 128-bit compares, the
+// branchless lower bound, and the search of the shared-memory top-of-tree index.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace planb {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kRounds = 4;  // addresses per 8-lane group in flight during the L2 levels
+
+// 128-bit unsigned k < x
+__device__ __forceinline__ bool less128(uint64_t kh, uint64_t kl, uint64_t xh, uint64_t xl) {
+  return (kh < xh) | ((kh == xh) & (kl < xl));
+}
+
+#ifdef PLANB_BOUNDS_CHECK
+__device__ __forceinline__ void report(uint32_t* status, uint32_t code) {
+  if (status) atomicOr(status, code);
+}
+#endif
+
+// Number of entries of the sorted array a[0..n) that are below x (n >= 1), branch-free with a
+// trip count that depends on n only (Khuong and Morin's branchless binary search).
+template <class Load>
+__device__ __forceinline__ uint32_t count_below(Load load, uint32_t n, uint64_t xh, uint64_t xl) {
+  uint32_t b = 0;
+  while (n > 1) {
+    const uint32_t half = n >> 1;
+    const ulonglong2 u = load(b + half);
+    b = less128(u.x, u.y, xh, xl) ? b + half : b;
+    n -= half;
+  }
+  const ulonglong2 u = load(b);
+  return b + (less128(u.x, u.y, xh, xl) ? 1u : 0u);
+}
+
+// Entries of the staged index Uh[0..N) (ascending high halves) below the address, counting an
+// entry with an equal high half by its low half (read from the global index). With a radix
+// directory the search starts in the entries of the address's bucket: entries of lower buckets
+// have smaller high halves, entries of higher buckets larger ones.
+__device__ __forceinline__ uint32_t index_count(const uint64_t* Uh, uint32_t N,
+                                                const uint16_t* Dir, uint32_t dir_bits,
+                                                uint32_t dir_shift, uint64_t dir_base,
+                                                const ulonglong2* sidx, uint64_t my_hi,
+                                                uint64_t my_lo) {
+  uint32_t lo = 0, n = N;
+  if (dir_bits) {
+    const uint64_t v = my_hi >> dir_shift;
+    uint64_t bk = v > dir_base ? v - dir_base : 0ull;
+    const uint64_t last = (1ull << dir_bits) - 1ull;
+    bk = bk < last ? bk : last;
+    lo = Dir[bk];
+    n = Dir[bk + 1] - lo;
+  }
+  uint32_t cnt = lo;
+  if (n) {
+    uint32_t b = lo;
+    while (n > 1) {
+      const uint32_t half = n >> 1;
+      b = Uh[b + half] < my_hi ? b + half : b;
+      n -= half;
+    }
+    cnt = b + (Uh[b] < my_hi ? 1u : 0u);
+  }
+  while (cnt < N && Uh[cnt] == my_hi && __ldg(&sidx[cnt].y) < my_lo) cnt++;
+  return cnt;
+}
+
+}  // namespace
+}  // namespace planb

@@ -22,8 +22,9 @@
 //           smem_levels levels are staged in shared memory per CTA. Four addresses per warp step.
 //   hybrid  (default) levels 0 .. S-1 are replaced by a per-thread branchless lower bound over the
 //           level-S subtree maxima staged in shared memory (the same count a descent of those
-//           levels yields, at one 16-byte entry per level-S node instead of a 128-byte node per
-//           internal node); the remaining D - S levels, read from L2, are descended by 8-lane
+//           levels yields, at one 8-byte high half per level-S node instead of a 128-byte node per
+//           internal node), started inside the address's bucket of a radix directory over those
+//           high halves; the remaining D - S levels, read from L2, are descended by 8-lane
 //           groups with four addresses per group in flight, so a warp keeps 16 node fetches
 //           outstanding. The address-to-group broadcast of the paper's vector broadcast (Listing
 //           1's set1) is a warp shuffle.
@@ -34,6 +35,7 @@
 // coalesced.
 #include <cuda_runtime.h>
 
+#include "descent.cuh"
 #include "learned.cuh"
 #include "planb_internal.h"
 
@@ -41,7 +43,6 @@ namespace planb {
 
 namespace {
 
-constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct KParams {
   const ulonglong2* nodes;    // F8X128 nodes (key j of node i at nodes[i*8 + j])
@@ -86,64 +87,6 @@ __device__ __forceinline__ Seg segment(const KParams& p) {
 template <bool MULTI = true>
 __device__ __forceinline__ void store_out(const KParams& p, uint64_t j, uint16_t v) {
   p.out[(MULTI && p.perm) ? p.perm[j] : j] = v;
-}
-
-// 128-bit unsigned k < x
-__device__ __forceinline__ bool less128(uint64_t kh, uint64_t kl, uint64_t xh, uint64_t xl) {
-  return (kh < xh) | ((kh == xh) & (kl < xl));
-}
-
-#ifdef PLANB_BOUNDS_CHECK
-__device__ __forceinline__ void report(uint32_t* status, uint32_t code) {
-  if (status) atomicOr(status, code);
-}
-#endif
-
-// Number of entries of the sorted array a[0..n) that are below x (n >= 1), branch-free with a
-// trip count that depends on n only (Khuong and Morin's branchless binary search).
-template <class Load>
-__device__ __forceinline__ uint32_t count_below(Load load, uint32_t n, uint64_t xh, uint64_t xl) {
-  uint32_t b = 0;
-  while (n > 1) {
-    const uint32_t half = n >> 1;
-    const ulonglong2 u = load(b + half);
-    b = less128(u.x, u.y, xh, xl) ? b + half : b;
-    n -= half;
-  }
-  const ulonglong2 u = load(b);
-  return b + (less128(u.x, u.y, xh, xl) ? 1u : 0u);
-}
-
-// Entries of the staged index Uh[0..N) (ascending high halves) below the address, counting an
-// entry with an equal high half by its low half (read from the global index). With a radix
-// directory the search starts in the entries of the address's bucket: entries of lower buckets
-// have smaller high halves, entries of higher buckets larger ones.
-__device__ __forceinline__ uint32_t index_count(const uint64_t* Uh, uint32_t N,
-                                                const uint16_t* Dir, uint32_t dir_bits,
-                                                uint32_t dir_shift, uint64_t dir_base,
-                                                const ulonglong2* sidx, uint64_t my_hi,
-                                                uint64_t my_lo) {
-  uint32_t lo = 0, n = N;
-  if (dir_bits) {
-    const uint64_t v = my_hi >> dir_shift;
-    uint64_t bk = v > dir_base ? v - dir_base : 0ull;
-    const uint64_t last = (1ull << dir_bits) - 1ull;
-    bk = bk < last ? bk : last;
-    lo = Dir[bk];
-    n = Dir[bk + 1] - lo;
-  }
-  uint32_t cnt = lo;
-  if (n) {
-    uint32_t b = lo;
-    while (n > 1) {
-      const uint32_t half = n >> 1;
-      b = Uh[b + half] < my_hi ? b + half : b;
-      n -= half;
-    }
-    cnt = b + (Uh[b] < my_hi ? 1u : 0u);
-  }
-  while (cnt < N && Uh[cnt] == my_hi && __ldg(&sidx[cnt].y) < my_lo) cnt++;
-  return cnt;
 }
 
 // ------------------------------------------------------------------------------- coop F8X128
@@ -271,7 +214,6 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
 // In the L2 levels a group needs the address of the lane it serves: only the high half and the node
 // index are broadcast; the low half is broadcast only when some lane of the warp finds a key whose
 // high half equals the address's.
-constexpr int kRounds = 4;  // addresses per group in flight during the L2 levels
 
 //
 // LEARNED: phase A first asks the learned position model (learned.cuh) for the address's interval
@@ -458,178 +400,6 @@ __global__ void __launch_bounds__(256) lookup_flat(const KParams p) {
   }
 }
 
-// ------------------------------------------------------------------------------- multi, one launch
-// All tables of a bucketed multi-table batch in one persistent launch. CTA b takes the b-th
-// contiguous chunk of the bucketed addresses (a multiple of 32), so it meets only the few tables
-// whose segments overlap its chunk; for each it stages that table's top-of-tree index (high halves)
-// in shared memory and runs the hybrid descent of lookup_hybrid — phase A over the index, then the
-// table's remaining DB levels from L2 by 8-lane groups — writing each result at its bucketed
-// position. The tile code is instantiated per (DB, packed) and picked per table; depths beyond
-// kMultiMaxDb take a run-time level loop. Addresses with an id beyond the tables (after range[T])
-// are left to the gather that follows.
-constexpr int kMultiMaxDb = 4;
-
-template <int DB, bool PACKED>   // DB < 0: run-time depth d.db
-__device__ __forceinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
-                                            const uint16_t* Dir, uint64_t s0,
-                                            uint64_t s1, const uint64_t* __restrict__ xhi,
-                                            const uint64_t* __restrict__ xlo,
-                                            uint16_t* __restrict__ out, uint32_t* status) {
-  const ulonglong2* nodes = static_cast<const ulonglong2*>(d.nodes);
-  const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
-  const uint32_t N = d.sidx_n;
-  const uint32_t db = DB >= 0 ? static_cast<uint32_t>(DB) : d.db;
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t g = lane >> 3;
-  const uint32_t j = lane & 7u;
-  const uint32_t gshift = g * 8u;
-  const uint32_t gmask = 0xFFu << gshift;
-  const uint32_t wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (uint64_t base = s0 + static_cast<uint64_t>(wid) * 32u; base < s1; base += nw * 32u) {
-    const uint64_t mine = base + lane;
-    const bool ok = mine < s1;
-    const uint64_t my_hi = ok ? xhi[mine] : 0ull;
-    const uint64_t my_lo = ok ? xlo[mine] : 0ull;
-    const uint32_t cnt =
-        N ? index_count(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, sidx, my_hi, my_lo) : 0u;
-    uint32_t result = 0;
-    if (db == 0) {
-      uint32_t rank = cnt;
-#ifdef PLANB_BOUNDS_CHECK
-      if (rank >= d.n_intervals) {
-        report(status, 2u);
-        rank = 0;
-      }
-#endif
-      result = __ldg(d.values + rank);
-    } else {
-      const uint32_t my_node = d.sidx_node + cnt;
-      uint64_t my_rank = 0;
-#pragma unroll
-      for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
-        uint64_t qh[kRounds];
-        uint32_t nd[kRounds], c[kRounds];
-        ulonglong2 key[kRounds];
-#pragma unroll
-        for (int i = 0; i < kRounds; i++) {
-          const uint32_t src = gshift + r0 + i;
-          qh[i] = __shfl_sync(kFull, my_hi, src);
-          nd[i] = __shfl_sync(kFull, my_node, src);
-        }
-#pragma unroll
-        for (uint32_t l = 0; l < db; l++) {
-#pragma unroll
-          for (int i = 0; i < kRounds; i++)
-            key[i] = __ldg(nodes + static_cast<uint64_t>(nd[i]) * 8u + j);
-          const bool last = l + 1 == db;
-          const bool keylane = !(PACKED && last) || j < 7u;
-          bool lt[kRounds], eq[kRounds];
-          bool anyeq = false;
-#pragma unroll
-          for (int i = 0; i < kRounds; i++) {
-            lt[i] = keylane & (key[i].x < qh[i]);
-            eq[i] = keylane & (key[i].x == qh[i]);
-            anyeq |= eq[i];
-          }
-          if (__any_sync(kFull, anyeq)) {
-#pragma unroll
-            for (int i = 0; i < kRounds; i++) {
-              const uint64_t ql = __shfl_sync(kFull, my_lo, gshift + r0 + i);
-              lt[i] = lt[i] | (eq[i] & (key[i].y < ql));
-            }
-          }
-#pragma unroll
-          for (int i = 0; i < kRounds; i++) {
-            c[i] = __popc(__ballot_sync(kFull, lt[i]) & gmask);
-            if (!last) nd[i] = nd[i] * 9u + 1u + c[i];
-          }
-        }
-        if (PACKED) {
-          // the next hop of slot c sits in slot 7 of the same leaf line (lane 7 of the group)
-#pragma unroll
-          for (int i = 0; i < kRounds; i++) {
-#ifdef PLANB_BOUNDS_CHECK
-            if (c[i] > 6u) report(status, 4u);
-#endif
-            const uint32_t ci = c[i] & 7u;
-            const uint64_t w = ci < 4u ? key[i].x : key[i].y;
-            const uint32_t f = static_cast<uint32_t>(w >> (16u * (ci & 3u))) & 0xFFFFu;
-            const uint32_t v = __shfl_sync(kFull, f, gshift + 7u);
-            if (j == r0 + i) result = v;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < kRounds; i++) {
-            uint64_t rank = static_cast<uint64_t>(nd[i] - d.internal_nodes) * 8u + c[i];
-#ifdef PLANB_BOUNDS_CHECK
-            if (rank >= d.n_intervals) {
-              report(status, 4u);
-              rank = 0;
-            }
-#endif
-            if (j == r0 + i) my_rank = rank;
-          }
-        }
-      }
-      if (!PACKED) result = __ldg(d.values + my_rank);
-    }
-    if (ok) out[mine] = static_cast<uint16_t>(result);
-  }
-}
-
-__global__ void __launch_bounds__(512, 2)
-    lookup_multi_persistent(const MultiDesc* __restrict__ desc, uint32_t T,
-                            const uint64_t* __restrict__ range, const uint64_t* __restrict__ xhi,
-                            const uint64_t* __restrict__ xlo, uint16_t* __restrict__ out,
-                            uint32_t* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* R = reinterpret_cast<uint64_t*>(smem_raw);           // range[0 .. T+1]
-  uint64_t* Uh = R + ((T + 3u) & ~1u);                           // the staged index
-  for (uint32_t i = threadIdx.x; i <= T + 1u; i += blockDim.x) R[i] = range[i];
-  __syncthreads();
-  const uint64_t nreal = R[T];
-  const uint64_t chunk = ((nreal + gridDim.x - 1) / gridDim.x + 31u) & ~31ull;
-  const uint64_t c0 = min(static_cast<uint64_t>(blockIdx.x) * chunk, nreal);
-  const uint64_t c1 = min(c0 + chunk, nreal);
-  if (c0 >= c1) return;   // the whole CTA leaves together
-  uint32_t t = 0;
-  while (t + 1u < T && R[t + 1] <= c0) t++;
-  for (; t < T && R[t] < c1; t++) {
-    const uint64_t s0 = max(R[t], c0), s1 = min(R[t + 1], c1);
-    if (s0 >= s1) continue;
-    __shared__ MultiDesc d;   // kept in shared memory: the tile loop is short of registers
-    __syncthreads();          // the previous table's readers are done with Uh and d
-    if (threadIdx.x == 0) d = desc[t];
-    __syncthreads();
-    const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
-    for (uint32_t i = threadIdx.x; i < d.sidx_n; i += blockDim.x) Uh[i] = __ldg(&sidx[i].x);
-    uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((d.sidx_n + 1u) & ~1u));
-    const uint32_t dn = d.dir_bits ? (1u << d.dir_bits) + 1u : 0u;
-    for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(d.dir + i);
-    __syncthreads();
-    const uint32_t sel = d.db <= static_cast<uint32_t>(kMultiMaxDb) ? d.db : 15u;
-    if (d.packed) {
-      switch (sel) {
-        case 0: multi_tiles<0, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        case 1: multi_tiles<1, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        case 2: multi_tiles<2, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        case 3: multi_tiles<3, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        case 4: multi_tiles<4, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        default: multi_tiles<-1, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-      }
-    } else {
-      switch (sel) {
-        case 0: multi_tiles<0, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        case 1: multi_tiles<1, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        case 2: multi_tiles<2, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        case 3: multi_tiles<3, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        case 4: multi_tiles<4, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-        default: multi_tiles<-1, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-      }
-    }
-  }
-}
-
 typedef void (*KernelFn)(const KParams);
 
 constexpr int kMaxDepth = 10;
@@ -796,33 +566,6 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   if (cfg.blocks > 0 && blocks > static_cast<uint64_t>(cfg.blocks)) blocks = cfg.blocks;
   fn<<<static_cast<unsigned>(blocks), cfg.threads, cfg.smem_bytes,
        static_cast<cudaStream_t>(stream)>>>(p);
-  return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
-}
-
-int multi_persistent_setup(int device, size_t smem_bytes, int* ctas) {
-  int limit = 0, sms = 0, per_sm = 0;
-  const void* fn = reinterpret_cast<const void*>(lookup_multi_persistent);
-  if (int rc = dynamic_smem_limit(fn, device, &limit)) return rc;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
-    return PLANB_ECUDA;
-  if (smem_bytes > static_cast<size_t>(limit)) return PLANB_EINVAL;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess)
-    return PLANB_ECUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, smem_bytes) != cudaSuccess)
-    return PLANB_ECUDA;
-  if (per_sm < 1) return PLANB_EINVAL;
-  *ctas = sms * per_sm;
-  return PLANB_OK;
-}
-
-int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t* d_range,
-                            const uint64_t* d_hi, const uint64_t* d_lo, uint16_t* d_out,
-                            uint32_t* d_status, int ctas, size_t smem_bytes, void* stream) {
-  if (T == 0 || T > 255 || ctas < 1) return PLANB_EINVAL;
-  cudaGetLastError();
-  lookup_multi_persistent<<<static_cast<unsigned>(ctas), 512, smem_bytes,
-                            static_cast<cudaStream_t>(stream)>>>(d_desc, T, d_range, d_hi, d_lo,
-                                                                 d_out, d_status);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

@@ -89,14 +89,18 @@ __global__ void __launch_bounds__(kScanThreads) mt_rowscan_kernel(uint32_t* __re
 // One block: range[t] = sum of the totals of rows before t (range[T] starts the invalid-id
 // segment, range[T+1] = the batch size).
 __global__ void mt_tablescan_kernel(const uint64_t* __restrict__ totals, uint32_t T,
-                                    uint64_t* __restrict__ range) {
+                                    uint64_t* __restrict__ range,
+                                    unsigned long long* __restrict__ next_item) {
   typedef cub::BlockScan<uint64_t, 256> Scan;
   __shared__ typename Scan::TempStorage tmp;
   const uint32_t t = threadIdx.x;
   uint64_t v = t <= T ? totals[t] : 0ull, excl = 0, all = 0;
   Scan(tmp).ExclusiveSum(v, excl, all);
   if (t <= T) range[t] = excl;
-  if (t == 0) range[T + 1] = all;
+  if (t == 0) {
+    range[T + 1] = all;
+    *next_item = 0ull;   // the persistent lookup that follows claims its work from here
+  }
 }
 
 // The scatter works through its chunk in tiles of kTile addresses: the tile is ranked per table
@@ -211,7 +215,8 @@ int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* 
   uint64_t* totals = d_range + (T + 2);   // T + 1 words of scratch after the range
   mt_hist_kernel<<<G, 256, sh, st>>>(d_tid, n, T, chunk, d_counts, d_n);
   mt_rowscan_kernel<<<T + 1, kScanThreads, 0, st>>>(d_counts, G, totals);
-  mt_tablescan_kernel<<<1, 256, 0, st>>>(totals, T, d_range);
+  mt_tablescan_kernel<<<1, 256, 0, st>>>(
+      totals, T, d_range, reinterpret_cast<unsigned long long*>(d_range + 2 * T + 3));
   mt_scatter_kernel<<<G, kScatterThreads, 0, st>>>(d_hi, d_lo, d_tid, n, T, chunk, d_counts,
                                                     d_range, d_bhi, d_blo, d_where, d_n);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;

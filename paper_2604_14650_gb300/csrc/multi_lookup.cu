@@ -1,0 +1,236 @@
+// Multi-table lookups in one persistent launch (the lookup stage of planb_multi_lookup).
+#include <cuda_runtime.h>
+
+#include "descent.cuh"
+#include "planb_internal.h"
+
+// multi_tiles<0, ...> keeps a level loop that never runs (its tables are resolved by the index)
+#pragma nv_diag_suppress 186
+
+namespace planb {
+
+namespace {
+
+// All tables of a bucketed multi-table batch in one persistent launch. The bucketed addresses are
+// cut into work items of W consecutive addresses, which the CTAs claim in order from a global
+// counter, so the CTAs running at one time work on a narrow window of the grouped batch and only
+// two or three tables are live in L2 at once. A CTA stages the top-of-tree index (high halves) and
+// radix directory of each table it meets in shared memory — keeping them while its next item is
+// in the same table — and runs the hybrid descent of lookup_hybrid: phase A over the index, then
+// the table's remaining DB levels from L2 by 8-lane groups, writing each result at its bucketed
+// position. The tile code is instantiated per (DB, packed) and picked per table; depths beyond
+// kMultiMaxDb take a run-time level loop. Addresses with an id beyond the tables (after range[T])
+// are left to the gather that follows.
+constexpr int kMultiMaxDb = 4;
+
+template <int DB, bool PACKED>   // DB < 0: run-time depth d.db
+__device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
+                                         const uint16_t* Dir, uint64_t s0, uint64_t s1,
+                                         const uint64_t* __restrict__ xhi,
+                                         const uint64_t* __restrict__ xlo,
+                                         uint16_t* __restrict__ out, uint32_t* status) {
+  const ulonglong2* nodes = static_cast<const ulonglong2*>(d.nodes);
+  const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
+  const uint32_t N = d.sidx_n;
+  const uint32_t db = DB >= 0 ? static_cast<uint32_t>(DB) : d.db;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t g = lane >> 3;
+  const uint32_t j = lane & 7u;
+  const uint32_t gshift = g * 8u;
+  const uint32_t gmask = 0xFFu << gshift;
+  const uint32_t wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint64_t base = s0 + static_cast<uint64_t>(wid) * 32u; base < s1; base += nw * 32u) {
+    const uint64_t mine = base + lane;
+    const bool ok = mine < s1;
+    const uint64_t my_hi = ok ? xhi[mine] : 0ull;
+    const uint64_t my_lo = ok ? xlo[mine] : 0ull;
+    const uint32_t cnt =
+        N ? index_count(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, sidx, my_hi, my_lo) : 0u;
+    uint32_t result = 0;
+    if (db == 0) {
+      uint32_t rank = cnt;
+#ifdef PLANB_BOUNDS_CHECK
+      if (rank >= d.n_intervals) {
+        report(status, 2u);
+        rank = 0;
+      }
+#endif
+      result = __ldg(d.values + rank);
+    } else {
+      const uint32_t my_node = d.sidx_node + cnt;
+      uint64_t my_rank = 0;
+#pragma unroll
+      for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
+        uint64_t qh[kRounds];
+        uint32_t nd[kRounds], c[kRounds];
+        ulonglong2 key[kRounds];
+#pragma unroll
+        for (int i = 0; i < kRounds; i++) {
+          const uint32_t src = gshift + r0 + i;
+          qh[i] = __shfl_sync(kFull, my_hi, src);
+          nd[i] = __shfl_sync(kFull, my_node, src);
+        }
+#pragma unroll
+        for (uint32_t l = 0; l < db; l++) {
+#pragma unroll
+          for (int i = 0; i < kRounds; i++)
+            key[i] = __ldg(nodes + static_cast<uint64_t>(nd[i]) * 8u + j);
+          const bool last = l + 1 == db;
+          const bool keylane = !(PACKED && last) || j < 7u;
+          bool lt[kRounds], eq[kRounds];
+          bool anyeq = false;
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            lt[i] = keylane & (key[i].x < qh[i]);
+            eq[i] = keylane & (key[i].x == qh[i]);
+            anyeq |= eq[i];
+          }
+          if (__any_sync(kFull, anyeq)) {
+#pragma unroll
+            for (int i = 0; i < kRounds; i++) {
+              const uint64_t ql = __shfl_sync(kFull, my_lo, gshift + r0 + i);
+              lt[i] = lt[i] | (eq[i] & (key[i].y < ql));
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            c[i] = __popc(__ballot_sync(kFull, lt[i]) & gmask);
+            if (!last) nd[i] = nd[i] * 9u + 1u + c[i];
+          }
+        }
+        if (PACKED) {
+          // the next hop of slot c sits in slot 7 of the same leaf line (lane 7 of the group)
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+#ifdef PLANB_BOUNDS_CHECK
+            if (c[i] > 6u) report(status, 4u);
+#endif
+            const uint32_t ci = c[i] & 7u;
+            const uint64_t w = ci < 4u ? key[i].x : key[i].y;
+            const uint32_t f = static_cast<uint32_t>(w >> (16u * (ci & 3u))) & 0xFFFFu;
+            const uint32_t v = __shfl_sync(kFull, f, gshift + 7u);
+            if (j == r0 + i) result = v;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            uint64_t rank = static_cast<uint64_t>(nd[i] - d.internal_nodes) * 8u + c[i];
+#ifdef PLANB_BOUNDS_CHECK
+            if (rank >= d.n_intervals) {
+              report(status, 4u);
+              rank = 0;
+            }
+#endif
+            if (j == r0 + i) my_rank = rank;
+          }
+        }
+      }
+      if (!PACKED) result = __ldg(d.values + my_rank);
+    }
+    if (ok) out[mine] = static_cast<uint16_t>(result);
+  }
+}
+
+__global__ void __launch_bounds__(512, 2)
+    lookup_multi_persistent(const MultiDesc* __restrict__ desc, uint32_t T,
+                            const uint64_t* __restrict__ range, const uint64_t* __restrict__ xhi,
+                            const uint64_t* __restrict__ xlo, uint16_t* __restrict__ out,
+                            unsigned long long* __restrict__ next_item,
+                            uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* R = reinterpret_cast<uint64_t*>(smem_raw);           // range[0 .. T+1]
+  uint64_t* Uh = R + ((T + 3u) & ~1u);                           // the staged index
+  __shared__ MultiDesc d;          // the staged table (kept in shared memory: registers are short)
+  __shared__ unsigned long long item;
+  for (uint32_t i = threadIdx.x; i <= T + 1u; i += blockDim.x) R[i] = range[i];
+  __syncthreads();
+  const uint64_t nreal = R[T];
+  // items of W bucketed addresses, handed out in order: the CTAs running at one time work on a
+  // narrow window of the grouped batch, so only two or three tables are live in L2 at once; W
+  // shrinks with the batch so a small batch still spreads over many CTAs
+  uint64_t W = (nreal / (static_cast<uint64_t>(gridDim.x) * 4u) + 511u) & ~511ull;
+  W = W < 512u ? 512u : (W > 16384u ? 16384u : W);
+  uint32_t staged = 0xFFFFFFFFu;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(next_item, 1ull);
+    __syncthreads();
+    const uint64_t beg = item * W;
+    __syncthreads();   // every thread has read item before thread 0 takes the next one
+    if (beg >= nreal) break;
+    const uint64_t end = min(beg + W, nreal);
+    uint32_t lo = 0, hi = T;   // the table holding address beg: R[t] <= beg < R[t+1]
+    while (hi - lo > 1u) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (R[mid] <= beg) lo = mid; else hi = mid;
+    }
+    for (uint32_t t = lo; t < T && R[t] < end; t++) {
+      const uint64_t s0 = max(R[t], beg), s1 = min(R[t + 1], end);
+      if (s0 >= s1) continue;
+      uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((d.sidx_n + 1u) & ~1u));
+      if (t != staged) {
+        __syncthreads();   // the previous table's readers are done with Uh and d
+        if (threadIdx.x == 0) d = desc[t];
+        __syncthreads();
+        const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
+        for (uint32_t i = threadIdx.x; i < d.sidx_n; i += blockDim.x) Uh[i] = __ldg(&sidx[i].x);
+        Dir = reinterpret_cast<uint16_t*>(Uh + ((d.sidx_n + 1u) & ~1u));
+        const uint32_t dn = d.dir_bits ? (1u << d.dir_bits) + 1u : 0u;
+        for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(d.dir + i);
+        __syncthreads();
+        staged = t;
+      }
+      const uint32_t sel = d.db <= static_cast<uint32_t>(kMultiMaxDb) ? d.db : 15u;
+      if (d.packed) {
+        switch (sel) {
+          case 0: multi_tiles<0, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 1: multi_tiles<1, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 2: multi_tiles<2, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 3: multi_tiles<3, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 4: multi_tiles<4, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          default: multi_tiles<-1, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        }
+      } else {
+        switch (sel) {
+          case 0: multi_tiles<0, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 1: multi_tiles<1, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 2: multi_tiles<2, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 3: multi_tiles<3, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 4: multi_tiles<4, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          default: multi_tiles<-1, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int multi_persistent_setup(int device, size_t smem_bytes, int* ctas) {
+  int limit = 0, sms = 0, per_sm = 0;
+  const void* fn = reinterpret_cast<const void*>(lookup_multi_persistent);
+  if (int rc = dynamic_smem_limit(fn, device, &limit)) return rc;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return PLANB_ECUDA;
+  if (smem_bytes > static_cast<size_t>(limit)) return PLANB_EINVAL;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess)
+    return PLANB_ECUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 512, smem_bytes) != cudaSuccess)
+    return PLANB_ECUDA;
+  if (per_sm < 1) return PLANB_EINVAL;
+  *ctas = sms * per_sm;
+  return PLANB_OK;
+}
+
+int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t* d_range,
+                            const uint64_t* d_hi, const uint64_t* d_lo, uint16_t* d_out,
+                            unsigned long long* d_next_item, uint32_t* d_status, int ctas,
+                            size_t smem_bytes, void* stream) {
+  if (T == 0 || T > 255 || ctas < 1) return PLANB_EINVAL;
+  cudaGetLastError();
+  lookup_multi_persistent<<<static_cast<unsigned>(ctas), 512, smem_bytes,
+                            static_cast<cudaStream_t>(stream)>>>(d_desc, T, d_range, d_hi, d_lo,
+                                                                 d_out, d_next_item, d_status);
+  return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+}  // namespace planb

@@ -246,16 +246,19 @@ struct MultiDesc {
 int multi_persistent_setup(int device, size_t smem_bytes, int* ctas);
 // Looks up the bucketed addresses [0, range[T]) of d_hi/d_lo against table t of d_desc for the
 // addresses in [range[t], range[t+1]), writing each result at its bucketed position in d_out.
-// smem_bytes: 8 * (T + 3 rounded to even) + the largest over the tables of 8 * sidx_n rounded up
-// to 16 bytes plus 2 * (2^dir_bits + 1), at most the device maximum.
+// Work items are claimed from *d_next_item, which must be 0 when the launch starts (the bucketing
+// resets it). smem_bytes: 8 * (T + 3 rounded to even) + the largest over the tables of 8 * sidx_n
+// rounded up to 16 bytes plus 2 * (2^dir_bits + 1), at most the device maximum.
 int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t* d_range,
                             const uint64_t* d_hi, const uint64_t* d_lo, uint16_t* d_out,
-                            uint32_t* d_status, int ctas, size_t smem_bytes, void* stream);
+                            unsigned long long* d_next_item, uint32_t* d_status, int ctas,
+                            size_t smem_bytes, void* stream);
 
 // Multi-table bucketing (multi.cu): groups n addresses by their u8 table id (ids >= T form one
 // extra segment) into d_bhi/d_blo, table-major, with d_where[i] = the bucketed position of address
-// i; d_range[t] .. d_range[t+1] bound table t's segment; d_range has room for 2T + 3 words (the
-// last T + 1 are scratch). d_counts holds (T+1) x G words. n < 2^32.
+// i; d_range[t] .. d_range[t+1] bound table t's segment; d_range has room for 2T + 4 words (then
+// T + 1 words of scratch, then the persistent lookup's work counter, which is reset to 0).
+// d_counts holds (T+1) x G words. n < 2^32.
 // With d_n the kernels read the batch size from device memory (n then only bounds it).
 int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
                      uint32_t T, uint32_t G, uint32_t* d_counts, uint64_t* d_range,
@@ -270,6 +273,10 @@ int launch_gather(const uint8_t* d_tid, const uint32_t* d_where, const uint16_t*
 // out[0..5] = registers, max threads per block, max dynamic shared bytes, local bytes, static shared
 // bytes, constant bytes.
 int kernel_attributes(const DevTable& t, bool multi, int* out);
+
+// Room for dynamic shared memory of a kernel function: the device's opt-in maximum per block less
+// the function's static shared memory.
+int dynamic_smem_limit(const void* fn, int device, int* limit);
 
 // Occupancy-derived launch configuration for a table on a device.
 int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, LaunchCfg& cfg);

@@ -58,6 +58,7 @@ struct Slot {
   std::vector<std::shared_ptr<Request>> reqs;
   std::vector<size_t> offs;
   bool busy = false;
+  std::chrono::steady_clock::time_point launched;
 };
 
 struct PendingUpdate {
@@ -88,13 +89,17 @@ struct planb_server {
   double rebuild_ms = 0;
   std::vector<float> lat_us;           // ring of recent request latencies
   size_t lat_pos = 0, lat_count = 0;
+  std::vector<float> batch_us;         // ring of recent batch durations (launch to completion)
+  size_t batch_pos = 0, batch_count = 0;
   int last_error = PLANB_OK;
   char last_detail[512] = "";
+  uint64_t recaptures = 0;             // batches whose slot group saw a swapped table
 };
 
 namespace {
 
 constexpr size_t kLatRing = size_t(1) << 20;
+constexpr size_t kBatchRing = size_t(1) << 18;
 
 // with m->mu held: remember a failure and where it happened
 void note_error(planb_server* m, int rc, const char* where, const char* why) {
@@ -103,7 +108,7 @@ void note_error(planb_server* m, int rc, const char* where, const char* why) {
 }
 
 void free_slot(Slot& s) {
-  if (s.mt) planb_multi_destroy(s.mt);
+  if (s.mt) planb_multi_destroy(s.mt);   // its captures are counted by the caller when it matters
   if (s.ev) cudaEventDestroy(s.ev);
   if (s.st) cudaStreamDestroy(s.st);
   if (s.h_hi) cudaFreeHost(s.h_hi);
@@ -140,6 +145,11 @@ int make_slot(Slot& s, size_t cap) {
 // with m->mu held: results of a finished slot go to their requests
 void complete_slot(planb_server* m, Slot& s, int status) {
   const auto now = clock_t_::now();
+  if (!s.reqs.empty()) {
+    m->batch_us[m->batch_pos] = std::chrono::duration<float, std::micro>(now - s.launched).count();
+    m->batch_pos = (m->batch_pos + 1) % kBatchRing;
+    m->batch_count++;
+  }
   for (size_t i = 0; i < s.reqs.size(); i++) {
     Request& r = *s.reqs[i];
     if (status == PLANB_OK) std::memcpy(r.out, s.h_out + s.offs[i], r.n * 2);
@@ -194,10 +204,13 @@ void dispatcher_main(planb_server* m) {
     }
     // a group for the current table set
     if (!slot->mt || slot->tables_version != m->tables_version) {
-      if (slot->mt) planb_multi_destroy(slot->mt);
+      if (slot->mt) {
+        m->recaptures += planb_multi_captures(slot->mt);
+        planb_multi_destroy(slot->mt);
+      }
       slot->mt = nullptr;
       const int rc = planb_multi_create(m->tables.data(), static_cast<uint32_t>(m->tables.size()),
-                                        m->o.max_batch, 0, &slot->mt);
+                                        m->o.max_batch, m->o.multi_flags, &slot->mt);
       if (rc) {
         note_error(m, rc, "slot table group", planb_last_error());
         while (!m->queue.empty()) {
@@ -226,6 +239,7 @@ void dispatcher_main(planb_server* m) {
       std::memset(slot->h_tid + slot->offs[i], static_cast<int>(r.table), r.n);
     }
     *slot->h_n = total;
+    slot->launched = clock_t_::now();
     cudaStream_t st = slot->st;
     bool ok =
         cudaMemcpyAsync(slot->d_n, slot->h_n, 8, cudaMemcpyHostToDevice, st) == cudaSuccess &&
@@ -320,7 +334,8 @@ int planb_server_create(const planb_server_opts* opts, planb_server** out) {
     o.struct_size = sizeof(o);
   }
   if (o.slots < 1 || o.slots > 64 || o.max_batch < 1 || o.max_request < 1 ||
-      o.max_request > o.max_batch || o.update_period_us < 100)
+      o.max_request > o.max_batch || o.update_period_us < 100 ||
+      (o.multi_flags & ~(PLANB_MULTI_NO_GRAPH | PLANB_MULTI_PER_TABLE)))
     return PLANB_EINVAL;
   try {
     std::unique_ptr<planb_server> m(new planb_server());
@@ -330,6 +345,7 @@ int planb_server_create(const planb_server_opts* opts, planb_server** out) {
     m->device = dev;
     if (cudaSetDevice(dev) != cudaSuccess) return PLANB_ENODEV;
     m->lat_us.assign(kLatRing, 0.0f);
+    m->batch_us.assign(kBatchRing, 0.0f);
     m->slots.resize(o.slots);
     for (Slot& s : m->slots) {
       const int rc = make_slot(s, o.max_batch);
@@ -424,9 +440,13 @@ int planb_server_update(planb_server* m, uint32_t table_id, const planb_route* i
 
 int planb_server_stats(planb_server* m, planb_server_stats_t* out) {
   if (!m || !out) return PLANB_EINVAL;
-  std::vector<float> lat;
+  std::vector<float> lat, bat;
+  uint64_t recaptures = 0;
   {
     std::lock_guard<std::mutex> lk(m->mu);
+    bat.assign(m->batch_us.begin(), m->batch_us.begin() + std::min(m->batch_count, kBatchRing));
+    recaptures = m->recaptures;
+    for (Slot& s : m->slots) recaptures += planb_multi_captures(s.mt);
     std::memset(out, 0, sizeof(*out));
     out->requests = m->requests;
     out->lookups = m->lookups;
@@ -452,6 +472,17 @@ int planb_server_stats(planb_server* m, planb_server_stats_t* out) {
     out->p99_us = pct(0.99);
     out->max_us = *std::max_element(lat.begin(), lat.end());
   }
+  if (!bat.empty()) {
+    auto pct = [&](double q) {
+      const size_t i = std::min(bat.size() - 1, static_cast<size_t>(q * bat.size()));
+      std::nth_element(bat.begin(), bat.begin() + i, bat.end());
+      return static_cast<double>(bat[i]);
+    };
+    out->batch_p50_us = pct(0.50);
+    out->batch_p99_us = pct(0.99);
+    out->batch_max_us = *std::max_element(bat.begin(), bat.end());
+  }
+  out->recaptures = recaptures;
   return PLANB_OK;
 }
 
@@ -468,6 +499,8 @@ void planb_server_reset_stats(planb_server* m) {
   m->requests = m->lookups = m->batches = m->updates = m->update_batches = 0;
   m->rebuild_ms = 0;
   m->lat_pos = m->lat_count = 0;
+  m->batch_pos = m->batch_count = 0;
+  m->recaptures = 0;
 }
 
 void planb_server_destroy(planb_server* m) {

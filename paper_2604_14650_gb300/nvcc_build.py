@@ -18,11 +18,11 @@ OUT = os.path.join(HERE, "_build", platform.machine())
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["builder.cpp", "lookup.cu", "learned.cu", "multi.cu", "capi.cu", "server.cu",
-           "gpu_builder.cu"]
+SOURCES = ["builder.cpp", "lookup.cu", "multi_lookup.cu", "learned.cu", "multi.cu", "capi.cu",
+           "server.cu", "gpu_builder.cu"]
 LIBS = {"libplanb.so": [], "libplanb_checked.so": ["-DPLANB_BOUNDS_CHECK"]}
-# the only translation unit the bounds-checking define changes; the others are compiled once
-CHECKED_SOURCES = {"lookup.cu"}
+# the translation units the bounds-checking define changes; the others are compiled once
+CHECKED_SOURCES = {"lookup.cu", "multi_lookup.cu"}
 
 
 def nvcc() -> str:
@@ -49,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> dict:
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
     headers = [os.path.join(CSRC, "planb_internal.h"), os.path.join(CSRC, "learned.cuh"),
-               os.path.join(INCLUDE, "planb.h")]
+               os.path.join(CSRC, "descent.cuh"), os.path.join(INCLUDE, "planb.h")]
     jobs, links = [], {}
     for lib, defines in LIBS.items():
         objs = []

@@ -1,0 +1,29 @@
+"""The autotuner's host logic (no GPU): candidate sets and the cache key's size classes."""
+import pytest
+
+pytest.importorskip("numpy")
+from paper_2604_14650_gb300.autotune import candidates, size_class  # noqa: E402
+
+
+def test_candidates_cover_formats_depths_and_launch_shapes():
+    c = candidates(depth=6, auto_levels=4)
+    assert {x["format"] for x in c} == {"f8x128", "f8v7", "f16hi"}
+    assert {x["smem_levels"] for x in c if x["kernel"] == "hybrid"} == {3, 4}
+    assert {(x["block_threads"], x["ctas_per_sm"]) for x in c if x["kernel"] == "hybrid"} == \
+        {(512, 0), (256, 0), (512, 1)}
+
+
+def test_persistent_candidates_stay_in_the_single_launch():
+    c = candidates(depth=6, auto_levels=4, persistent=True)
+    assert c and all(x["kernel"] == "hybrid" and x["format"] in ("f8x128", "f8v7") for x in c)
+    assert all("block_threads" not in x for x in c)
+    assert candidates(depth=3, auto_levels=0, persistent=True) == [
+        dict(format="f8x128", kernel="hybrid", smem_levels=0),
+        dict(format="f8v7", kernel="hybrid", smem_levels=0)]
+
+
+def test_size_classes_are_half_octaves():
+    assert size_class(1024) == 10.0
+    assert size_class(1448) == 10.5          # 2^10.5 = 1448.2
+    assert size_class(2048) == 11.0
+    assert size_class(0) == size_class(2) == 1.0

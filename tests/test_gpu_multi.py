@@ -137,3 +137,27 @@ def test_multi_table_tiny_batches(n):
         assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
     for f in fibs:
         f.close()
+
+
+def test_autotuned_group_is_exact_and_persistent(tmp_path):
+    from paper_2604_14650_gb300.autotune import Autotuner
+    sizes = [2000, 30_000, 9000]
+    fibs_in, tid, xh, xl = workload(sizes, 200_000, seed=71)
+    tuner = Autotuner(cache_path=str(tmp_path / "tune.json"), warmup=1, reps=2, persistent=True)
+    fibs = []
+    for t, f in enumerate(fibs_in):
+        sel = tid == t
+        opts = tuner.best(f.hi, f.lo, f.len, f.nh, dev(xh[sel]), dev(xl[sel]))
+        assert opts["kernel"] == "hybrid" and opts["format"] in ("f8x128", "f8v7")
+        fibs.append(pb.Fib(f.hi, f.lo, f.len, f.nh, **opts))
+    # a second tuner on the same cache answers from it
+    again = Autotuner(cache_path=str(tmp_path / "tune.json"), persistent=True)
+    assert again.best(fibs_in[1].hi, fibs_in[1].lo, fibs_in[1].len, fibs_in[1].nh, None, None) == \
+        tuner.best(fibs_in[1].hi, fibs_in[1].lo, fibs_in[1].len, fibs_in[1].nh, None, None)
+    with pb.MultiFib(fibs, max_batch=200_000) as mt:
+        out = mt.lookup(dev(xh), dev(xl), dev(tid, np.uint8))
+        torch.cuda.synchronize()
+        assert mt.persistent
+        assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
+    for f in fibs:
+        f.close()
