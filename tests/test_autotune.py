@@ -27,3 +27,19 @@ def test_size_classes_are_half_octaves():
     assert size_class(1448) == 10.5          # 2^10.5 = 1448.2
     assert size_class(2048) == 11.0
     assert size_class(0) == size_class(2) == 1.0
+
+
+def test_benchmark_reads_recorded_counters_safely():
+    """bench.py's reader of profiles/traffic.json answers a dict or None for every kernel listed
+    there (and for an unknown one), never raises."""
+    import json
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    path = os.path.join(root, "profiles", "traffic.json")
+    names = list(json.load(open(path))) if os.path.exists(path) else []
+    for name in names + ["no such kernel"]:
+        r = bench.recorded_counters(name)
+        assert r is None or isinstance(r, dict)
