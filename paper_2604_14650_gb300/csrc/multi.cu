@@ -38,17 +38,18 @@ __global__ void mt_hist_kernel(const uint8_t* __restrict__ tid, uint64_t n, uint
   __syncthreads();
   const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * chunk;
   const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
-  const uint32_t lane = threadIdx.x & 31u;
-  // every lane of the block runs the same trip count so the warp match sees the whole warp
-  for (uint64_t i0 = b0; i0 < b1; i0 += blockDim.x) {
-    const uint64_t i = i0 + threadIdx.x;
-    uint32_t t = 0xFFFFu;
-    if (i < b1) {
-      const uint32_t t0 = tid[i];
-      t = t0 < T ? t0 : T;
+  // eight independent id loads per thread per step keep enough reads in flight
+  constexpr int kUnroll = 8;
+  for (uint64_t i0 = b0 + threadIdx.x; i0 < b1; i0 += static_cast<uint64_t>(kUnroll) * blockDim.x) {
+    uint32_t t[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; k++) {
+      const uint64_t i = i0 + static_cast<uint64_t>(k) * blockDim.x;
+      t[k] = i < b1 ? tid[i] : 0xFFFFu;
     }
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, t);
-    if (i < b1 && lane == __ffs(peers) - 1u) atomicAdd(&h[t], __popc(peers));
+#pragma unroll
+    for (int k = 0; k < kUnroll; k++)
+      if (t[k] != 0xFFFFu) atomicAdd(&h[t[k] < T ? t[k] : T], 1u);
   }
   __syncthreads();
   for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) counts[t * gridDim.x + blockIdx.x] = h[t];
@@ -196,9 +197,25 @@ __global__ void mt_gather_kernel(const uint8_t* __restrict__ tid, const uint32_t
     const uint64_t dn = *d_n;
     n = dn < n ? dn : n;
   }
-  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
-    out[i] = tid[i] < T ? bres[where[i]] : static_cast<uint16_t>(0);
+  // eight independent (id, position, result) chains per thread per step keep reads in flight
+  constexpr int kUnroll = 8;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i0 < n;
+       i0 += kUnroll * stride) {
+    uint32_t w[kUnroll];
+    bool v[kUnroll];
+#pragma unroll
+    for (int k = 0; k < kUnroll; k++) {
+      const uint64_t i = i0 + k * stride;
+      v[k] = i < n && tid[i] < T;
+      w[k] = i < n ? where[i] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kUnroll; k++) {
+      const uint64_t i = i0 + k * stride;
+      if (i < n) out[i] = v[k] ? bres[w[k]] : static_cast<uint16_t>(0);
+    }
+  }
 }
 
 }  // namespace
