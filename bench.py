@@ -362,6 +362,24 @@ def run_planb(args):
                "api": "planb_lookup_host (pinned host buffers, chunked H2D/kernel/D2H pipeline)"}
         if not np.array_equal(po.numpy().view(np.uint16)[idx], want):
             raise SystemExit("e2e parity failure")
+        # the same through planb_lookup_mapped: the kernel reads the pinned addresses and writes
+        # the next hops over the host link itself, no copy engine in between
+        po.fill_(-1)
+        fib.lookup_mapped(ph, pl, po, stream)
+        stream.synchronize()
+        if not np.array_equal(po.numpy().view(np.uint16)[idx], want):
+            raise SystemExit("mapped e2e parity failure")
+        barrier(dist, local)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            fib.lookup_mapped(ph, pl, po, stream)
+        stream.synchronize()
+        barrier(dist, local)
+        dt = max_over_ranks(dist, time.perf_counter() - t0, True)
+        e2e["mapped"] = {"value": n * world * args.e2e_steps / dt / 1e9, "unit": UNIT,
+                         "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 2 * n,
+                         "api": "planb_lookup_mapped (pinned host buffers read and written by "
+                                "the lookup kernel over the host link)"}
         del ph, pl, po
 
     # p50/p99 latency of 2^16-address batches, each launch event-timed

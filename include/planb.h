@@ -195,6 +195,19 @@ typedef struct {
                    earlier in the same batch) is a counted no-op */
 
 /*
+ * planb_lookup_mapped — planb_lookup on page-locked host buffers, read and written by the lookup
+ * kernel itself over the host link (on a Grace-Blackwell node, NVLink-C2C) instead of being copied:
+ * the address stream goes straight from host memory into the descent and the next hops straight
+ * back. addr_hi, addr_lo, out: host arrays of n entries in page-locked memory the device can address
+ * (cudaHostAlloc, or cudaHostRegister with the mapped flag; a PyTorch pinned tensor); asynchronous
+ * on `stream` like planb_lookup. The paper has no counterpart (its lookups run where the packets
+ * are). Errors: PLANB_EINVAL (null, misaligned, or a buffer that is not such memory: nothing is
+ * launched), PLANB_ECUDA.
+ */
+int planb_lookup_mapped(const planb_fib *fib, const uint64_t *addr_hi, const uint64_t *addr_lo,
+                        size_t n, uint16_t *out, planb_stream_t stream);
+
+/*
  * planb_update — applies a batch of route changes by rebuild-and-swap (Section 3.6, "Dynamic FIB
  * Update"): the changes are merged into the table's canonical prefix list (withdraws first, then
  * inserts, each batch in order), a complete new table is built and uploaded, and the fib is

@@ -88,6 +88,7 @@ _SIGS = {
     "planb_lookup_host": (C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     "planb_update": (C.c_int, [_vp, _vp, _sz, _vp, _sz, _vp]),
     "planb_forget_stream": (C.c_int, [_vp, _vp]),
+    "planb_lookup_mapped": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_stats": (C.c_int, [_vp, _vp]),
     "planb_device_status": (C.c_int, [_vp, C.POINTER(C.c_uint32)]),
     "planb_destroy": (None, [_vp]),
@@ -302,6 +303,21 @@ class Fib:
         """Same as lookup on raw device pointers (for timing loops)."""
         _check(self._lib.planb_lookup(self._h, C.c_void_p(hi_ptr), C.c_void_p(lo_ptr), n,
                                       C.c_void_p(out_ptr), _stream_handle(stream)), "planb_lookup")
+
+    def lookup_mapped(self, addr_hi, addr_lo, out, stream=None):
+        """Lookups on pinned host tensors read and written directly by the kernel (no copies);
+        asynchronous on `stream`."""
+        for t in (addr_hi, addr_lo, out):
+            if t.is_cuda or not t.is_pinned() or not t.is_contiguous():
+                raise ValueError("lookup_mapped takes contiguous pinned host tensors")
+        n = addr_hi.numel()
+        if addr_lo.numel() != n or out.numel() != n or out.element_size() != 2:
+            raise ValueError("buffer sizes differ")
+        _check(self._lib.planb_lookup_mapped(self._h, C.c_void_p(addr_hi.data_ptr()),
+                                             C.c_void_p(addr_lo.data_ptr()), n,
+                                             C.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "planb_lookup_mapped")
+        return out
 
     def lookup_host(self, addr_hi, addr_lo, out=None):
         """Next hops of host arrays (numpy, or CPU tensors — pinned for full speed); synchronous."""

@@ -555,6 +555,42 @@ int planb_lookup(const planb_fib* fib_c, const uint64_t* d_addr_hi, const uint64
   return planb::launch_lookup(t->dt, t->cfg, d_addr_hi, d_addr_lo, n, d_out, f->d_status, stream);
 }
 
+int planb_lookup_mapped(const planb_fib* fib_c, const uint64_t* addr_hi, const uint64_t* addr_lo,
+                        size_t n, uint16_t* out, planb_stream_t stream) {
+  if (!fib_c) return PLANB_EINVAL;
+  if (n == 0) return PLANB_OK;
+  if (!addr_hi || !addr_lo || !out) return PLANB_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(addr_hi) | reinterpret_cast<uintptr_t>(addr_lo)) & 7u ||
+      reinterpret_cast<uintptr_t>(out) & 1u)
+    return PLANB_EINVAL;
+  planb_fib* f = const_cast<planb_fib*>(fib_c);
+  DeviceGuard g(f->device);
+  if (!g.ok) return PLANB_ECUDA;
+  // each buffer must be page-locked host memory the device can address (else no launch at all)
+  const void* host[3] = {addr_hi, addr_lo, out};
+  void* dev[3] = {nullptr, nullptr, nullptr};
+  for (int i = 0; i < 3; i++) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return fail_detail(PLANB_EINVAL, "mapped lookup: not page-locked host memory");
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer)
+      return fail_detail(PLANB_EINVAL, "mapped lookup: not page-locked host memory");
+    dev[i] = a.devicePointer;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::shared_ptr<Table> t;
+  {
+    std::lock_guard<std::mutex> lk(f->cur_mu);
+    t = f->cur;
+    note_stream(f, st);
+  }
+  return planb::launch_lookup(t->dt, t->cfg, static_cast<const uint64_t*>(dev[0]),
+                              static_cast<const uint64_t*>(dev[1]), n,
+                              static_cast<uint16_t*>(dev[2]), f->d_status, st);
+}
+
 int planb_lookup_host(planb_fib* f, const uint64_t* addr_hi, const uint64_t* addr_lo, size_t n,
                       uint16_t* out) {
   if (!f) return PLANB_EINVAL;

@@ -249,11 +249,26 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
 
   const Seg seg = segment<MULTI>(p);
+  // the addresses of a warp's next tile are loaded while it works on the current one, so the
+  // stream's HBM latency overlaps the descent
+  uint64_t nx_hi = 0, nx_lo = 0;
+  {
+    const uint64_t first = warp * 32 + lane;
+    if (first < seg.n) {
+      nx_hi = p.xhi[seg.off + first];
+      nx_lo = p.xlo[seg.off + first];
+    }
+  }
   for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
     const uint64_t mine = base + lane;
     const bool ok = mine < seg.n;
-    const uint64_t my_hi = ok ? p.xhi[seg.off + mine] : 0ull;
-    const uint64_t my_lo = ok ? p.xlo[seg.off + mine] : 0ull;
+    const uint64_t my_hi = nx_hi;
+    const uint64_t my_lo = nx_lo;
+    {
+      const uint64_t next = mine + nwarps * 32;
+      nx_hi = next < seg.n ? p.xhi[seg.off + next] : 0ull;
+      nx_lo = next < seg.n ? p.xlo[seg.off + next] : 0ull;
+    }
     // phase A: per-thread count over the level-S subtree maxima in shared memory
     uint32_t cnt = 0;
     bool have = false;

@@ -236,3 +236,34 @@ def test_tables_sharing_a_kernel_with_different_shared_memory():
         for f, fib in ((big, fb), (small, fs)):
             xh, xl = synth.gen_trace(f, 100_000, seed=403)
             assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl))
+
+
+def test_mapped_lookup_on_pinned_host_buffers():
+    """planb_lookup_mapped: the kernel reads pinned host addresses and writes pinned host results
+    directly; unpinned buffers are refused before anything is launched."""
+    import ctypes
+    f = synth.gen_fib(30_000, seed=901, nh_max=4095)
+    xh, xl = synth.gen_trace(f, 1_000_003, seed=902)
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh) as fib:
+        ph = torch.from_numpy(xh.view(np.int64)).pin_memory()
+        pl = torch.from_numpy(xl.view(np.int64)).pin_memory()
+        po = torch.full((xh.size,), -1, dtype=torch.int16).pin_memory()
+        s = torch.cuda.Stream()
+        fib.lookup_mapped(ph, pl, po, s)
+        s.synchronize()
+        assert np.array_equal(po.numpy().view(np.uint16), want)
+        # a slice at an offset inside the pinned buffers
+        k0, k1 = 12_345, 600_001
+        po2 = torch.full((k1 - k0,), -1, dtype=torch.int16).pin_memory()
+        fib.lookup_mapped(ph[k0:k1], pl[k0:k1], po2, s)
+        s.synchronize()
+        assert np.array_equal(po2.numpy().view(np.uint16), want[k0:k1])
+        # pageable memory: refused by the library itself
+        hh, hl = np.ascontiguousarray(xh[:1000]), np.ascontiguousarray(xl[:1000])
+        out = np.zeros(1000, np.uint16)
+        rc = fib._lib.planb_lookup_mapped(fib._h, ctypes.c_void_p(hh.ctypes.data),
+                                          ctypes.c_void_p(hl.ctypes.data), 1000,
+                                          ctypes.c_void_p(out.ctypes.data), None)
+        assert rc == -1   # PLANB_EINVAL
+        assert np.all(out == 0)
