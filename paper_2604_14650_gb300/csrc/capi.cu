@@ -967,7 +967,10 @@ struct planb_multi {
   uint32_t G = 0;                // bucketing chunks
   void* mem = nullptr;
   uint64_t *bhi = nullptr, *blo = nullptr, *range = nullptr;
-  uint32_t *where = nullptr, *counts = nullptr;
+  uint16_t* where = nullptr;      // each address's slot in its bucketing tile
+  uint32_t* counts = nullptr;
+  uint32_t* tile_start = nullptr; // per bucketing tile and table: run start in the bucketed arrays
+  uint16_t* tile_base = nullptr;  // ... and its first slot in the tile
   uint16_t* bres = nullptr;      // results in bucketed order
   planb::MultiDesc* desc = nullptr;  // per-table descriptors of the single persistent launch
   bool persist = false;          // the current tables all fit the single persistent launch
@@ -998,7 +1001,8 @@ int multi_pipeline(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cu
                    const uint64_t* d_addr_hi, const uint64_t* d_addr_lo, const uint8_t* d_table,
                    size_t n, uint16_t* d_out, cudaStream_t s, const uint64_t* d_n, bool fork) {
   int rc = planb::launch_bucketing(d_addr_hi, d_addr_lo, d_table, n, m->T, m->G, m->counts,
-                                   m->range, m->bhi, m->blo, m->where, s, d_n);
+                                   m->range, m->bhi, m->blo, m->where, m->tile_start,
+                                   m->tile_base, s, d_n);
   if (rc) return fail_detail(rc, "multi: bucketing", cudaGetLastError());
   cudaError_t e = cudaSuccess;
   fork = fork && !m->persist;
@@ -1027,7 +1031,8 @@ int multi_pipeline(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cu
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, m->join[k], 0);
   }
   if (e != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: join", e);
-  rc = planb::launch_gather(d_table, m->where, m->bres, n, m->T, m->G, d_out, s, d_n);
+  rc = planb::launch_gather(m->where, m->tile_start, m->tile_base, m->bres, n, m->T, m->G, d_out,
+                            s, d_n);
   if (rc) return fail_detail(rc, "multi: gather", cudaGetLastError());
   return PLANB_OK;
 }
@@ -1062,11 +1067,14 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     m->G = static_cast<uint32_t>(sms) * 8u;
     const size_t cap = max_batch;
     auto up = [](size_t x) { return ((x + 255) / 256) * 256; };
-    const size_t where_off = cap * 16, bres_off = where_off + up(cap * 4),
+    const size_t tiles = planb::bucketing_tiles(cap, m->G) * (m->T + 1);
+    const size_t where_off = cap * 16, bres_off = where_off + up(cap * 2),
                  counts_off = bres_off + up(cap * 2),
                  range_off = counts_off + up(static_cast<size_t>(m->T + 1) * m->G * 4);
     const size_t desc_off = range_off + up((2 * m->T + 4) * 8);
-    const size_t bytes = desc_off + m->T * sizeof(planb::MultiDesc);
+    const size_t tstart_off = desc_off + up(m->T * sizeof(planb::MultiDesc));
+    const size_t tbase_off = tstart_off + up(tiles * 4);
+    const size_t bytes = tbase_off + up(tiles * 2);
     if (cudaMalloc(&m->mem, bytes) != cudaSuccess) {
       m->mem = nullptr;
       cudaGetLastError();
@@ -1075,7 +1083,9 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     char* b = static_cast<char*>(m->mem);
     m->bhi = reinterpret_cast<uint64_t*>(b);
     m->blo = m->bhi + cap;
-    m->where = reinterpret_cast<uint32_t*>(b + where_off);
+    m->where = reinterpret_cast<uint16_t*>(b + where_off);
+    m->tile_start = reinterpret_cast<uint32_t*>(b + tstart_off);
+    m->tile_base = reinterpret_cast<uint16_t*>(b + tbase_off);
     m->bres = reinterpret_cast<uint16_t*>(b + bres_off);
     m->counts = reinterpret_cast<uint32_t*>(b + counts_off);
     m->range = reinterpret_cast<uint64_t*>(b + range_off);

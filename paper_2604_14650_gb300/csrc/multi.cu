@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(kScatterThreads)
                       const uint8_t* __restrict__ tid, uint64_t n, uint32_t T, uint64_t chunk,
                       const uint32_t* __restrict__ offsets, const uint64_t* __restrict__ range,
                       uint64_t* __restrict__ bhi, uint64_t* __restrict__ blo,
-                      uint32_t* __restrict__ where, const uint64_t* __restrict__ d_n) {
+                      uint16_t* __restrict__ where, uint32_t* __restrict__ tile_start,
+                      uint16_t* __restrict__ tile_base, const uint64_t* __restrict__ d_n) {
   typedef cub::BlockScan<uint32_t, kScatterThreads> Scan;
   __shared__ typename Scan::TempStorage scan_tmp;
   __shared__ uint32_t cur[256], cnt[256], base[256];
@@ -132,7 +133,9 @@ __global__ void __launch_bounds__(kScatterThreads)
     cur[t] = static_cast<uint32_t>(range[t]) + offsets[t * gridDim.x + blockIdx.x];
   const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * chunk;
   const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
-  for (uint64_t tb = b0; tb < b1; tb += kTile) {
+  const uint64_t tiles_per_chunk = (chunk + kTile - 1) / kTile;
+  uint64_t tile = static_cast<uint64_t>(blockIdx.x) * tiles_per_chunk;
+  for (uint64_t tb = b0; tb < b1; tb += kTile, tile++) {
     for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) cnt[t] = 0;
     __syncthreads();
     uint32_t tt[kScatterItems], rank[kScatterItems];
@@ -160,7 +163,12 @@ __global__ void __launch_bounds__(kScatterThreads)
     {
       uint32_t v = threadIdx.x <= T ? cnt[threadIdx.x] : 0u, excl = 0;
       Scan(scan_tmp).ExclusiveSum(v, excl);
-      if (threadIdx.x <= T) base[threadIdx.x] = excl;
+      if (threadIdx.x <= T) {
+        base[threadIdx.x] = excl;
+        // for the gather: where each table's run of this tile starts, in the tile and globally
+        tile_start[tile * (T + 1) + threadIdx.x] = cur[threadIdx.x];
+        tile_base[tile * (T + 1) + threadIdx.x] = static_cast<uint16_t>(excl);
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(kScatterThreads)
         s_hi[slot] = vh[k];
         s_lo[slot] = vl[k];
         s_t[slot] = static_cast<uint8_t>(t);
-        where[e] = cur[t] + rank[k];
+        where[e] = static_cast<uint16_t>(slot);
       }
     }
     __syncthreads();
@@ -189,40 +197,58 @@ __global__ void __launch_bounds__(kScatterThreads)
   }
 }
 
-// out[i] = the result at the bucketed position of address i; 0 for an id beyond the tables
-__global__ void mt_gather_kernel(const uint8_t* __restrict__ tid, const uint32_t* __restrict__ where,
-                                 const uint16_t* __restrict__ bres, uint64_t n, uint32_t T,
-                                 uint16_t* __restrict__ out, const uint64_t* __restrict__ d_n) {
-  if (d_n) {
-    const uint64_t dn = *d_n;
-    n = dn < n ? dn : n;
-  }
-  // eight independent (id, position, result) chains per thread per step keep reads in flight
-  constexpr int kUnroll = 8;
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  for (uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i0 < n;
-       i0 += kUnroll * stride) {
-    uint32_t w[kUnroll];
-    bool v[kUnroll];
-#pragma unroll
-    for (int k = 0; k < kUnroll; k++) {
-      const uint64_t i = i0 + k * stride;
-      v[k] = i < n && tid[i] < T;
-      w[k] = i < n ? where[i] : 0u;
+// The gather, tile by tile in the scatter's decomposition: a tile's results are its tables' runs
+// of the bucketed results (each run contiguous), read into shared memory in slot order; then
+// out[i] = the result at address i's slot, coalesced in input order. Slots of ids beyond the tables
+// read 0.
+constexpr int kGatherThreads = 256;
+
+__global__ void __launch_bounds__(kGatherThreads)
+    mt_gather_kernel(const uint16_t* __restrict__ where, const uint32_t* __restrict__ tile_start,
+                     const uint16_t* __restrict__ tile_base, const uint16_t* __restrict__ bres,
+                     uint64_t n, uint32_t T, uint64_t chunk, uint16_t* __restrict__ out,
+                     const uint64_t* __restrict__ d_n) {
+  __shared__ uint32_t st[256];
+  __shared__ uint32_t sb[256];
+  __shared__ uint16_t res[kTile];
+  batch_shape(d_n, n, chunk);
+  const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * chunk;
+  const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+  const uint64_t tiles_per_chunk = (chunk + kTile - 1) / kTile;
+  uint64_t tile = static_cast<uint64_t>(blockIdx.x) * tiles_per_chunk;
+  for (uint64_t tb = b0; tb < b1; tb += kTile, tile++) {
+    const uint32_t m = static_cast<uint32_t>(b1 - tb < kTile ? b1 - tb : kTile);
+    for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) {
+      st[t] = tile_start[tile * (T + 1) + t];
+      sb[t] = tile_base[tile * (T + 1) + t];
     }
-#pragma unroll
-    for (int k = 0; k < kUnroll; k++) {
-      const uint64_t i = i0 + k * stride;
-      if (i < n) out[i] = v[k] ? bres[w[k]] : static_cast<uint16_t>(0);
+    __syncthreads();
+    for (uint32_t slot = threadIdx.x; slot < m; slot += blockDim.x) {
+      // the table of this slot: the last t with sb[t] <= slot (empty tables share the next base)
+      uint32_t lo = 0, hi = T + 1;
+      while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (sb[mid] <= slot) lo = mid; else hi = mid;
+      }
+      res[slot] = lo < T ? bres[st[lo] + (slot - sb[lo])] : static_cast<uint16_t>(0);
     }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) out[tb + k] = res[where[tb + k]];
+    __syncthreads();
   }
 }
 
 }  // namespace
 
+size_t bucketing_tiles(size_t cap, uint32_t G) {
+  const size_t chunk = cap ? (cap + G - 1) / G : 1;
+  return static_cast<size_t>(G) * ((chunk + kTile - 1) / kTile);
+}
+
 int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
                      uint32_t T, uint32_t G, uint32_t* d_counts, uint64_t* d_range,
-                     uint64_t* d_bhi, uint64_t* d_blo, uint32_t* d_where, void* stream,
+                     uint64_t* d_bhi, uint64_t* d_blo, uint16_t* d_where,
+                     uint32_t* d_tile_start, uint16_t* d_tile_base, void* stream,
                      const uint64_t* d_n) {
   if (T == 0 || T > 255 || G == 0 || n >= (uint64_t(1) << 32)) return PLANB_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -235,17 +261,18 @@ int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* 
   mt_tablescan_kernel<<<1, 256, 0, st>>>(
       totals, T, d_range, reinterpret_cast<unsigned long long*>(d_range + 2 * T + 3));
   mt_scatter_kernel<<<G, kScatterThreads, 0, st>>>(d_hi, d_lo, d_tid, n, T, chunk, d_counts,
-                                                    d_range, d_bhi, d_blo, d_where, d_n);
+                                                    d_range, d_bhi, d_blo, d_where, d_tile_start,
+                                                    d_tile_base, d_n);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 
-int launch_gather(const uint8_t* d_tid, const uint32_t* d_where, const uint16_t* d_bres, size_t n,
-                  uint32_t T, uint32_t G, uint16_t* d_out, void* stream, const uint64_t* d_n) {
-  const uint64_t want = (static_cast<uint64_t>(n) + 255) / 256;
-  const unsigned blocks = static_cast<unsigned>(want < G ? (want ? want : 1) : G);
+int launch_gather(const uint16_t* d_where, const uint32_t* d_tile_start,
+                  const uint16_t* d_tile_base, const uint16_t* d_bres, size_t n, uint32_t T,
+                  uint32_t G, uint16_t* d_out, void* stream, const uint64_t* d_n) {
+  const uint64_t chunk = n ? (n + G - 1) / G : 1;
   cudaGetLastError();
-  mt_gather_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(d_tid, d_where, d_bres,
-                                                                          n, T, d_out, d_n);
+  mt_gather_kernel<<<G, kGatherThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      d_where, d_tile_start, d_tile_base, d_bres, n, T, chunk, d_out, d_n);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

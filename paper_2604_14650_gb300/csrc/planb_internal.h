@@ -255,19 +255,26 @@ int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t*
                             size_t smem_bytes, void* stream);
 
 // Multi-table bucketing (multi.cu): groups n addresses by their u8 table id (ids >= T form one
-// extra segment) into d_bhi/d_blo, table-major, with d_where[i] = the bucketed position of address
-// i; d_range[t] .. d_range[t+1] bound table t's segment; d_range has room for 2T + 4 words (then
-// T + 1 words of scratch, then the persistent lookup's work counter, which is reset to 0).
-// d_counts holds (T+1) x G words. n < 2^32.
-// With d_n the kernels read the batch size from device memory (n then only bounds it).
+// extra segment) into d_bhi/d_blo, table-major; d_range[t] .. d_range[t+1] bound table t's
+// segment; d_range has room for 2T + 4 words (then T + 1 words of scratch, then the persistent
+// lookup's work counter, which is reset to 0). d_counts holds (T+1) x G words. The batch is cut
+// into G chunks and each chunk into tiles of up to 2,048 addresses: d_where[i] is address i's slot
+// within its tile (the tile's addresses in table order), and for tile k and table t,
+// d_tile_start[k(T+1) + t] and d_tile_base[k(T+1) + t] are where the tile's run of table t starts
+// in the bucketed arrays and at which slot. The tile arrays hold bucketing_tiles(n bound, G) x
+// (T+1) entries. n < 2^32. With d_n the kernels read the batch size from device memory (n then
+// only bounds it).
+size_t bucketing_tiles(size_t cap, uint32_t G);
 int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
                      uint32_t T, uint32_t G, uint32_t* d_counts, uint64_t* d_range,
-                     uint64_t* d_bhi, uint64_t* d_blo, uint32_t* d_where, void* stream,
+                     uint64_t* d_bhi, uint64_t* d_blo, uint16_t* d_where,
+                     uint32_t* d_tile_start, uint16_t* d_tile_base, void* stream,
                      const uint64_t* d_n = nullptr);
-// d_out[i] = d_bres[d_where[i]] for ids below T, else 0 (at most G blocks; d_n as above).
-int launch_gather(const uint8_t* d_tid, const uint32_t* d_where, const uint16_t* d_bres, size_t n,
-                  uint32_t T, uint32_t G, uint16_t* d_out, void* stream,
-                  const uint64_t* d_n = nullptr);
+// d_out[i] = the bucketed result of address i (d_bres in bucketed order), 0 for ids >= T, using
+// the tile records of launch_bucketing (same n, G and d_n).
+int launch_gather(const uint16_t* d_where, const uint32_t* d_tile_start,
+                  const uint16_t* d_tile_base, const uint16_t* d_bres, size_t n, uint32_t T,
+                  uint32_t G, uint16_t* d_out, void* stream, const uint64_t* d_n = nullptr);
 
 // cudaFuncGetAttributes of the lookup kernel a table uses (multi: its multi-table form):
 // out[0..5] = registers, max threads per block, max dynamic shared bytes, local bytes, static shared
