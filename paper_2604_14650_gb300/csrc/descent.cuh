@@ -42,11 +42,27 @@ __device__ __forceinline__ uint32_t count_below(Load load, uint32_t n, uint64_t 
 // entry with an equal high half by its low half (read from the global index). With a radix
 // directory the search starts in the entries of the address's bucket: entries of lower buckets
 // have smaller high halves, entries of higher buckets larger ones.
+// An address's low half, read from memory the first time a comparison needs it (only when a key's
+// high half equals the address's, which is rare), so the common lookup reads 8 bytes of address.
+// (The address of the low half is passed to each get() rather than kept, to spare registers.)
+struct LazyLo {
+  uint64_t v;
+  bool have;
+  __device__ __forceinline__ explicit LazyLo(bool ok) : v(0), have(!ok) {}
+  __device__ __forceinline__ uint64_t get(const uint64_t* src) {
+    if (!have) {
+      v = *src;
+      have = true;
+    }
+    return v;
+  }
+};
+
 __device__ __forceinline__ uint32_t index_count(const uint64_t* Uh, uint32_t N,
                                                 const uint16_t* Dir, uint32_t dir_bits,
                                                 uint32_t dir_shift, uint64_t dir_base,
                                                 const ulonglong2* sidx, uint64_t my_hi,
-                                                uint64_t my_lo) {
+                                                LazyLo& my_lo, const uint64_t* lo_src) {
   uint32_t lo = 0, n = N;
   if (dir_bits) {
     const uint64_t v = my_hi >> dir_shift;
@@ -66,7 +82,7 @@ __device__ __forceinline__ uint32_t index_count(const uint64_t* Uh, uint32_t N,
     }
     cnt = b + (Uh[b] < my_hi ? 1u : 0u);
   }
-  while (cnt < N && Uh[cnt] == my_hi && __ldg(&sidx[cnt].y) < my_lo) cnt++;
+  while (cnt < N && Uh[cnt] == my_hi && __ldg(&sidx[cnt].y) < my_lo.get(lo_src)) cnt++;
   return cnt;
 }
 

@@ -251,23 +251,20 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   const Seg seg = segment<MULTI>(p);
   // the addresses of a warp's next tile are loaded while it works on the current one, so the
   // stream's HBM latency overlaps the descent
-  uint64_t nx_hi = 0, nx_lo = 0;
+  uint64_t nx_hi = 0;
   {
     const uint64_t first = warp * 32 + lane;
-    if (first < seg.n) {
-      nx_hi = p.xhi[seg.off + first];
-      nx_lo = p.xlo[seg.off + first];
-    }
+    if (first < seg.n) nx_hi = p.xhi[seg.off + first];
   }
   for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
     const uint64_t mine = base + lane;
     const bool ok = mine < seg.n;
     const uint64_t my_hi = nx_hi;
-    const uint64_t my_lo = nx_lo;
+    LazyLo my_lo(ok);   // read on a high-half tie only
+    const uint64_t* lo_src = p.xlo + seg.off + mine;
     {
       const uint64_t next = mine + nwarps * 32;
       nx_hi = next < seg.n ? p.xhi[seg.off + next] : 0ull;
-      nx_lo = next < seg.n ? p.xlo[seg.off + next] : 0ull;
     }
     // phase A: per-thread count over the level-S subtree maxima in shared memory
     uint32_t cnt = 0;
@@ -275,7 +272,7 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
     if constexpr (LEARNED) {
       auto below = [&](uint32_t q) {   // index entry q < address
         const uint64_t h = Uh[q];
-        return h < my_hi || (h == my_hi && __ldg(&p.sidx[q].y) < my_lo);
+        return h < my_hi || (h == my_hi && __ldg(&p.sidx[q].y) < my_lo.get(lo_src));
       };
       const uint32_t leaf = predict_leaf(p.lp, my_hi);
       const uint32_t e = Le[leaf];
@@ -302,7 +299,8 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
       }
     }
     if (N && !have)
-      cnt = index_count(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, p.sidx, my_hi, my_lo);
+      cnt = index_count(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, p.sidx, my_hi, my_lo,
+                        lo_src);
     if constexpr (DB == 0) {
       uint32_t rank = cnt;
 #ifdef PLANB_BOUNDS_CHECK
@@ -347,7 +345,10 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
           if (__any_sync(kFull, anyeq)) {
 #pragma unroll
             for (int i = 0; i < kRounds; i++) {
-              const uint64_t ql = __shfl_sync(kFull, my_lo, gshift + r0 + i);
+              // the owner of address i of each group reads its low half if its group saw a tie
+              const uint32_t need = __ballot_sync(kFull, eq[i]) & gmask;
+              if (need && j == r0 + i) my_lo.get(lo_src);
+              const uint64_t ql = __shfl_sync(kFull, my_lo.v, gshift + r0 + i);
               lt[i] = lt[i] | (eq[i] & (key[i].y < ql));
             }
           }

@@ -209,8 +209,9 @@ __global__ void __launch_bounds__(kGatherThreads)
                      uint64_t n, uint32_t T, uint64_t chunk, uint16_t* __restrict__ out,
                      const uint64_t* __restrict__ d_n) {
   __shared__ uint32_t st[256];
-  __shared__ uint32_t sb[256];
+  __shared__ uint32_t sb[257];
   __shared__ uint16_t res[kTile];
+  constexpr uint32_t kPer = kTile / kGatherThreads;   // consecutive slots per thread
   batch_shape(d_n, n, chunk);
   const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * chunk;
   const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
@@ -222,15 +223,23 @@ __global__ void __launch_bounds__(kGatherThreads)
       st[t] = tile_start[tile * (T + 1) + t];
       sb[t] = tile_base[tile * (T + 1) + t];
     }
+    if (threadIdx.x == 0) sb[T + 1] = m;
     __syncthreads();
-    for (uint32_t slot = threadIdx.x; slot < m; slot += blockDim.x) {
-      // the table of this slot: the last t with sb[t] <= slot (empty tables share the next base)
+    // each thread fills kPer consecutive slots: one search for the first slot's table (the last t
+    // with sb[t] <= slot; empty tables share the next table's base), then a forward walk
+    const uint32_t s0 = threadIdx.x * kPer;
+    if (s0 < m) {
       uint32_t lo = 0, hi = T + 1;
       while (hi - lo > 1u) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (sb[mid] <= slot) lo = mid; else hi = mid;
+        if (sb[mid] <= s0) lo = mid; else hi = mid;
       }
-      res[slot] = lo < T ? bres[st[lo] + (slot - sb[lo])] : static_cast<uint16_t>(0);
+      uint32_t t = lo;
+      const uint32_t s1 = s0 + kPer < m ? s0 + kPer : m;
+      for (uint32_t slot = s0; slot < s1; slot++) {
+        while (sb[t + 1] <= slot) t++;
+        res[slot] = t < T ? bres[st[t] + (slot - sb[t])] : static_cast<uint16_t>(0);
+      }
     }
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) out[tb + k] = res[where[tb + k]];

@@ -43,9 +43,11 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
     const uint64_t mine = base + lane;
     const bool ok = mine < s1;
     const uint64_t my_hi = ok ? xhi[mine] : 0ull;
-    const uint64_t my_lo = ok ? xlo[mine] : 0ull;
+    LazyLo my_lo(ok);   // read on a high-half tie only
     const uint32_t cnt =
-        N ? index_count(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, sidx, my_hi, my_lo) : 0u;
+        N ? index_count(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, sidx, my_hi, my_lo,
+                        xlo + mine)
+          : 0u;
     uint32_t result = 0;
     if (db == 0) {
       uint32_t rank = cnt;
@@ -88,7 +90,9 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
           if (__any_sync(kFull, anyeq)) {
 #pragma unroll
             for (int i = 0; i < kRounds; i++) {
-              const uint64_t ql = __shfl_sync(kFull, my_lo, gshift + r0 + i);
+              const uint32_t need = __ballot_sync(kFull, eq[i]) & gmask;
+              if (need && j == r0 + i) my_lo.get(xlo + mine);
+              const uint64_t ql = __shfl_sync(kFull, my_lo.v, gshift + r0 + i);
               lt[i] = lt[i] | (eq[i] & (key[i].y < ql));
             }
           }
