@@ -359,7 +359,8 @@ def run_planb(args):
         dt = max_over_ranks(dist, time.perf_counter() - t0, True)
         e2e = {"value": n * world * args.e2e_steps / dt / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 2 * n,
-               "api": "planb_lookup_host (pinned host buffers, chunked H2D/kernel/D2H pipeline)"}
+               "api": "planb_lookup_host (pinned host buffers: the lookup kernel reads the "
+                      "addresses and writes the next hops over the host link)"}
         if not np.array_equal(po.numpy().view(np.uint16)[idx], want):
             raise SystemExit("e2e parity failure")
         # the same through planb_lookup_mapped: the kernel reads the pinned addresses and writes

@@ -170,11 +170,13 @@ int planb_lookup(const planb_fib *fib, const uint64_t *d_addr_hi, const uint64_t
                  size_t n, uint16_t *d_out, planb_stream_t stream);
 
 /*
- * planb_lookup_host — the same lookup for addresses and results in HOST memory: the library
- * copies the addresses to the device in chunks, runs the lookup kernel on each chunk and copies
- * the next hops back, overlapping the copies of one chunk with the lookup of another on its own
- * streams. It returns when every result is in `out` (synchronous). Page-locked (pinned) host
- * buffers give full copy bandwidth; pageable ones work but are slower.
+ * planb_lookup_host — the same lookup for addresses and results in HOST memory. When all three
+ * buffers are page-locked and device-addressable, the lookup kernel reads the addresses and writes
+ * the next hops over the host link itself, as planb_lookup_mapped does (an address's low half is
+ * read only on a tie of high halves). Otherwise the library copies the addresses to the device in
+ * chunks, runs the lookup kernel on each chunk and copies the next hops back, overlapping the
+ * copies of one chunk with the lookup of another on its own streams. Either way it returns when
+ * every result is in `out` (synchronous).
  *   addr_hi, addr_lo: host arrays of n uint64_t; out: host array of n uint16_t.
  *   The device staging buffers are owned by the fib and reused by later calls.
  * Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ECUDA.

@@ -555,6 +555,26 @@ int planb_lookup(const planb_fib* fib_c, const uint64_t* d_addr_hi, const uint64
   return planb::launch_lookup(t->dt, t->cfg, d_addr_hi, d_addr_lo, n, d_out, f->d_status, stream);
 }
 
+}  // extern "C"
+
+namespace {
+// The device addresses of page-locked host buffers (all of them, or false).
+bool device_view(const void* const* host, void** dev, int k) {
+  for (int i = 0; i < k; i++) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, host[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+    dev[i] = a.devicePointer;
+  }
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
 int planb_lookup_mapped(const planb_fib* fib_c, const uint64_t* addr_hi, const uint64_t* addr_lo,
                         size_t n, uint16_t* out, planb_stream_t stream) {
   if (!fib_c) return PLANB_EINVAL;
@@ -569,16 +589,8 @@ int planb_lookup_mapped(const planb_fib* fib_c, const uint64_t* addr_hi, const u
   // each buffer must be page-locked host memory the device can address (else no launch at all)
   const void* host[3] = {addr_hi, addr_lo, out};
   void* dev[3] = {nullptr, nullptr, nullptr};
-  for (int i = 0; i < 3; i++) {
-    cudaPointerAttributes a{};
-    if (cudaPointerGetAttributes(&a, host[i]) != cudaSuccess) {
-      cudaGetLastError();
-      return fail_detail(PLANB_EINVAL, "mapped lookup: not page-locked host memory");
-    }
-    if (a.type != cudaMemoryTypeHost || !a.devicePointer)
-      return fail_detail(PLANB_EINVAL, "mapped lookup: not page-locked host memory");
-    dev[i] = a.devicePointer;
-  }
+  if (!device_view(host, dev, 3))
+    return fail_detail(PLANB_EINVAL, "mapped lookup: not page-locked host memory");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   std::shared_ptr<Table> t;
   {
@@ -588,7 +600,8 @@ int planb_lookup_mapped(const planb_fib* fib_c, const uint64_t* addr_hi, const u
   }
   return planb::launch_lookup(t->dt, t->cfg, static_cast<const uint64_t*>(dev[0]),
                               static_cast<const uint64_t*>(dev[1]), n,
-                              static_cast<uint16_t*>(dev[2]), f->d_status, st);
+                              static_cast<uint16_t*>(dev[2]), f->d_status, st, nullptr, nullptr,
+                              true);
 }
 
 int planb_lookup_host(planb_fib* f, const uint64_t* addr_hi, const uint64_t* addr_lo, size_t n,
@@ -617,6 +630,21 @@ int planb_lookup_host(planb_fib* f, const uint64_t* addr_hi, const uint64_t* add
     std::lock_guard<std::mutex> lk(f->cur_mu);
     t = f->cur;
     for (int s = 0; s < kHostSlots; s++) note_stream(f, f->hs[s]);
+  }
+  // page-locked buffers: the kernel reads and writes them over the host link itself (no copies;
+  // low halves only on a tie), which moves fewer bytes than the copy pipeline below
+  {
+    const void* host[3] = {addr_hi, addr_lo, out};
+    void* dev[3] = {nullptr, nullptr, nullptr};
+    if (!((reinterpret_cast<uintptr_t>(addr_hi) | reinterpret_cast<uintptr_t>(addr_lo)) & 7u) &&
+        !(reinterpret_cast<uintptr_t>(out) & 1u) && device_view(host, dev, 3)) {
+      int rc = planb::launch_lookup(t->dt, t->cfg, static_cast<const uint64_t*>(dev[0]),
+                                    static_cast<const uint64_t*>(dev[1]), n,
+                                    static_cast<uint16_t*>(dev[2]), f->d_status, f->hs[0],
+                                    nullptr, nullptr, true);
+      if (cudaStreamSynchronize(f->hs[0]) != cudaSuccess) rc = PLANB_ECUDA;
+      return rc;
+    }
   }
   int rc = PLANB_OK;
   size_t chunk_id = 0;

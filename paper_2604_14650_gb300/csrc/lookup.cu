@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
 // buckets of ranks [rank - e, rank + e], and a short search among them gives the count — accepted
 // only when the entries just outside the window bracket the address (so the count is exact whatever
 // the model said). Otherwise, and for leaves marked for the tree, the full binary search runs.
-template <int DB, bool PACKED, bool LEARNED, bool MULTI>
+template <int DB, bool PACKED, bool LEARNED, bool MULTI, bool LAZY = false>
 __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
@@ -251,20 +251,30 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   const Seg seg = segment<MULTI>(p);
   // the addresses of a warp's next tile are loaded while it works on the current one, so the
   // stream's HBM latency overlaps the descent
-  uint64_t nx_hi = 0;
+  // LAZY (addresses in host memory, read over the host link): an address's low half is read only
+  // on a high-half tie; otherwise it is loaded, and prefetched, with the high half
+  uint64_t nx_hi = 0, nx_lo = 0;
   {
     const uint64_t first = warp * 32 + lane;
-    if (first < seg.n) nx_hi = p.xhi[seg.off + first];
+    if (first < seg.n) {
+      nx_hi = p.xhi[seg.off + first];
+      if (!LAZY) nx_lo = p.xlo[seg.off + first];
+    }
   }
   for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
     const uint64_t mine = base + lane;
     const bool ok = mine < seg.n;
     const uint64_t my_hi = nx_hi;
-    LazyLo my_lo(ok);   // read on a high-half tie only
+    LazyLo my_lo(ok);
+    if (!LAZY) {
+      my_lo.v = nx_lo;
+      my_lo.have = true;
+    }
     const uint64_t* lo_src = p.xlo + seg.off + mine;
     {
       const uint64_t next = mine + nwarps * 32;
       nx_hi = next < seg.n ? p.xhi[seg.off + next] : 0ull;
+      if (!LAZY) nx_lo = next < seg.n ? p.xlo[seg.off + next] : 0ull;
     }
     // phase A: per-thread count over the level-S subtree maxima in shared memory
     uint32_t cnt = 0;
@@ -420,7 +430,7 @@ typedef void (*KernelFn)(const KParams);
 
 constexpr int kMaxDepth = 10;
 
-KernelFn kernel_for(const DevTable& t, bool multi = false) {
+KernelFn kernel_for(const DevTable& t, bool multi = false, bool lazy = false) {
   static const KernelFn f8[kMaxDepth + 1] = {
       nullptr,            lookup_coop_f8<1>, lookup_coop_f8<2>, lookup_coop_f8<3>,
       lookup_coop_f8<4>,  lookup_coop_f8<5>, lookup_coop_f8<6>, lookup_coop_f8<7>,
@@ -443,12 +453,25 @@ KernelFn kernel_for(const DevTable& t, bool multi = false) {
   static const KernelFn hyb_multi[2][kMaxDepth + 1] = {PLANB_HYB(false, false, true),
                                                        PLANB_HYB(true, false, true)};
 #undef PLANB_HYB
+#define PLANB_HYB_LAZY(P)                                                                       \
+  {                                                                                               \
+    lookup_hybrid<0, P, false, false, true>, lookup_hybrid<1, P, false, false, true>,            \
+        lookup_hybrid<2, P, false, false, true>, lookup_hybrid<3, P, false, false, true>,        \
+        lookup_hybrid<4, P, false, false, true>, lookup_hybrid<5, P, false, false, true>,        \
+        lookup_hybrid<6, P, false, false, true>, lookup_hybrid<7, P, false, false, true>,        \
+        lookup_hybrid<8, P, false, false, true>, lookup_hybrid<9, P, false, false, true>,        \
+        lookup_hybrid<10, P, false, false, true>                                                  \
+  }
+  static const KernelFn hyb_lazy[2][kMaxDepth + 1] = {PLANB_HYB_LAZY(false), PLANB_HYB_LAZY(true)};
+#undef PLANB_HYB_LAZY
   const uint32_t D = t.depth;
   if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
   if (t.format == PLANB_FMT_F16HI) return f16[D];
   const bool packed = t.format == PLANB_FMT_F8V7;
   if (t.kernel == kHybrid && multi)
     return t.smem_levels <= D ? hyb_multi[packed][D - t.smem_levels] : nullptr;
+  if (t.kernel == kHybrid && lazy)
+    return t.smem_levels <= D ? hyb_lazy[packed][D - t.smem_levels] : nullptr;
   if (t.kernel == kHybrid || t.kernel == kLearned)
     return t.smem_levels <= D ? hyb[packed][t.kernel == kLearned][D - t.smem_levels] : nullptr;
   if (packed) return nullptr;
@@ -514,7 +537,8 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
   // The dynamic shared-memory limit is a property of the kernel function, which tables of other
   // sizes share: raise it once to the device's opt-in maximum rather than to this table's need
   // (a later, smaller table would otherwise lower it under an earlier one).
-  for (KernelFn f : {fn, (t.kernel == kHybrid) ? kernel_for(t, true) : nullptr}) {
+  for (KernelFn f : {fn, (t.kernel == kHybrid) ? kernel_for(t, true) : nullptr,
+                     (t.kernel == kHybrid) ? kernel_for(t, false, true) : nullptr}) {
     if (!f) continue;
     int limit = 0;
     if (int rc = dynamic_smem_limit(reinterpret_cast<const void*>(f), device, &limit)) return rc;
@@ -537,11 +561,12 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
 
 int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   const uint64_t* d_lo, size_t n, uint16_t* d_out, uint32_t* d_status,
-                  void* stream, const uint64_t* d_range, const uint32_t* d_perm) {
+                  void* stream, const uint64_t* d_range, const uint32_t* d_perm,
+                  bool lazy_lo) {
   if (n == 0) return PLANB_OK;
   const bool multi = d_range != nullptr || d_perm != nullptr;
   if (multi && t.kernel == kLearned) return PLANB_EINVAL;   // no multi-table form
-  KernelFn fn = kernel_for(t, multi);
+  KernelFn fn = kernel_for(t, multi, lazy_lo && !multi);
   if (!fn) return PLANB_EINVAL;
   cudaGetLastError();   // the check below is about this launch, not an earlier call's leftover
   KParams p;

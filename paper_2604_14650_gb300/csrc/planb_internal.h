@@ -217,11 +217,13 @@ struct LaunchCfg {
 
 // Launches the lookup kernel for one table on `stream`. d_status may be null. With d_range (device
 // [begin, end)) the launch handles addresses begin..end-1 of d_hi/d_lo instead of 0..n-1 (n then only
-// sizes the grid); with d_perm the result of address j is stored at d_out[d_perm[j]].
+// sizes the grid); with d_perm the result of address j is stored at d_out[d_perm[j]]. lazy_lo (hybrid
+// tables, single table): read an address's low half only on a high-half tie, for addresses that
+// live in host memory and cross the host link.
 int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   const uint64_t* d_lo, size_t n, uint16_t* d_out, uint32_t* d_status,
                   void* stream, const uint64_t* d_range = nullptr,
-                  const uint32_t* d_perm = nullptr);
+                  const uint32_t* d_perm = nullptr, bool lazy_lo = false);
 
 // One table of the single-launch multi-table kernel (F8X128 or F8V7 tables of the hybrid kernel).
 struct MultiDesc {

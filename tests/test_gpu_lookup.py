@@ -154,8 +154,11 @@ def test_lookup_host_matches_device_path():
         pin_h = torch.from_numpy(xh.view(np.int64)).pin_memory()
         pin_l = torch.from_numpy(xl.view(np.int64)).pin_memory()
         out = torch.empty(n, dtype=torch.int16).pin_memory()
-        fib.lookup_host(pin_h, pin_l, out=out)
+        fib.lookup_host(pin_h, pin_l, out=out)       # all pinned: the kernel reads host memory
         assert np.array_equal(out.numpy().view(np.uint16), got)
+        mixed = np.zeros(n, np.uint16)               # pageable result buffer: the copy pipeline
+        fib.lookup_host(pin_h, pin_l, out=mixed)
+        assert np.array_equal(mixed, got)
 
 
 def test_api_errors():
@@ -236,6 +239,23 @@ def test_tables_sharing_a_kernel_with_different_shared_memory():
         for f, fib in ((big, fb), (small, fs)):
             xh, xl = synth.gen_trace(f, 100_000, seed=403)
             assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl))
+
+
+@pytest.mark.parametrize("fmt", ["f8x128", "f8v7"])
+def test_mapped_lookup_formats_and_ties(fmt):
+    """The low half is read only on a tie of high halves: addresses inside /64 and longer prefixes
+    (and the 30 % uniform ones) exercise both the tie path and the plain path."""
+    f = synth.gen_fib(40_000, seed=911, nh_max=4095)
+    xh, xl = synth.gen_trace(f, 700_001, seed=912)
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as fib:
+        ph = torch.from_numpy(xh.view(np.int64)).pin_memory()
+        pl = torch.from_numpy(xl.view(np.int64)).pin_memory()
+        po = torch.full((xh.size,), -1, dtype=torch.int16).pin_memory()
+        s = torch.cuda.Stream()
+        fib.lookup_mapped(ph, pl, po, s)
+        s.synchronize()
+        assert np.array_equal(po.numpy().view(np.uint16), want)
 
 
 def test_mapped_lookup_on_pinned_host_buffers():
