@@ -457,7 +457,7 @@ def run_planb(args):
     # the kernel's name as ncu prints it
     if kname == "hybrid":
         kernel = (f"lookup_hybrid<{st['depth'] - st['smem_levels']}, "
-                  f"{1 if args.format == 'f8v7' else 0}, 0, 0>")
+                  f"{1 if args.format == 'f8v7' else 0}, 0, 0, 0>")
     elif kname == "flat":
         kernel = "lookup_flat"
     else:
