@@ -414,6 +414,8 @@ def run_planb(args):
                                 ("linearized tree, coop 16-lane, 64-bit key halves", "f16hi", "coop"),
                                 ("linearized tree, hybrid smem index + coop L2", "f8x128", "hybrid"),
                                 ("hybrid + next hops packed in the leaf line", "f8v7", "hybrid"),
+                                ("hybrid on 16-key leaves (index over the leaves, one L2 line)",
+                                 "f16hi", "hybrid"),
                                 ("learned position model (RMI, MLP root) + tree, 128-bit keys",
                                  "f8x128", "learned"),
                                 ("learned position model (RMI, MLP root) + tree, packed leaves",
@@ -455,7 +457,9 @@ def run_planb(args):
     peak, peak_kind = measured_peaks()
     kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
     # the kernel's name as ncu prints it
-    if kname == "hybrid":
+    if kname == "hybrid" and args.format == "f16hi":
+        kernel = f"lookup_hybrid16<{st['depth'] - st['smem_levels']}>"
+    elif kname == "hybrid":
         kernel = (f"lookup_hybrid<{st['depth'] - st['smem_levels']}, "
                   f"{1 if args.format == 'f8v7' else 0}, 0, 0, 0>")
     elif kname == "flat":

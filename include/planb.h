@@ -59,9 +59,12 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
 /* coop: every level by 8-lane (16-lane for F16HI) groups, one coalesced 128-byte node line per
  * level (Listing 1's node search as a warp ballot + popcount), top levels staged in shared memory */
 #define PLANB_KERNEL_COOP 1
-/* hybrid (F8X128 only): the top S levels are replaced by a per-thread lower bound over the level-S
- * subtree maxima held in shared memory (the same count, so the same node); the remaining levels
- * are descended cooperatively from L2 with several addresses per lane group in flight */
+/* hybrid (F8X128, F8V7, F16HI): the top S levels are replaced by a per-thread lower bound over the
+ * level-S subtree maxima held in shared memory (the same count, so the same node), started in the
+ * address's bucket of a radix directory; the remaining levels are descended cooperatively from L2
+ * with several addresses per lane group in flight. With F16HI (16 keys per leaf) the index over
+ * the leaves of a 200k-prefix table fits one CTA's shared memory, leaving the leaf line alone in
+ * L2; such tables run one 1024-thread CTA per SM and cannot join a multi-table group. */
 #define PLANB_KERNEL_HYBRID 2
 /* flat (F8X128 only): per-thread binary search over the sorted interval keys in global memory;
  * the GPU analogue of the paper's ablation baseline (Section 4.5, std::lower_bound) */
@@ -267,7 +270,8 @@ typedef struct planb_multi planb_multi; /* several tables (VRFs) served by one c
  * outlive the group; updates to them are picked up by later lookups. max_batch: most addresses per
  * planb_multi_lookup call (< 2^32); the group owns about max_batch x 20.2 bytes of device scratch
  * (plus about 3 bytes per address per 1,000 tables).
- * Tables built with PLANB_KERNEL_LEARNED cannot join a group. flags: 0, or an OR of the
+ * Tables built with PLANB_KERNEL_LEARNED, or F16HI tables of the hybrid kernel, cannot join a
+ * group. flags: 0, or an OR of the
  * PLANB_MULTI_* flags below. Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ECUDA.
  */
 #define PLANB_MULTI_NO_GRAPH 1u  /* flag: launch the pipeline directly instead of a captured graph */

@@ -40,6 +40,8 @@ def candidates(depth: int, auto_levels: int, persistent: bool = False) -> list[d
             for threads, ctas in ((512, 0), (256, 0), (512, 1)):
                 out.append(dict(format=fmt, kernel="hybrid", smem_levels=s, block_threads=threads,
                                 ctas_per_sm=ctas))
+    out.append(dict(format="f16hi", kernel="hybrid", smem_levels=-1, block_threads=0,
+                    ctas_per_sm=0))
     out.append(dict(format="f8x128", kernel="coop", smem_levels=-1, block_threads=256,
                     ctas_per_sm=0))
     out.append(dict(format="f16hi", kernel="coop", smem_levels=-1, block_threads=256,

@@ -129,6 +129,7 @@ int check_device(int dev) {
 
 constexpr size_t kSmemBudget = 96 * 1024;   // per CTA; two hybrid CTAs fit one SM
 constexpr size_t kDirBudget = 16 * 1024;     // the hybrid index's radix directory (2^13 + 1 u16)
+constexpr size_t kSmem16Budget = 224 * 1024; // F16HI hybrid: one CTA per SM
 
 uint32_t auto_smem_levels(const planb::Layout& L, uint32_t format) {
   // whole tree when it is small, else the deepest prefix of levels within 64 KiB
@@ -191,7 +192,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   const uint32_t format = static_cast<uint32_t>(o.format);
   const uint32_t k = format == PLANB_FMT_F16HI ? 16 : 8;
   uint32_t kernel = static_cast<uint32_t>(o.kernel);
-  if (format == PLANB_FMT_F16HI) kernel = planb::kCoop;
+  if (format == PLANB_FMT_F16HI && kernel != PLANB_KERNEL_HYBRID) kernel = planb::kCoop;
   else if (kernel == PLANB_KERNEL_AUTO) kernel = planb::kHybrid;
   const bool learned = kernel == planb::kLearned;
   if (on_dev && learned) {  // the model is fitted from the host copy of the intervals
@@ -225,10 +226,12 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                           : std::min<uint32_t>(o.smem_levels, t->L.D);
     while (s > 0 && planb::sidx_entries(t->L, s) * 8 + leaf_bytes > 200 * 1024) s--;
   } else if (kernel == planb::kHybrid) {
-    // the index shares the budget with its radix directory (at most 16 KB)
-    s = o.smem_levels < 0 ? auto_index_levels(t->L, kSmemBudget - kDirBudget)
+    // the index shares the budget with its radix directory (at most 16 KB); the F16HI form runs
+    // one CTA per SM and may take nearly all of its shared memory
+    const size_t budget = format == PLANB_FMT_F16HI ? kSmem16Budget : kSmemBudget;
+    s = o.smem_levels < 0 ? auto_index_levels(t->L, budget - kDirBudget)
                           : std::min<uint32_t>(o.smem_levels, t->L.D);
-    while (s > 0 && planb::sidx_entries(t->L, s) * 8 > 200 * 1024) s--;
+    while (s > 0 && planb::sidx_entries(t->L, s) * 8 > budget - kDirBudget) s--;
   } else if (kernel == planb::kFlat) {
     s = 0;
   } else {
@@ -485,7 +488,7 @@ int planb_build(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint
     return PLANB_EINVAL;
   if (o.block_threads < 0 || o.block_threads > 512 || o.block_threads % 32) return PLANB_EINVAL;
   if (o.kernel < PLANB_KERNEL_AUTO || o.kernel > PLANB_KERNEL_LEARNED) return PLANB_EINVAL;
-  if (o.format == PLANB_FMT_F16HI && o.kernel > PLANB_KERNEL_COOP) return PLANB_EINVAL;
+  if (o.format == PLANB_FMT_F16HI && o.kernel > PLANB_KERNEL_HYBRID) return PLANB_EINVAL;
   if (o.model_leaves < 0 || o.model_leaves > 8192 || o.model_iters < -1) return PLANB_EINVAL;
   if (o.builder != PLANB_BUILDER_HOST && o.builder != PLANB_BUILDER_DEVICE) return PLANB_EINVAL;
   try {
@@ -1078,7 +1081,8 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     return PLANB_EINVAL;
   for (uint32_t t = 0; t < n_tables; t++)
     if (!fibs[t] || fibs[t]->device != fibs[0]->device ||
-        fibs[t]->opts.kernel == PLANB_KERNEL_LEARNED)
+        fibs[t]->opts.kernel == PLANB_KERNEL_LEARNED ||
+        (fibs[t]->opts.format == PLANB_FMT_F16HI && fibs[t]->opts.kernel == PLANB_KERNEL_HYBRID))
       return PLANB_EINVAL;
   try {
     std::unique_ptr<planb_multi> m(new planb_multi());

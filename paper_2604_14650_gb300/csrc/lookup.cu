@@ -344,28 +344,23 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
             key[i] = __ldg(p.nodes + static_cast<uint64_t>(nd[i]) * 8u + j);
           // in a packed leaf, slot 7 holds next hops, not a key
           const bool keylane = !PACKED || (l + 1 < DB) || (j < 7u);
-          bool lt[kRounds], eq[kRounds];
+          // (few predicates live at once: the equalities are recomputed on the tie path)
           bool anyeq = false;
 #pragma unroll
-          for (int i = 0; i < kRounds; i++) {
-            lt[i] = keylane & (key[i].x < qh[i]);
-            eq[i] = keylane & (key[i].x == qh[i]);
-            anyeq |= eq[i];
-          }
-          if (__any_sync(kFull, anyeq)) {
+          for (int i = 0; i < kRounds; i++) anyeq |= keylane & (key[i].x == qh[i]);
+          const bool tie = __any_sync(kFull, anyeq);
 #pragma unroll
-            for (int i = 0; i < kRounds; i++) {
+          for (int i = 0; i < kRounds; i++) {
+            bool lt = keylane & (key[i].x < qh[i]);
+            if (tie) {
+              const bool eq = keylane & (key[i].x == qh[i]);
               // the owner of address i of each group reads its low half if its group saw a tie
-              const uint32_t need = __ballot_sync(kFull, eq[i]) & gmask;
+              const uint32_t need = __ballot_sync(kFull, eq) & gmask;
               if (need && j == r0 + i) my_lo.get(lo_src);
               const uint64_t ql = __shfl_sync(kFull, my_lo.v, gshift + r0 + i);
-              lt[i] = lt[i] | (eq[i] & (key[i].y < ql));
+              lt = lt | (eq & (key[i].y < ql));
             }
-          }
-#pragma unroll
-          for (int i = 0; i < kRounds; i++) {
-            const uint32_t m = __ballot_sync(kFull, lt[i]);
-            c[i] = __popc(m & gmask);
+            c[i] = __popc(__ballot_sync(kFull, lt) & gmask);
             if (l + 1 < DB) nd[i] = nd[i] * 9u + 1u + c[i];
           }
           if (PACKED && l + 1 == DB) {
@@ -402,6 +397,112 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
       if (!PACKED) result = __ldg(p.values + my_rank);
       if (ok) store_out<MULTI>(p, seg.off + mine, static_cast<uint16_t>(result));
     }
+  }
+}
+
+// ------------------------------------------------------------------------------- hybrid, F16HI
+// The hybrid descent on the F16HI layout (17-ary nodes of 16 high halves, low halves in a parallel
+// array). 16 keys per leaf make the leaf level small enough that the index over it fits one CTA's
+// shared memory at backbone size, so phase B is often the leaf line alone: one dependent L2 round
+// trip before the next hop instead of two. One 1024-thread CTA per SM holds the index; in phase B
+// lane j of an 8-lane group loads the high halves of keys 2j and 2j+1 (16 bytes, so the group's
+// loads are the node's one 128-byte line) and the count is the sum of two ballots.
+template <int DB>
+__global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const uint32_t N = p.sidx_n;
+  uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
+  uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((N + 1u) & ~1u));
+  const uint32_t dn = p.dir_bits ? (1u << p.dir_bits) + 1u : 0u;
+  for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(p.dir + i);
+  __syncthreads();
+
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t g = lane >> 3;
+  const uint32_t j = lane & 7u;
+  const uint32_t gshift = g * 8u;
+  const uint32_t gmask = 0xFFu << gshift;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  const ulonglong2* hi2 = reinterpret_cast<const ulonglong2*>(p.nodes_hi);
+
+  const Seg seg = segment<false>(p);
+  uint64_t nx_hi = 0, nx_lo = 0;
+  {
+    const uint64_t first = warp * 32 + lane;
+    if (first < seg.n) {
+      nx_hi = p.xhi[first];
+      nx_lo = p.xlo[first];
+    }
+  }
+  for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
+    const uint64_t mine = base + lane;
+    const bool ok = mine < seg.n;
+    const uint64_t my_hi = nx_hi;
+    LazyLo my_lo(ok);
+    my_lo.v = nx_lo;
+    my_lo.have = true;
+    {
+      const uint64_t next = mine + nwarps * 32;
+      nx_hi = next < seg.n ? p.xhi[next] : 0ull;
+      nx_lo = next < seg.n ? p.xlo[next] : 0ull;
+    }
+    const uint32_t cnt =
+        N ? index_count(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, p.sidx, my_hi, my_lo,
+                        p.xlo + mine)
+          : 0u;
+    uint64_t my_rank = cnt;
+    if constexpr (DB > 0) {
+      const uint32_t my_node = p.sidx_node + cnt;
+#pragma unroll
+      for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
+        uint64_t qh[kRounds];
+        uint32_t nd[kRounds];
+#pragma unroll
+        for (int i = 0; i < kRounds; i++) {
+          const uint32_t src = gshift + r0 + i;
+          qh[i] = __shfl_sync(kFull, my_hi, src);
+          nd[i] = __shfl_sync(kFull, my_node, src);
+        }
+#pragma unroll
+        for (int l = 0; l < DB; l++) {
+          ulonglong2 kh[kRounds];
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) kh[i] = __ldg(hi2 + static_cast<uint64_t>(nd[i]) * 8u + j);
+          // (few predicates live at once: the equalities are recomputed on the tie path)
+          bool anyeq = false;
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) anyeq |= (kh[i].x == qh[i]) | (kh[i].y == qh[i]);
+          const bool tie = __any_sync(kFull, anyeq);
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            bool lt0 = kh[i].x < qh[i], lt1 = kh[i].y < qh[i];
+            if (tie) {
+              const uint64_t ql = __shfl_sync(kFull, my_lo.v, gshift + r0 + i);
+              const uint64_t at = static_cast<uint64_t>(nd[i]) * 16u + 2u * j;
+              if (kh[i].x == qh[i]) lt0 = __ldg(p.nodes_lo + at) < ql;
+              if (kh[i].y == qh[i]) lt1 = __ldg(p.nodes_lo + at + 1u) < ql;
+            }
+            const uint32_t c = __popc(__ballot_sync(kFull, lt0) & gmask) +
+                               __popc(__ballot_sync(kFull, lt1) & gmask);
+            if (l + 1 < DB) {
+              nd[i] = nd[i] * 17u + 1u + c;
+            } else if (j == r0 + i) {
+              my_rank = static_cast<uint64_t>(nd[i] - p.internal_nodes) * 16u + c;
+            }
+          }
+        }
+      }
+    }
+#ifdef PLANB_BOUNDS_CHECK
+    if (my_rank >= p.n_intervals) {
+      report(p.status, 4u);
+      my_rank = 0;
+    }
+#endif
+    const uint16_t v = __ldg(p.values + my_rank);
+    if (ok) p.out[mine] = v;
   }
 }
 
@@ -464,8 +565,14 @@ KernelFn kernel_for(const DevTable& t, bool multi = false, bool lazy = false) {
   }
   static const KernelFn hyb_lazy[2][kMaxDepth + 1] = {PLANB_HYB_LAZY(false), PLANB_HYB_LAZY(true)};
 #undef PLANB_HYB_LAZY
+  static const KernelFn hyb16[kMaxDepth + 1] = {
+      lookup_hybrid16<0>, lookup_hybrid16<1>, lookup_hybrid16<2>, lookup_hybrid16<3>,
+      lookup_hybrid16<4>, lookup_hybrid16<5>, lookup_hybrid16<6>, lookup_hybrid16<7>,
+      lookup_hybrid16<8>, lookup_hybrid16<9>, lookup_hybrid16<10>};
   const uint32_t D = t.depth;
   if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
+  if (t.format == PLANB_FMT_F16HI && t.kernel == kHybrid)
+    return (!multi && t.smem_levels <= D) ? hyb16[D - t.smem_levels] : nullptr;
   if (t.format == PLANB_FMT_F16HI) return f16[D];
   const bool packed = t.format == PLANB_FMT_F8V7;
   if (t.kernel == kHybrid && multi)
@@ -522,11 +629,12 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
   if (!fn) return PLANB_EINVAL;
   const bool f8 = t.format != PLANB_FMT_F16HI;
   const bool hyb = (t.kernel == kHybrid || t.kernel == kLearned) && f8;
-  const int max_threads = hyb ? 512 : 256;
+  const bool hyb16 = t.kernel == kHybrid && !f8;   // one 1024-thread CTA per SM
+  const int max_threads = hyb16 ? 1024 : (hyb ? 512 : 256);
   if (threads <= 0) threads = max_threads;
   if (threads % 32 || threads > max_threads) return PLANB_EINVAL;
   cfg.threads = threads;
-  if (hyb)
+  if (hyb || hyb16)
     cfg.smem_bytes = static_cast<size_t>((t.sidx_n + 1) & ~1ull) * 8u +
                      (t.dir_bits ? ((((1u << t.dir_bits) + 1u) + 7u) & ~7u) * 2u : 0u) +
                      (t.kernel == kLearned ? static_cast<size_t>(t.lp.leaves) * 18u : 0u);

@@ -92,7 +92,7 @@ def test_device_intervals_equal_host_and_pass_oracle_checks(name, merge):
 
 
 VARIANTS = [("f8x128", "hybrid"), ("f8x128", "coop"), ("f8x128", "flat"), ("f8v7", "hybrid"),
-            ("f16hi", "coop")]
+            ("f16hi", "coop"), ("f16hi", "hybrid")]
 
 
 @pytest.mark.parametrize("fmt,kernel", VARIANTS)

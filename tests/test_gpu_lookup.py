@@ -57,7 +57,7 @@ def boundary_probes(f):
 FORMATS = ["f8x128", "f16hi"]
 # (node format, kernel) pairs: every lookup kernel of the library
 VARIANTS = [("f8v7", "hybrid"), ("f8v7", "learned"), ("f8x128", "hybrid"), ("f8x128", "learned"),
-            ("f8x128", "coop"), ("f8x128", "flat"), ("f16hi", "coop")]
+            ("f8x128", "coop"), ("f8x128", "flat"), ("f16hi", "coop"), ("f16hi", "hybrid")]
 VIDS = [f"{f}-{k}" for f, k in VARIANTS]
 
 

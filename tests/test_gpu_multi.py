@@ -117,9 +117,10 @@ def test_multi_table_sees_updates(per_table):
         f.close()
 
 
-def test_learned_tables_cannot_join():
+@pytest.mark.parametrize("fmt,kernel", [("f8x128", "learned"), ("f16hi", "hybrid")])
+def test_tables_without_a_multi_form_cannot_join(fmt, kernel):
     f = synth.gen_fib(2000, seed=3)
-    with pb.Fib(f.hi, f.lo, f.len, f.nh, kernel="learned") as fib:
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel) as fib:
         with pytest.raises(pb.PlanbError):
             pb.MultiFib([fib], max_batch=1000)
 
