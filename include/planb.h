@@ -55,7 +55,7 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
 #define PLANB_FMT_F8V7 2
 
 /* ----------------------------------------------------------------------------- lookup kernels */
-#define PLANB_KERNEL_AUTO 0   /* hybrid for F8X128, coop for F16HI                                */
+#define PLANB_KERNEL_AUTO 0   /* hybrid                                                            */
 /* coop: every level by 8-lane (16-lane for F16HI) groups, one coalesced 128-byte node line per
  * level (Listing 1's node search as a warp ballot + popcount), top levels staged in shared memory */
 #define PLANB_KERNEL_COOP 1

@@ -192,8 +192,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   const uint32_t format = static_cast<uint32_t>(o.format);
   const uint32_t k = format == PLANB_FMT_F16HI ? 16 : 8;
   uint32_t kernel = static_cast<uint32_t>(o.kernel);
-  if (format == PLANB_FMT_F16HI && kernel != PLANB_KERNEL_HYBRID) kernel = planb::kCoop;
-  else if (kernel == PLANB_KERNEL_AUTO) kernel = planb::kHybrid;
+  if (kernel == PLANB_KERNEL_AUTO) kernel = planb::kHybrid;
   const bool learned = kernel == planb::kLearned;
   if (on_dev && learned) {  // the model is fitted from the host copy of the intervals
     int rc = planb::gpu_download(giv, bs->s, iv);
@@ -1079,11 +1078,13 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
   if (!fibs || n_tables == 0 || n_tables > 255 || max_batch == 0 ||
       max_batch >= (size_t(1) << 32))
     return PLANB_EINVAL;
-  for (uint32_t t = 0; t < n_tables; t++)
-    if (!fibs[t] || fibs[t]->device != fibs[0]->device ||
-        fibs[t]->opts.kernel == PLANB_KERNEL_LEARNED ||
-        (fibs[t]->opts.format == PLANB_FMT_F16HI && fibs[t]->opts.kernel == PLANB_KERNEL_HYBRID))
-      return PLANB_EINVAL;
+  for (uint32_t t = 0; t < n_tables; t++) {
+    if (!fibs[t] || fibs[t]->device != fibs[0]->device) return PLANB_EINVAL;
+    std::lock_guard<std::mutex> lk(fibs[t]->cur_mu);
+    const planb::DevTable& d = fibs[t]->cur->dt;
+    if (d.kernel == planb::kLearned || (d.format == PLANB_FMT_F16HI && d.kernel == planb::kHybrid))
+      return PLANB_EINVAL;   // no multi-table form
+  }
   try {
     std::unique_ptr<planb_multi> m(new planb_multi());
     m->device = fibs[0]->device;

@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
 // trip before the next hop instead of two. One 1024-thread CTA per SM holds the index; in phase B
 // lane j of an 8-lane group loads the high halves of keys 2j and 2j+1 (16 bytes, so the group's
 // loads are the node's one 128-byte line) and the count is the sum of two ballots.
-template <int DB>
+template <int DB, bool LAZY = false>
 __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
@@ -428,12 +428,13 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   const ulonglong2* hi2 = reinterpret_cast<const ulonglong2*>(p.nodes_hi);
 
   const Seg seg = segment<false>(p);
+  // LAZY (addresses in host memory): low halves read only on a high-half tie, as lookup_hybrid
   uint64_t nx_hi = 0, nx_lo = 0;
   {
     const uint64_t first = warp * 32 + lane;
     if (first < seg.n) {
       nx_hi = p.xhi[first];
-      nx_lo = p.xlo[first];
+      if (!LAZY) nx_lo = p.xlo[first];
     }
   }
   for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
@@ -441,12 +442,14 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
     const bool ok = mine < seg.n;
     const uint64_t my_hi = nx_hi;
     LazyLo my_lo(ok);
-    my_lo.v = nx_lo;
-    my_lo.have = true;
+    if (!LAZY) {
+      my_lo.v = nx_lo;
+      my_lo.have = true;
+    }
     {
       const uint64_t next = mine + nwarps * 32;
       nx_hi = next < seg.n ? p.xhi[next] : 0ull;
-      nx_lo = next < seg.n ? p.xlo[next] : 0ull;
+      if (!LAZY) nx_lo = next < seg.n ? p.xlo[next] : 0ull;
     }
     const uint32_t cnt =
         N ? index_count(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, p.sidx, my_hi, my_lo,
@@ -479,6 +482,11 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
           for (int i = 0; i < kRounds; i++) {
             bool lt0 = kh[i].x < qh[i], lt1 = kh[i].y < qh[i];
             if (tie) {
+              if (LAZY) {   // the owner of address i of each group reads its low half on a tie
+                const bool eq = (kh[i].x == qh[i]) | (kh[i].y == qh[i]);
+                const uint32_t need = __ballot_sync(kFull, eq) & gmask;
+                if (need && j == r0 + i) my_lo.get(p.xlo + mine);
+              }
               const uint64_t ql = __shfl_sync(kFull, my_lo.v, gshift + r0 + i);
               const uint64_t at = static_cast<uint64_t>(nd[i]) * 16u + 2u * j;
               if (kh[i].x == qh[i]) lt0 = __ldg(p.nodes_lo + at) < ql;
@@ -565,14 +573,18 @@ KernelFn kernel_for(const DevTable& t, bool multi = false, bool lazy = false) {
   }
   static const KernelFn hyb_lazy[2][kMaxDepth + 1] = {PLANB_HYB_LAZY(false), PLANB_HYB_LAZY(true)};
 #undef PLANB_HYB_LAZY
-  static const KernelFn hyb16[kMaxDepth + 1] = {
-      lookup_hybrid16<0>, lookup_hybrid16<1>, lookup_hybrid16<2>, lookup_hybrid16<3>,
-      lookup_hybrid16<4>, lookup_hybrid16<5>, lookup_hybrid16<6>, lookup_hybrid16<7>,
-      lookup_hybrid16<8>, lookup_hybrid16<9>, lookup_hybrid16<10>};
+  static const KernelFn hyb16[2][kMaxDepth + 1] = {
+      {lookup_hybrid16<0>, lookup_hybrid16<1>, lookup_hybrid16<2>, lookup_hybrid16<3>,
+       lookup_hybrid16<4>, lookup_hybrid16<5>, lookup_hybrid16<6>, lookup_hybrid16<7>,
+       lookup_hybrid16<8>, lookup_hybrid16<9>, lookup_hybrid16<10>},
+      {lookup_hybrid16<0, true>, lookup_hybrid16<1, true>, lookup_hybrid16<2, true>,
+       lookup_hybrid16<3, true>, lookup_hybrid16<4, true>, lookup_hybrid16<5, true>,
+       lookup_hybrid16<6, true>, lookup_hybrid16<7, true>, lookup_hybrid16<8, true>,
+       lookup_hybrid16<9, true>, lookup_hybrid16<10, true>}};
   const uint32_t D = t.depth;
   if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
   if (t.format == PLANB_FMT_F16HI && t.kernel == kHybrid)
-    return (!multi && t.smem_levels <= D) ? hyb16[D - t.smem_levels] : nullptr;
+    return (!multi && t.smem_levels <= D) ? hyb16[lazy ? 1 : 0][D - t.smem_levels] : nullptr;
   if (t.format == PLANB_FMT_F16HI) return f16[D];
   const bool packed = t.format == PLANB_FMT_F8V7;
   if (t.kernel == kHybrid && multi)
