@@ -58,6 +58,36 @@ struct LazyLo {
   }
 };
 
+// The same count searched in place in global memory (the index's high halves at stride 16 bytes,
+// the directory as stored), for launches too small to repay staging the index per CTA.
+__device__ __forceinline__ uint32_t index_count_global(const ulonglong2* sidx, uint32_t N,
+                                                       const uint16_t* dir, uint32_t dir_bits,
+                                                       uint32_t dir_shift, uint64_t dir_base,
+                                                       uint64_t my_hi, LazyLo& my_lo,
+                                                       const uint64_t* lo_src) {
+  uint32_t lo = 0, n = N;
+  if (dir_bits) {
+    const uint64_t v = my_hi >> dir_shift;
+    uint64_t bk = v > dir_base ? v - dir_base : 0ull;
+    const uint64_t last = (1ull << dir_bits) - 1ull;
+    bk = bk < last ? bk : last;
+    lo = __ldg(dir + bk);
+    n = __ldg(dir + bk + 1) - lo;
+  }
+  uint32_t cnt = lo;
+  if (n) {
+    uint32_t b = lo;
+    while (n > 1) {
+      const uint32_t half = n >> 1;
+      b = __ldg(&sidx[b + half].x) < my_hi ? b + half : b;
+      n -= half;
+    }
+    cnt = b + (__ldg(&sidx[b].x) < my_hi ? 1u : 0u);
+  }
+  while (cnt < N && __ldg(&sidx[cnt].x) == my_hi && __ldg(&sidx[cnt].y) < my_lo.get(lo_src)) cnt++;
+  return cnt;
+}
+
 __device__ __forceinline__ uint32_t index_count(const uint64_t* Uh, uint32_t N,
                                                 const uint16_t* Dir, uint32_t dir_bits,
                                                 uint32_t dir_shift, uint64_t dir_base,

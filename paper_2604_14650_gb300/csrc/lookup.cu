@@ -226,10 +226,16 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
   uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
-  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
+  // a launch with under two tiles per warp searches the index in place instead of staging it
+  // (single-table, not learned: the learned path always stages its leaf models)
+  const bool staged =
+      LEARNED || MULTI || ((p.n + 31) / 32) >= 2ull * gridDim.x * (blockDim.x / 32);
+  if (staged)
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
   uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((N + 1u) & ~1u));
   const uint32_t dn = p.dir_bits ? (1u << p.dir_bits) + 1u : 0u;
-  for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(p.dir + i);
+  if (staged)
+    for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(p.dir + i);
   LeafModel* Lm = reinterpret_cast<LeafModel*>(Dir + ((dn + 7u) & ~7u));
   uint16_t* Le = reinterpret_cast<uint16_t*>(Lm + (LEARNED ? p.lp.leaves : 0u));
   if (LEARNED) {
@@ -308,9 +314,12 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
         have = ok;
       }
     }
-    if (N && !have)
+    if (N && !have && staged)
       cnt = index_count(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, p.sidx, my_hi, my_lo,
                         lo_src);
+    else if (N && !have)
+      cnt = index_count_global(p.sidx, N, p.dir, p.dir_bits, p.dir_shift, p.dir_base, my_hi,
+                               my_lo, lo_src);
     if constexpr (DB == 0) {
       uint32_t rank = cnt;
 #ifdef PLANB_BOUNDS_CHECK
@@ -412,11 +421,15 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
   uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
-  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
   uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((N + 1u) & ~1u));
-  const uint32_t dn = p.dir_bits ? (1u << p.dir_bits) + 1u : 0u;
-  for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(p.dir + i);
-  __syncthreads();
+  // a launch with under two tiles per warp searches the index in place instead of staging it
+  const bool staged = ((p.n + 31) / 32) >= 2ull * gridDim.x * (blockDim.x / 32);
+  if (staged) {
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
+    const uint32_t dn = p.dir_bits ? (1u << p.dir_bits) + 1u : 0u;
+    for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(p.dir + i);
+    __syncthreads();
+  }
 
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t g = lane >> 3;
@@ -451,10 +464,13 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
       nx_hi = next < seg.n ? p.xhi[next] : 0ull;
       if (!LAZY) nx_lo = next < seg.n ? p.xlo[next] : 0ull;
     }
-    const uint32_t cnt =
-        N ? index_count(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, p.sidx, my_hi, my_lo,
-                        p.xlo + mine)
-          : 0u;
+    uint32_t cnt = 0;
+    if (N && staged)
+      cnt = index_count(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, p.sidx, my_hi, my_lo,
+                        p.xlo + mine);
+    else if (N)
+      cnt = index_count_global(p.sidx, N, p.dir, p.dir_bits, p.dir_shift, p.dir_base, my_hi,
+                               my_lo, p.xlo + mine);
     uint64_t my_rank = cnt;
     if constexpr (DB > 0) {
       const uint32_t my_node = p.sidx_node + cnt;

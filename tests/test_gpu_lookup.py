@@ -287,3 +287,18 @@ def test_mapped_lookup_on_pinned_host_buffers():
                                           ctypes.c_void_p(out.ctypes.data), None)
         assert rc == -1   # PLANB_EINVAL
         assert np.all(out == 0)
+
+
+@pytest.mark.parametrize("fmt", ["f8x128", "f16hi"])
+def test_small_and_large_launches_agree(fmt):
+    """Launches with under two 32-address tiles per warp search the index in global memory, larger
+    ones stage it in shared memory; both give the oracle's answers, at sizes on both sides."""
+    f = synth.gen_fib(200_000, seed=921, nh_max=4095)
+    xh, xl = synth.gen_trace(f, 3_000_000, seed=922)
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl)
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel="hybrid") as fib:
+        dh, dl = dev(xh), dev(xl)
+        for k in (1, 31, 4096, 65_536, 300_000, 3_000_000):
+            out = fib.lookup(dh[:k], dl[:k])
+            torch.cuda.synchronize()
+            assert np.array_equal(out.cpu().numpy().view(np.uint16), want[:k]), k
