@@ -65,6 +65,8 @@ struct KParams {
   const LeafModel* leaves;    // learned: leaf models (copied to shared memory)
   const uint16_t* leaf_err;   // learned: per-leaf window half-width or kLeafFallback
   LearnedParams lp;           // learned: root weights and range reduction
+  uint32_t staged;            // hybrid: 1 = index and directory staged in shared memory, 0 =
+                              // searched in place (small launches; no shared memory given)
   const uint16_t* dir;        // hybrid: radix directory over the index (dir_bits = 0: none)
   uint32_t dir_bits, dir_shift;
   uint64_t dir_base;
@@ -226,10 +228,9 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
   uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
-  // a launch with under two tiles per warp searches the index in place instead of staging it
-  // (single-table, not learned: the learned path always stages its leaf models)
-  const bool staged =
-      LEARNED || MULTI || ((p.n + 31) / 32) >= 2ull * gridDim.x * (blockDim.x / 32);
+  // a small launch searches the index in place instead of staging it (decided by the host;
+  // the learned and multi-table forms always stage)
+  const bool staged = LEARNED || MULTI || p.staged != 0;
   if (staged)
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
   uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((N + 1u) & ~1u));
@@ -422,8 +423,8 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   const uint32_t N = p.sidx_n;
   uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
   uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((N + 1u) & ~1u));
-  // a launch with under two tiles per warp searches the index in place instead of staging it
-  const bool staged = ((p.n + 31) / 32) >= 2ull * gridDim.x * (blockDim.x / 32);
+  // a small launch searches the index in place instead of staging it (decided by the host)
+  const bool staged = p.staged != 0;
   if (staged) {
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
     const uint32_t dn = p.dir_bits ? (1u << p.dir_bits) + 1u : 0u;
@@ -733,16 +734,29 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   p.range = d_range;
   p.perm = d_perm;
   uint64_t blocks;
+  int threads = cfg.threads;
+  size_t smem = cfg.smem_bytes;
+  p.staged = 1;
   if (t.kernel == kFlat) {
     blocks = (n + cfg.threads - 1) / cfg.threads;
   } else {
     const uint64_t tiles = (n + 31) / 32;
     const uint64_t warps_per_block = cfg.threads / 32;
     blocks = (tiles + warps_per_block - 1) / warps_per_block;
+    // Under two tiles per warp of the full grid, staging the index would cost more than it saves:
+    // search it in place, with small CTAs and no shared memory, so the launch spreads over every SM.
+    const bool small = t.kernel == kHybrid && !multi && cfg.blocks > 0 &&
+                       tiles < 2ull * static_cast<uint64_t>(cfg.blocks) * warps_per_block;
+    if (small) {
+      p.staged = 0;
+      threads = 256;
+      smem = 0;
+      blocks = (tiles + 7) / 8;
+    }
   }
-  if (cfg.blocks > 0 && blocks > static_cast<uint64_t>(cfg.blocks)) blocks = cfg.blocks;
-  fn<<<static_cast<unsigned>(blocks), cfg.threads, cfg.smem_bytes,
-       static_cast<cudaStream_t>(stream)>>>(p);
+  if (p.staged && cfg.blocks > 0 && blocks > static_cast<uint64_t>(cfg.blocks)) blocks = cfg.blocks;
+  if (blocks > 65535u * 32u) blocks = 65535u * 32u;
+  fn<<<static_cast<unsigned>(blocks), threads, smem, static_cast<cudaStream_t>(stream)>>>(p);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 
