@@ -5,7 +5,9 @@ Workload (default): a 200,000-prefix synthetic backbone FIB (BGP-like length mix
 1 % /128, next hops in [1, 4095], ::/0 -> 0) and 2^28 lookup addresses per GPU (70 % uniform inside
 a random prefix, 30 % uniform over the 128-bit space). One step = one planb_lookup over all 2^28
 device-resident addresses: key ingest, tree descent, next-hop gather and result store (hot-path
-steps a5-a10). The 4 GiB key stream is larger than L2, so no flush is needed between steps.
+steps a5-a10). The 4 GiB key stream is larger than L2, so no flush is needed between steps. The
+table is built as F16HI with the hybrid kernel (the fastest form at this size; ``--format``
+chooses another); the ablation block times every other form on the same table and addresses.
 
 Prints ONE JSON line on rank 0. ``--impl reference`` times the CPU oracle (binary trie) instead.
 Multi-GPU (torchrun, one rank per GPU): each rank looks up its own 2^28 addresses against a replica
@@ -459,7 +461,7 @@ def run_planb(args):
     kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
     # the kernel's name as ncu prints it
     if kname == "hybrid" and args.format == "f16hi":
-        kernel = f"lookup_hybrid16<{st['depth'] - st['smem_levels']}>"
+        kernel = f"lookup_hybrid16<{st['depth'] - st['smem_levels']}, 0>"
     elif kname == "hybrid":
         kernel = (f"lookup_hybrid<{st['depth'] - st['smem_levels']}, "
                   f"{1 if args.format == 'f8v7' else 0}, 0, 0, 0>")
