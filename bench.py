@@ -384,7 +384,22 @@ def run_planb(args):
                          "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 2 * n,
                          "api": "planb_lookup_mapped (pinned host buffers read and written by "
                                 "the lookup kernel over the host link)"}
-        del ph, pl, po
+        # the host link's own rate for a plain pinned-to-device copy of the high halves: the
+        # ceiling of a lookup path that must move at least 8 + 2 bytes per address across it
+        dbuf = torch.empty(n, dtype=torch.int64, device=f"cuda:{local}")
+        dbuf.copy_(ph, non_blocking=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(2):
+            dbuf.copy_(ph, non_blocking=True)
+        b.record()
+        b.synchronize()
+        link = 2 * 8 * n / (a.elapsed_time(b) / 1e3) / 1e9
+        e2e["host_link"] = {"h2d_copy_gbs": link, "bytes_per_lookup_crossing": 10,
+                            "ceiling_B_lookups_per_s": link / 10,
+                            "frac": e2e["value"] * 10 / link}
+        del ph, pl, po, dbuf
 
     # p50/p99 latency of 2^16-address batches, each launch event-timed
     lat = None
