@@ -1097,7 +1097,10 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess)
       return PLANB_ECUDA;
-    m->G = static_cast<uint32_t>(sms) * 8u;
+    // bucketing chunks: eight per SM for large batches, but no more than one 2,048-address tile
+    // each at max_batch, so a group sized for small batches (a serving slot) launches few blocks
+    const size_t by_batch = (max_batch + 2047) / 2048;
+    m->G = static_cast<uint32_t>(std::max<size_t>(1, std::min<size_t>(by_batch, size_t(sms) * 8u)));
     const size_t cap = max_batch;
     auto up = [](size_t x) { return ((x + 255) / 256) * 256; };
     const size_t tiles = planb::bucketing_tiles(cap, m->G) * (m->T + 1);
