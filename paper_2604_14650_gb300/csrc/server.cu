@@ -72,7 +72,8 @@ struct planb_server {
   planb_server_opts o{};
   int device = 0;
   std::mutex mu;                       // tables, queue, tickets, stats
-  std::condition_variable cv_queue, cv_done;
+  std::condition_variable cv_queue, cv_done;   // dispatcher wake-ups; request completions
+  std::condition_variable cv_upd;              // the updater's period timer (and shutdown)
   std::vector<planb_fib*> tables;
   uint64_t tables_version = 0;
   uint64_t table_bytes = 0;
@@ -167,6 +168,12 @@ void complete_slot(planb_server* m, Slot& s, int status) {
   m->cv_done.notify_all();
 }
 
+// Runs on the CUDA runtime's callback thread when a slot's batch (copies, lookups, copies back)
+// has finished: wakes the dispatcher at once instead of at its next poll. No CUDA calls here.
+void CUDART_CB batch_done(void* user) {
+  static_cast<planb_server*>(user)->cv_queue.notify_all();
+}
+
 void dispatcher_main(planb_server* m) {
   cudaSetDevice(m->device);
   size_t next_slot = 0;
@@ -182,8 +189,9 @@ void dispatcher_main(planb_server* m) {
     if (m->queue.empty()) {
       bool busy = false;
       for (Slot& s : m->slots) busy |= s.busy;
-      // idle: sleep until work arrives; busy: poll the slots again shortly
-      m->cv_queue.wait_for(lk, busy ? std::chrono::microseconds(20) : std::chrono::milliseconds(5));
+      // idle: sleep until work arrives; busy: until a batch finishes (its callback notifies),
+      // with a short timeout as a fallback
+      m->cv_queue.wait_for(lk, busy ? std::chrono::microseconds(200) : std::chrono::milliseconds(5));
       continue;
     }
     Slot* slot = nullptr;
@@ -253,7 +261,8 @@ void dispatcher_main(planb_server* m) {
     if (rc == PLANB_OK &&
         (cudaMemcpyAsync(slot->h_out, slot->d_out, total * 2, cudaMemcpyDeviceToHost, st) !=
              cudaSuccess ||
-         cudaEventRecord(slot->ev, st) != cudaSuccess))
+         cudaEventRecord(slot->ev, st) != cudaSuccess ||
+         cudaLaunchHostFunc(st, batch_done, m) != cudaSuccess))
       rc = PLANB_ECUDA;
     const char* why = rc == PLANB_OK ? "" : (ok ? planb_last_error() : "staging copy");
     char why_copy[256];
@@ -276,7 +285,7 @@ void updater_main(planb_server* m) {
     std::vector<planb_fib*> tabs;
     {
       std::unique_lock<std::mutex> lk(m->mu);
-      m->cv_queue.wait_for(lk, std::chrono::microseconds(m->o.update_period_us));
+      m->cv_upd.wait_for(lk, std::chrono::microseconds(m->o.update_period_us));
       if (m->stop.load()) break;
       if (!m->pending_count) continue;
       for (uint32_t t = 0; t < m->pending.size(); t++) {
@@ -507,6 +516,7 @@ void planb_server_destroy(planb_server* m) {
   if (!m) return;
   m->stop.store(true);
   m->cv_queue.notify_all();
+  m->cv_upd.notify_all();
   if (m->dispatcher.joinable()) m->dispatcher.join();
   if (m->updater.joinable()) m->updater.join();
   cudaSetDevice(m->device);
