@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
               const uint64_t ql = __shfl_sync(kFull, my_lo.v, gshift + r0 + i);
               lt = lt | (eq & (key[i].y < ql));
             }
-            c[i] = __reduce_add_sync(gmask, lt ? 1u : 0u);   // keys below, within the group
+            c[i] = __popc(__ballot_sync(kFull, lt) & gmask);
             if (l + 1 < DB) nd[i] = nd[i] * 9u + 1u + c[i];
           }
           if (PACKED && l + 1 == DB) {
@@ -509,7 +509,8 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
               if (kh[i].x == qh[i]) lt0 = __ldg(p.nodes_lo + at) < ql;
               if (kh[i].y == qh[i]) lt1 = __ldg(p.nodes_lo + at + 1u) < ql;
             }
-            const uint32_t c = __reduce_add_sync(gmask, (lt0 ? 1u : 0u) + (lt1 ? 1u : 0u));
+            const uint32_t c = __popc(__ballot_sync(kFull, lt0) & gmask) +
+                               __popc(__ballot_sync(kFull, lt1) & gmask);
             if (l + 1 < DB) {
               nd[i] = nd[i] * 17u + 1u + c;
             } else if (j == r0 + i) {

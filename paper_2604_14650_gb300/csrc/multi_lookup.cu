@@ -98,7 +98,7 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
           }
 #pragma unroll
           for (int i = 0; i < kRounds; i++) {
-            c[i] = __reduce_add_sync(gmask, lt[i] ? 1u : 0u);   // keys below, within the group
+            c[i] = __popc(__ballot_sync(kFull, lt[i]) & gmask);
             if (!last) nd[i] = nd[i] * 9u + 1u + c[i];
           }
         }
