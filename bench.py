@@ -171,6 +171,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_peaks_mhz() -> float:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError):
+        return 2070.0
+
+
 def recorded_counters(kernel: str):
     """Per-lookup counters of a kernel from the ncu capture summarised in profiles/traffic.json,
     if the kernel's source has not changed since the capture (else None)."""
@@ -502,6 +511,9 @@ def run_planb(args):
                         "bytes_per_lookup": rec["l2_bytes_per_lookup"]},
                  "l1_lsu_pipe": {"frac_at_capture": rec["l1_lsu_wavefronts_pct_of_peak"] / 100,
                                  "smem_wavefronts_per_lookup": rec["smem_wavefronts_per_lookup"]},
+                 # instruction issue: warp-instructions per lookup (capture) at this run's rate
+                 # against 4 schedulers x SMs x the SM clock sampled under load
+                 "issue": None,
                  "source": "profiles/traffic.json (ncu --set full capture of this kernel)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -531,6 +543,15 @@ def run_planb(args):
         "clocks": clk,
         "gpu_launches": args.steps,
     }
+    if roofs is not None and rec.get("warp_inst_per_lookup"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or measured_peaks_mhz()
+        peak_ginst = 4 * sms * mhz / 1e3
+        ach = rec["warp_inst_per_lookup"] * (n / avg_launch_s) / 1e9
+        roofs["issue"] = {"achieved": ach, "peak": peak_ginst, "unit": "G warp-instructions/s",
+                          "frac": ach / peak_ginst,
+                          "warp_inst_per_lookup": rec["warp_inst_per_lookup"],
+                          "issue_active_at_capture": rec.get("issue_active_pct", 0) / 100}
     if rank == 0:
         print(json.dumps(line), flush=True)
     fib.close()
