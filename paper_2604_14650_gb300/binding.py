@@ -433,6 +433,11 @@ class MultiFib:
         return out
 
     @property
+    def captures(self) -> int:
+        """Graph captures so far (the first lookup, then changes of buffers or launch shape)."""
+        return int(self._lib.planb_multi_captures(self._h))
+
+    @property
     def persistent(self) -> bool:
         """True when the lookups run as the single persistent launch over all tables."""
         rc = self._lib.planb_multi_persistent(self._h)

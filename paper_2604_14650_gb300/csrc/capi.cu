@@ -1003,6 +1003,8 @@ struct planb_multi {
   uint16_t* tile_base = nullptr;  // ... and its first slot in the tile
   uint16_t* bres = nullptr;      // results in bucketed order
   planb::MultiDesc* desc = nullptr;  // per-table descriptors of the single persistent launch
+  planb::MultiDesc* hdesc = nullptr; // page-locked staging of the descriptors (stream-ordered copy)
+  cudaEvent_t desc_copied = nullptr; // the last copy out of hdesc has been made
   bool persist = false;          // the current tables all fit the single persistent launch
   int persist_ctas = 0;
   size_t persist_smem = 0;
@@ -1127,7 +1129,10 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     m->range = reinterpret_cast<uint64_t*>(b + range_off);
     m->desc = reinterpret_cast<planb::MultiDesc*>(b + desc_off);
     bool ok = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&m->desc_copied, cudaEventDisableTiming) == cudaSuccess &&
+              cudaHostAlloc(reinterpret_cast<void**>(&m->hdesc),
+                            m->T * sizeof(planb::MultiDesc), cudaHostAllocDefault) == cudaSuccess;
     for (int k = 0; ok && k < planb_multi::kBranches; k++)
       ok = cudaStreamCreateWithFlags(&m->side[k], cudaStreamNonBlocking) == cudaSuccess &&
            cudaEventCreateWithFlags(&m->join[k], cudaEventDisableTiming) == cudaSuccess;
@@ -1166,11 +1171,16 @@ int planb_multi_lookup_devn(planb_multi* m, const uint64_t* d_addr_hi, const uin
 namespace {
 // Decides whether the current tables can share the single persistent launch (every one a hybrid
 // F8X128 or F8V7 table whose index fits the shared memory) and writes their descriptors.
+// The descriptors are copied in stream order on st (from page-locked staging), so graphs already
+// queued on st read the old ones and later ones the new, without a host-side wait.
 int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cur,
                         cudaStream_t st) {
   m->persist = false;
   if (m->flags & PLANB_MULTI_PER_TABLE) return PLANB_OK;
-  std::vector<planb::MultiDesc> hd(m->T);
+  // the staging buffer is reused: its previous copy must have been made
+  const cudaError_t ew = cudaEventSynchronize(m->desc_copied);
+  if (ew != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: descriptor staging", ew);
+  planb::MultiDesc* hd = m->hdesc;
   uint64_t max_n = 0;
   for (uint32_t t = 0; t < m->T; t++) {
     const planb::DevTable& d = cur[t]->dt;
@@ -1196,17 +1206,24 @@ int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>
                           (d.dir_bits ? ((((1ull << d.dir_bits) + 1) + 7) & ~7ull) * 2u : 0u);
     max_n = std::max<uint64_t>(max_n, need);
   }
-  const size_t smem = ((m->T + 3u) & ~1u) * 8u + max_n;
-  int ctas = 0;
-  if (planb::multi_persistent_setup(m->device, smem, &ctas) != PLANB_OK) {
+  // rounded up to 16 KB, so that a table growing a little keeps the captured launch's size,
+  // unless the rounding would cost resident CTAs
+  const size_t exact = ((m->T + 3u) & ~1u) * 8u + max_n;
+  size_t smem = exact;
+  int ctas = 0, ctas_round = 0;
+  if (planb::multi_persistent_setup(m->device, exact, &ctas) != PLANB_OK) {
     cudaGetLastError();
     return PLANB_OK;   // too large for one CTA: per-table launches
   }
-  const cudaError_t e = cudaMemcpyAsync(m->desc, hd.data(), hd.size() * sizeof(planb::MultiDesc),
-                                        cudaMemcpyHostToDevice, st);
+  const size_t rounded = ((exact + 16383) / 16384) * 16384;
+  if (planb::multi_persistent_setup(m->device, rounded, &ctas_round) == PLANB_OK &&
+      ctas_round == ctas)
+    smem = rounded;
+  cudaGetLastError();
+  cudaError_t e = cudaMemcpyAsync(m->desc, hd, m->T * sizeof(planb::MultiDesc),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(m->desc_copied, st);
   if (e != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: descriptors", e);
-  const cudaError_t es = cudaStreamSynchronize(st);
-  if (es != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: descriptors", es);
   m->persist = true;
   m->persist_ctas = ctas;
   m->persist_smem = smem;
@@ -1235,20 +1252,25 @@ int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t*
   }
   bool changed = m->snap.size() != m->T;
   for (uint32_t t = 0; !changed && t < m->T; t++) changed = m->snap[t] != cur[t];
+  // New tables: the persistent launch reads them through its descriptors, rewritten in stream
+  // order, so its captured graph stays valid unless the launch's shape changed; per-table launches
+  // carry the table pointers in their parameters and are captured again.
+  bool reshape = false;
   if (changed) {
-    // new tables: the per-table descriptors of the persistent launch are rewritten once the
-    // work already queued on st (which reads them) is done
-    const cudaError_t es = cudaStreamSynchronize(st);
-    if (es != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: wait for previous work", es);
+    const bool was = m->persist;
+    const int ctas = m->persist_ctas;
+    const size_t smem = m->persist_smem;
     int rc = refresh_descriptors(m, cur, st);
     if (rc) return rc;
+    reshape = !m->persist || !was || ctas != m->persist_ctas || smem != m->persist_smem;
   }
   if (m->flags & PLANB_MULTI_NO_GRAPH) {
     if (changed) m->snap = cur;
     return multi_pipeline(m, cur, d_addr_hi, d_addr_lo, d_table, n, d_out, st, d_n, false);
   }
-  const bool same = !changed && m->exec && m->g_hi == d_addr_hi && m->g_lo == d_addr_lo &&
+  const bool same = !reshape && m->exec && m->g_hi == d_addr_hi && m->g_lo == d_addr_lo &&
                     m->g_tid == d_table && m->g_out == d_out && m->g_n == n && m->g_dn == d_n;
+  if (same && changed) m->snap = cur;   // the replayed graph reads the new descriptors
   if (!same) {
     // a table was swapped by an update, or the buffers changed: capture the pipeline again
     if (m->exec) {
@@ -1316,6 +1338,8 @@ void planb_multi_destroy(planb_multi* m) {
       if (m->join[k]) cudaEventDestroy(m->join[k]);
     }
     if (m->fork) cudaEventDestroy(m->fork);
+    if (m->desc_copied) cudaEventDestroy(m->desc_copied);
+    if (m->hdesc) cudaFreeHost(m->hdesc);
     if (m->mem) cudaFree(m->mem);
   }
   delete m;

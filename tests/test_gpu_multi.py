@@ -104,6 +104,7 @@ def test_multi_table_sees_updates(per_table):
         torch.cuda.synchronize()
         assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
         # withdraw every prefix of table 1 except the default: its addresses then all get 0
+        before = mt.captures
         f1 = fibs_in[1]
         keep = f1.len == 0
         fibs[1].update(wd_hi=f1.hi[~keep], wd_lo=f1.lo[~keep], wd_len=f1.len[~keep])
@@ -113,6 +114,35 @@ def test_multi_table_sees_updates(per_table):
         got = out.cpu().numpy().view(np.uint16)
         assert np.array_equal(got, expected(fibs_in, tid, xh, xl))
         assert np.all(got[tid == 1] == 0)
+        # a swapped table reaches the single persistent launch through its descriptors (no new
+        # capture while the launch keeps its shape); per-table launches are captured again
+        if not per_table:
+            assert mt.captures == before
+        else:
+            assert mt.captures == before + 1
+        # and again: a second update of another table, replayed
+        f0 = fibs_in[0]
+        upd = synth.gen_updates(f0, 500, seed=52)
+        fibs[0].update(*upd)
+        ref = {}
+        for h, l, L, n_ in zip(f0.hi, f0.lo, f0.len, f0.nh):
+            mh, ml = synth.top_mask(np.array([L]))
+            ref[(int(h & mh[0]), int(l & ml[0]), int(L))] = int(n_)
+        ih, il, iL, inh, wh, wl, wL = upd
+        for h, l, L in zip(wh, wl, wL):
+            mh, ml = synth.top_mask(np.array([L]))
+            ref.pop((int(h & mh[0]), int(l & ml[0]), int(L)), None)
+        for h, l, L, n_ in zip(ih, il, iL, inh):
+            mh, ml = synth.top_mask(np.array([L]))
+            ref[(int(h & mh[0]), int(l & ml[0]), int(L))] = int(n_)
+        ks = list(ref)
+        fibs_in[0] = synth.Fib(np.array([k[0] for k in ks], np.uint64),
+                               np.array([k[1] for k in ks], np.uint64),
+                               np.array([k[2] for k in ks], np.uint8),
+                               np.array([ref[k] for k in ks], np.uint16), 0)
+        out = mt.lookup(dh, dl, dt, out=out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
     for f in fibs:
         f.close()
 
