@@ -88,6 +88,19 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
 #define PLANB_BUILDER_HOST 0
 #define PLANB_BUILDER_DEVICE 1
 
+/* How the F16HI hybrid kernel settles keys whose high half equals the address's at the leaf
+ * (planb_opts.leaf_ties; results are the same either way).
+ * vote: every node search, leaf included, also votes on equal high halves (a 32-bit pre-test of
+ *   the group's keys) and compares low halves when a tie is possible.
+ * walk: the leaf is counted by high halves only; each lane then reads the key that follows its
+ *   count, alongside its next hop, and on an equal high half walks the equal keys by their low
+ *   halves (they follow the counted ones in key order). Fewer instructions, one more scattered
+ *   8-byte read per address, which costs little while the SM has room left for its L1 cache.
+ * auto: walk when the shared-memory index takes at most 128 KB, else vote. */
+#define PLANB_LEAF_TIES_AUTO 0
+#define PLANB_LEAF_TIES_VOTE 1
+#define PLANB_LEAF_TIES_WALK 2
+
 typedef struct planb_fib planb_fib; /* opaque; owns all host and device memory of one table */
 
 typedef struct {
@@ -105,7 +118,8 @@ typedef struct {
     int32_t model_leaves;   /* learned: leaf models L; 0 = automatic                              */
     int32_t model_iters;    /* learned: Adam steps of the root's training; -1 = default (2000)    */
     int32_t builder;        /* PLANB_BUILDER_*: where the build steps run; default host          */
-    int32_t reserved[4];    /* zero                                                              */
+    int32_t leaf_ties;      /* PLANB_LEAF_TIES_*: F16HI hybrid leaf tie handling; default auto   */
+    int32_t reserved[3];    /* zero                                                              */
 } planb_opts;
 
 /* Fills *o with the defaults. */
@@ -144,6 +158,8 @@ typedef struct {
     double model_covered;      /* learned: share of keys in leaves within the window limit       */
     double model_mean_err;     /* learned: mean bound over those keys                            */
     double model_train_ms;     /* learned: training time (GPU)                                   */
+    uint32_t leaf_ties;        /* F16HI hybrid: PLANB_LEAF_TIES_VOTE or _WALK in use; else 0     */
+    uint32_t pad0;
 } planb_stats_t;
 
 /*

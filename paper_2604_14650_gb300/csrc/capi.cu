@@ -130,6 +130,9 @@ int check_device(int dev) {
 constexpr size_t kSmemBudget = 96 * 1024;   // per CTA; two hybrid CTAs fit one SM
 constexpr size_t kDirBudget = 16 * 1024;     // the hybrid index's radix directory (2^13 + 1 u16)
 constexpr size_t kSmem16Budget = 224 * 1024; // F16HI hybrid: one CTA per SM
+// F16HI hybrid: largest index (bytes of shared memory) with which the leaf ties are walked; above
+// it the SM's L1 cache is too small to keep the leaf lines the walk's reads hit
+constexpr size_t kWalkSmemMax = 128 * 1024;
 
 uint32_t auto_smem_levels(const planb::Layout& L, uint32_t format) {
   // whole tree when it is small, else the deepest prefix of levels within 64 KiB
@@ -363,6 +366,11 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   t->dt.smem_nodes = kernel == planb::kCoop
                          ? static_cast<uint32_t>(planb::smem_bytes_for(t->L, format, s) / 128)
                          : 0;
+  t->dt.leaf_walk = 0;
+  if (format == PLANB_FMT_F16HI && kernel == planb::kHybrid)
+    t->dt.leaf_walk = o.leaf_ties == PLANB_LEAF_TIES_WALK ||
+                      (o.leaf_ties == PLANB_LEAF_TIES_AUTO &&
+                       planb::hybrid_smem_bytes(t->dt) <= kWalkSmemMax);
   rc = planb::plan_launch(t->dt, device, o.block_threads, o.ctas_per_sm, t->cfg);
   if (rc) return rc;
   t->upload_ms = ms_since(t1);
@@ -490,6 +498,7 @@ int planb_build(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint
   if (o.format == PLANB_FMT_F16HI && o.kernel > PLANB_KERNEL_HYBRID) return PLANB_EINVAL;
   if (o.model_leaves < 0 || o.model_leaves > 8192 || o.model_iters < -1) return PLANB_EINVAL;
   if (o.builder != PLANB_BUILDER_HOST && o.builder != PLANB_BUILDER_DEVICE) return PLANB_EINVAL;
+  if (o.leaf_ties < PLANB_LEAF_TIES_AUTO || o.leaf_ties > PLANB_LEAF_TIES_WALK) return PLANB_EINVAL;
   try {
     int dev = o.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return PLANB_ENODEV;
@@ -803,6 +812,8 @@ int planb_stats(const planb_fib* fib_c, planb_stats_t* out) {
   out->threads = static_cast<uint32_t>(t->cfg.threads);
   out->ctas = static_cast<uint32_t>(t->cfg.blocks);
   out->smem_bytes = static_cast<uint32_t>(t->cfg.smem_bytes);
+  if (t->dt.format == PLANB_FMT_F16HI && t->dt.kernel == planb::kHybrid)
+    out->leaf_ties = t->dt.leaf_walk ? PLANB_LEAF_TIES_WALK : PLANB_LEAF_TIES_VOTE;
   if (t->dt.kernel == planb::kLearned) {
     out->model_leaves = t->model.P.leaves;
     out->model_iters = t->model.iters;

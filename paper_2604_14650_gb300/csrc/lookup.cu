@@ -417,7 +417,9 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
 // trip before the next hop instead of two. One 1024-thread CTA per SM holds the index; in phase B
 // lane j of an 8-lane group loads the high halves of keys 2j and 2j+1 (16 bytes, so the group's
 // loads are the node's one 128-byte line) and the count is the sum of two ballots.
-template <int DB, bool LAZY = false>
+// WALK: the leaf level counts high halves only and each owner lane settles a tie afterwards (see
+// PLANB_LEAF_TIES_WALK); otherwise every level votes on possible ties.
+template <int DB, bool LAZY = false, bool WALK = false>
 __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
@@ -437,6 +439,7 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   const uint32_t j = lane & 7u;
   const uint32_t gshift = g * 8u;
   const uint32_t gmask = 0xFFu << gshift;
+  const uint32_t bsel = g | ((g + 4u) << 4) | (g << 8) | ((g + 4u) << 12);
   const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
   const ulonglong2* hi2 = reinterpret_cast<const ulonglong2*>(p.nodes_hi);
@@ -474,7 +477,13 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
                                my_lo, p.xlo + mine);
     uint64_t my_rank = cnt;
     if constexpr (DB > 0) {
-      const uint32_t my_node = p.sidx_node + cnt;
+      // A level compares full keys: the group votes on keys whose high half may equal the
+      // address's (equal low 32 bits), and where one does the low halves decide. Under WALK the
+      // leaf level counts high halves only, and the owner lane settles a tie afterwards: keys
+      // equal to the address in the high half follow the counted ones in key order, so the exact
+      // count adds those among them whose low half is below the address's.
+      uint32_t my_leaf = p.sidx_node + cnt;
+      uint32_t my_c = 0;
 #pragma unroll
       for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
         uint64_t qh[kRounds];
@@ -483,18 +492,25 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
         for (int i = 0; i < kRounds; i++) {
           const uint32_t src = gshift + r0 + i;
           qh[i] = __shfl_sync(kFull, my_hi, src);
-          nd[i] = __shfl_sync(kFull, my_node, src);
+          nd[i] = __shfl_sync(kFull, my_leaf, src);
         }
 #pragma unroll
         for (int l = 0; l < DB; l++) {
           ulonglong2 kh[kRounds];
 #pragma unroll
           for (int i = 0; i < kRounds; i++) kh[i] = __ldg(hi2 + static_cast<uint64_t>(nd[i]) * 8u + j);
-          // (few predicates live at once: the equalities are recomputed on the tie path)
-          bool anyeq = false;
+          bool tie = false;
+          if (l + 1 < DB || !WALK) {
+            // (few predicates live at once: the equalities are recomputed on the tie path)
+            bool anyeq = false;
 #pragma unroll
-          for (int i = 0; i < kRounds; i++) anyeq |= (kh[i].x == qh[i]) | (kh[i].y == qh[i]);
-          const bool tie = __any_sync(kFull, anyeq);
+            for (int i = 0; i < kRounds; i++) {
+              const uint32_t q32 = static_cast<uint32_t>(qh[i]);
+              anyeq |= (static_cast<uint32_t>(kh[i].x) == q32) |
+                       (static_cast<uint32_t>(kh[i].y) == q32);
+            }
+            tie = __any_sync(kFull, anyeq);
+          }
 #pragma unroll
           for (int i = 0; i < kRounds; i++) {
             bool lt0 = kh[i].x < qh[i], lt1 = kh[i].y < qh[i];
@@ -509,25 +525,70 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
               if (kh[i].x == qh[i]) lt0 = __ldg(p.nodes_lo + at) < ql;
               if (kh[i].y == qh[i]) lt1 = __ldg(p.nodes_lo + at + 1u) < ql;
             }
-            const uint32_t c = __popc(__ballot_sync(kFull, lt0) & gmask) +
-                               __popc(__ballot_sync(kFull, lt1) & gmask);
+            // the group's byte of both ballots in one word (twice), counted at once
+            const uint32_t c =
+                __popc(__byte_perm(__ballot_sync(kFull, lt0), __ballot_sync(kFull, lt1), bsel)) >> 1;
             if (l + 1 < DB) {
               nd[i] = nd[i] * 17u + 1u + c;
             } else if (j == r0 + i) {
-              my_rank = static_cast<uint64_t>(nd[i] - p.internal_nodes) * 16u + c;
+              my_leaf = nd[i];
+              my_c = c;
             }
           }
         }
       }
-    }
+      if constexpr (!WALK) {
+        my_rank = static_cast<uint64_t>(my_leaf - p.internal_nodes) * 16u + my_c;
 #ifdef PLANB_BOUNDS_CHECK
-    if (my_rank >= p.n_intervals) {
-      report(p.status, 4u);
-      my_rank = 0;
-    }
+        if (my_rank >= p.n_intervals) {
+          report(p.status, 4u);
+          my_rank = 0;
+        }
 #endif
-    const uint16_t v = __ldg(p.values + my_rank);
-    if (ok) p.out[mine] = v;
+        const uint16_t v = __ldg(p.values + my_rank);
+        if (ok) p.out[mine] = v;
+        continue;
+      }
+      // settle a high-half tie at the leaf (the key after the counted ones, if any, is the
+      // candidate; it is read together with the next hop of the high-half count)
+      const uint64_t at = static_cast<uint64_t>(my_leaf) * 16u + (my_c < 16u ? my_c : 15u);
+      const uint64_t kc = __ldg(p.nodes_hi + at);
+      my_rank = static_cast<uint64_t>(my_leaf - p.internal_nodes) * 16u + my_c;
+#ifdef PLANB_BOUNDS_CHECK
+      if (my_rank >= p.n_intervals) {
+        report(p.status, 4u);
+        my_rank = 0;
+      }
+#endif
+      uint16_t v = __ldg(p.values + my_rank);
+      if (my_c < 16u && kc == my_hi) {
+        const uint64_t ql = my_lo.get(p.xlo + mine);
+        uint32_t c = my_c;
+        while (c < 16u && __ldg(p.nodes_hi + at + (c - my_c)) == my_hi &&
+               __ldg(p.nodes_lo + at + (c - my_c)) < ql)
+          c++;
+        if (c != my_c) {
+          my_rank += c - my_c;
+#ifdef PLANB_BOUNDS_CHECK
+          if (my_rank >= p.n_intervals) {
+            report(p.status, 4u);
+            my_rank = 0;
+          }
+#endif
+          v = __ldg(p.values + my_rank);
+        }
+      }
+      if (ok) p.out[mine] = v;
+    } else {
+#ifdef PLANB_BOUNDS_CHECK
+      if (my_rank >= p.n_intervals) {
+        report(p.status, 4u);
+        my_rank = 0;
+      }
+#endif
+      const uint16_t v = __ldg(p.values + my_rank);
+      if (ok) p.out[mine] = v;
+    }
   }
 }
 
@@ -590,18 +651,24 @@ KernelFn kernel_for(const DevTable& t, bool multi = false, bool lazy = false) {
   }
   static const KernelFn hyb_lazy[2][kMaxDepth + 1] = {PLANB_HYB_LAZY(false), PLANB_HYB_LAZY(true)};
 #undef PLANB_HYB_LAZY
-  static const KernelFn hyb16[2][kMaxDepth + 1] = {
-      {lookup_hybrid16<0>, lookup_hybrid16<1>, lookup_hybrid16<2>, lookup_hybrid16<3>,
-       lookup_hybrid16<4>, lookup_hybrid16<5>, lookup_hybrid16<6>, lookup_hybrid16<7>,
-       lookup_hybrid16<8>, lookup_hybrid16<9>, lookup_hybrid16<10>},
-      {lookup_hybrid16<0, true>, lookup_hybrid16<1, true>, lookup_hybrid16<2, true>,
-       lookup_hybrid16<3, true>, lookup_hybrid16<4, true>, lookup_hybrid16<5, true>,
-       lookup_hybrid16<6, true>, lookup_hybrid16<7, true>, lookup_hybrid16<8, true>,
-       lookup_hybrid16<9, true>, lookup_hybrid16<10, true>}};
+#define PLANB_HYB16(L, W)                                                                       \
+  {                                                                                               \
+    lookup_hybrid16<0, L, W>, lookup_hybrid16<1, L, W>, lookup_hybrid16<2, L, W>,                 \
+        lookup_hybrid16<3, L, W>, lookup_hybrid16<4, L, W>, lookup_hybrid16<5, L, W>,             \
+        lookup_hybrid16<6, L, W>, lookup_hybrid16<7, L, W>, lookup_hybrid16<8, L, W>,             \
+        lookup_hybrid16<9, L, W>, lookup_hybrid16<10, L, W>                                       \
+  }
+  // [lazy][leaf walk]
+  static const KernelFn hyb16[2][2][kMaxDepth + 1] = {
+      {PLANB_HYB16(false, false), PLANB_HYB16(false, true)},
+      {PLANB_HYB16(true, false), PLANB_HYB16(true, true)}};
+#undef PLANB_HYB16
   const uint32_t D = t.depth;
   if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
   if (t.format == PLANB_FMT_F16HI && t.kernel == kHybrid)
-    return (!multi && t.smem_levels <= D) ? hyb16[lazy ? 1 : 0][D - t.smem_levels] : nullptr;
+    return (!multi && t.smem_levels <= D)
+               ? hyb16[lazy ? 1 : 0][t.leaf_walk ? 1 : 0][D - t.smem_levels]
+               : nullptr;
   if (t.format == PLANB_FMT_F16HI) return f16[D];
   const bool packed = t.format == PLANB_FMT_F8V7;
   if (t.kernel == kHybrid && multi)
@@ -653,6 +720,12 @@ int dynamic_smem_limit(const void* fn, int device, int* limit) {
   return *limit > 0 ? PLANB_OK : PLANB_EINVAL;
 }
 
+size_t hybrid_smem_bytes(const DevTable& t) {
+  return static_cast<size_t>((t.sidx_n + 1) & ~1ull) * 8u +
+         (t.dir_bits ? ((((1u << t.dir_bits) + 1u) + 7u) & ~7u) * 2u : 0u) +
+         (t.kernel == kLearned ? static_cast<size_t>(t.lp.leaves) * 18u : 0u);
+}
+
 int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, LaunchCfg& cfg) {
   KernelFn fn = kernel_for(t);
   if (!fn) return PLANB_EINVAL;
@@ -664,9 +737,7 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
   if (threads % 32 || threads > max_threads) return PLANB_EINVAL;
   cfg.threads = threads;
   if (hyb || hyb16)
-    cfg.smem_bytes = static_cast<size_t>((t.sidx_n + 1) & ~1ull) * 8u +
-                     (t.dir_bits ? ((((1u << t.dir_bits) + 1u) + 7u) & ~7u) * 2u : 0u) +
-                     (t.kernel == kLearned ? static_cast<size_t>(t.lp.leaves) * 18u : 0u);
+    cfg.smem_bytes = hybrid_smem_bytes(t);
   else if (t.kernel == kFlat && f8)
     cfg.smem_bytes = 0;
   else

@@ -207,7 +207,12 @@ struct DevTable {
   const LeafModel* leaves;  // learned: leaf models (device)
   const uint16_t* leaf_err; // learned: per-leaf window half-width (device)
   LearnedParams lp;         // learned: root weights and constants
+  uint32_t leaf_walk;       // F16HI hybrid: leaf ties settled by a walk (1) or a group vote (0)
 };
+
+// Dynamic shared memory of a hybrid or learned launch: the index's high halves, the radix
+// directory and the learned leaf models.
+size_t hybrid_smem_bytes(const DevTable& t);
 
 struct LaunchCfg {
   int threads = 256;

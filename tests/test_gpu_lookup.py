@@ -57,13 +57,20 @@ def boundary_probes(f):
 FORMATS = ["f8x128", "f16hi"]
 # (node format, kernel) pairs: every lookup kernel of the library
 VARIANTS = [("f8v7", "hybrid"), ("f8v7", "learned"), ("f8x128", "hybrid"), ("f8x128", "learned"),
-            ("f8x128", "coop"), ("f8x128", "flat"), ("f16hi", "coop"), ("f16hi", "hybrid")]
+            ("f8x128", "coop"), ("f8x128", "flat"), ("f16hi", "coop"), ("f16hi", "hybrid:vote"),
+            ("f16hi", "hybrid:walk")]
 VIDS = [f"{f}-{k}" for f, k in VARIANTS]
 
 
 def make(f, which, **kw):
+    """A table of format and kernel `which`; "hybrid:walk" / "hybrid:vote" also set the F16HI
+    hybrid's leaf tie handling (and check that it is the one in use)."""
     fmt, kernel = which
-    return pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel, **kw)
+    kernel, _, ties = kernel.partition(":")
+    fib = pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel, leaf_ties=ties or "auto", **kw)
+    if ties:
+        assert fib.stats()["leaf_ties"] == pb.LEAF_TIES[ties]
+    return fib
 
 
 @pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
