@@ -436,23 +436,19 @@ def run_planb(args):
         fib.lookup_ptr(hp, lp, n, op, stream)
         stream.synchronize()
         ref_out = d_out.clone()
-        for name, fmt, kern, ties in (
-                ("flat binary search (std::lower_bound analogue)", "f8x128", "flat", None),
-                ("linearized tree, coop 8-lane, 128-bit keys", "f8x128", "coop", None),
-                ("linearized tree, coop 16-lane, 64-bit key halves", "f16hi", "coop", None),
-                ("linearized tree, hybrid smem index + coop L2", "f8x128", "hybrid", None),
-                ("hybrid + next hops packed in the leaf line", "f8v7", "hybrid", None),
-                ("hybrid on 16-key leaves (index over the leaves, one L2 line), leaf ties voted",
-                 "f16hi", "hybrid", "vote"),
-                ("hybrid on 16-key leaves, leaf counted by high halves, ties walked",
-                 "f16hi", "hybrid", "walk"),
-                ("learned position model (RMI, MLP root) + tree, 128-bit keys",
-                 "f8x128", "learned", None),
-                ("learned position model (RMI, MLP root) + tree, packed leaves",
-                 "f8v7", "learned", None)):
-            key = f"{fmt}/{kern}" + (f"/{ties}" if ties else "")
+        for name, fmt, kern in (("flat binary search (std::lower_bound analogue)", "f8x128", "flat"),
+                                ("linearized tree, coop 8-lane, 128-bit keys", "f8x128", "coop"),
+                                ("linearized tree, coop 16-lane, 64-bit key halves", "f16hi", "coop"),
+                                ("linearized tree, hybrid smem index + coop L2", "f8x128", "hybrid"),
+                                ("hybrid + next hops packed in the leaf line", "f8v7", "hybrid"),
+                                ("hybrid on 16-key leaves (index over the leaves, one L2 line)",
+                                 "f16hi", "hybrid"),
+                                ("learned position model (RMI, MLP root) + tree, 128-bit keys",
+                                 "f8x128", "learned"),
+                                ("learned position model (RMI, MLP root) + tree, packed leaves",
+                                 "f8v7", "learned")):
             with pb.Fib(fib_in.hi, fib_in.lo, fib_in.len, fib_in.nh, format=fmt, kernel=kern,
-                        leaf_ties=ties or "auto", device=local) as v:
+                        device=local) as v:
                 for _ in range(2):
                     v.lookup_ptr(hp, lp, n, op, stream)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -462,18 +458,18 @@ def run_planb(args):
                 b.record(stream)
                 stream.synchronize()
                 vs = v.stats()
-                ablation[key] = {
+                ablation[f"{fmt}/{kern}"] = {
                     "what": name, "B_lookups_per_s": n * args.ablation_steps / a.elapsed_time(b) / 1e6,
                     "depth": vs["depth"], "smem_levels": vs["smem_levels"],
                     "smem_bytes": vs["smem_bytes"], "threads": vs["threads"], "ctas": vs["ctas"]}
                 if kern == "learned":
-                    ablation[key]["model"] = {
+                    ablation[f"{fmt}/{kern}"]["model"] = {
                         k[6:]: vs[k] for k in ("model_leaves", "model_iters", "model_max_err",
                                                "model_loss0", "model_loss", "model_covered",
                                                "model_mean_err", "model_train_ms")}
                 # results of every variant equal the headline launch's (exactness across kernels)
                 same = torch.equal(d_out.view(torch.int16), ref_out)
-                ablation[key]["same_results_as_headline"] = bool(same)
+                ablation[f"{fmt}/{kern}"]["same_results_as_headline"] = bool(same)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -489,8 +485,7 @@ def run_planb(args):
     kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
     # the kernel's name as ncu prints it
     if kname == "hybrid" and args.format == "f16hi":
-        kernel = (f"lookup_hybrid16<{st['depth'] - st['smem_levels']}, 0, "
-                  f"{1 if st['leaf_ties'] == 2 else 0}>")
+        kernel = f"lookup_hybrid16<{st['depth'] - st['smem_levels']}>"
     elif kname == "hybrid":
         kernel = (f"lookup_hybrid<{st['depth'] - st['smem_levels']}, "
                   f"{1 if args.format == 'f8v7' else 0}, 0, 0, 0>")
@@ -526,7 +521,6 @@ def run_planb(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded)",
         "config": {"workload": workload_name(args), "prefixes": args.prefixes,
                    "lookups_per_gpu": n, "traffic": args.traffic, "format": args.format,
-                   "leaf_ties": {1: "vote", 2: "walk"}.get(st["leaf_ties"]),
                    "kernel": kname, "depth": st["depth"], "smem_levels": st["smem_levels"],
                    "threads": st["threads"], "ctas": st["ctas"], "smem_bytes": st["smem_bytes"],
                    "intervals": st["n_intervals"], "table_bytes": st["node_bytes"] + st["value_bytes"],

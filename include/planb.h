@@ -45,7 +45,11 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
  * with 128-bit keys instead of the 64-bit key halves the paper uses). */
 #define PLANB_FMT_F8X128 0
 /* F16HI: 16 key high halves per 128-byte node, 17-ary (Section 3.2: 128-byte lines give 16-key,
- * 17-ary nodes); a parallel array holds the low halves, read only when a high half ties. */
+ * 17-ary nodes); a parallel array holds the low halves. Lookups count keys by their high halves
+ * alone. The next hops are 32-bit words whose bit 16 marks an interval whose key (its inclusive
+ * end) has a low half other than all-ones (a /65../128 boundary): only at such a count can a key
+ * that shares the address's high half still be below the address, and only there are the low
+ * halves (the key's and the address's) read. */
 #define PLANB_FMT_F16HI 1
 /* F8V7: internal nodes as F8X128; each 128-byte leaf line holds 7 keys and, in its last
  * 16 bytes, the 7 next hops of those keys. The paper keeps values in a separate array (Section 3.2,
@@ -88,19 +92,6 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
 #define PLANB_BUILDER_HOST 0
 #define PLANB_BUILDER_DEVICE 1
 
-/* How the F16HI hybrid kernel settles keys whose high half equals the address's at the leaf
- * (planb_opts.leaf_ties; results are the same either way).
- * vote: every node search, leaf included, also votes on equal high halves (a 32-bit pre-test of
- *   the group's keys) and compares low halves when a tie is possible.
- * walk: the leaf is counted by high halves only; each lane then reads the key that follows its
- *   count, alongside its next hop, and on an equal high half walks the equal keys by their low
- *   halves (they follow the counted ones in key order). Fewer instructions, one more scattered
- *   8-byte read per address, which costs little while the SM has room left for its L1 cache.
- * auto: walk when the shared-memory index takes at most 128 KB, else vote. */
-#define PLANB_LEAF_TIES_AUTO 0
-#define PLANB_LEAF_TIES_VOTE 1
-#define PLANB_LEAF_TIES_WALK 2
-
 typedef struct planb_fib planb_fib; /* opaque; owns all host and device memory of one table */
 
 typedef struct {
@@ -118,8 +109,7 @@ typedef struct {
     int32_t model_leaves;   /* learned: leaf models L; 0 = automatic                              */
     int32_t model_iters;    /* learned: Adam steps of the root's training; -1 = default (2000)    */
     int32_t builder;        /* PLANB_BUILDER_*: where the build steps run; default host          */
-    int32_t leaf_ties;      /* PLANB_LEAF_TIES_*: F16HI hybrid leaf tie handling; default auto   */
-    int32_t reserved[3];    /* zero                                                              */
+    int32_t reserved[4];    /* zero                                                              */
 } planb_opts;
 
 /* Fills *o with the defaults. */
@@ -158,8 +148,6 @@ typedef struct {
     double model_covered;      /* learned: share of keys in leaves within the window limit       */
     double model_mean_err;     /* learned: mean bound over those keys                            */
     double model_train_ms;     /* learned: training time (GPU)                                   */
-    uint32_t leaf_ties;        /* F16HI hybrid: PLANB_LEAF_TIES_VOTE or _WALK in use; else 0     */
-    uint32_t pad0;
 } planb_stats_t;
 
 /*

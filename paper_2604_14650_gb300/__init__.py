@@ -4,7 +4,7 @@ Prefixes become sorted elementary intervals (Section 3.1), laid out as a lineari
 (Section 3.2) that hand-written sm_103a CUDA kernels descend for each 128-bit address. The compute
 lives in ``libplanb.so`` (C ABI in ``include/planb.h``); this package is its Python binding.
 """
-from .binding import (FORMATS, KERNELS, LEAF_TIES, Fib, MultiFib, Server, PlanbError, child_index, debug_inject, intervals,  # noqa: F401
+from .binding import (FORMATS, KERNELS, Fib, MultiFib, Server, PlanbError, child_index, debug_inject, intervals,  # noqa: F401
                       layout_info, library_path, load, mlp_forward, mlp_grad, version)
 
 

@@ -23,7 +23,6 @@ PLANB_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EDEVICE", -5: "ENODEV", -6: "ETIMEOUT"}
 FORMATS = {"f8x128": 0, "f16hi": 1, "f8v7": 2}
 KERNELS = {"auto": 0, "coop": 1, "hybrid": 2, "flat": 3, "learned": 4}
-LEAF_TIES = {"auto": 0, "vote": 1, "walk": 2}
 BUILDERS = {"host": 0, "device": 1}
 
 
@@ -43,8 +42,7 @@ class Opts(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("format", C.c_int32), ("merge_equal_nh", C.c_int32),
                 ("smem_levels", C.c_int32), ("device", C.c_int32), ("block_threads", C.c_int32),
                 ("ctas_per_sm", C.c_int32), ("kernel", C.c_int32), ("model_leaves", C.c_int32),
-                ("model_iters", C.c_int32), ("builder", C.c_int32), ("leaf_ties", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("model_iters", C.c_int32), ("builder", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class Stats(C.Structure):
@@ -59,7 +57,7 @@ class Stats(C.Structure):
                 ("model_iters", C.c_uint32), ("model_max_err", C.c_uint32),
                 ("builder", C.c_uint32), ("model_loss0", C.c_double), ("model_loss", C.c_double),
                 ("model_covered", C.c_double), ("model_mean_err", C.c_double),
-                ("model_train_ms", C.c_double), ("leaf_ties", C.c_uint32), ("pad0", C.c_uint32)]
+                ("model_train_ms", C.c_double)]
 
 
 class LayoutT(C.Structure):
@@ -254,8 +252,7 @@ class Fib:
     def __init__(self, hi, lo, ln, nh, *, format: str = "f8x128", merge: bool = False,
                  smem_levels: int = -1, device: int | None = None, block_threads: int = 0,
                  ctas_per_sm: int = 0, kernel: str = "auto", model_leaves: int = 0,
-                 model_iters: int = -1, builder: str = "host", leaf_ties: str = "auto",
-                 variant: str = "libplanb.so"):
+                 model_iters: int = -1, builder: str = "host", variant: str = "libplanb.so"):
         self._lib = load(variant)
         self._h = None
         hi, lo, ln, nh = _np(hi, np.uint64), _np(lo, np.uint64), _np(ln, np.uint8), _np(nh, np.uint16)
@@ -273,7 +270,6 @@ class Fib:
         o.model_leaves = model_leaves
         o.model_iters = model_iters
         o.builder = BUILDERS[builder]
-        o.leaf_ties = LEAF_TIES[leaf_ties]
         h = C.c_void_p()
         _check(self._lib.planb_build(_ptr(hi), _ptr(lo), _ptr(ln), _ptr(nh), hi.size, C.byref(o),
                                      C.byref(h)), "planb_build")

@@ -266,6 +266,12 @@ void fill_f8v7(const Intervals& iv, const Layout& L, uint64_t* nodes) {
   }
 }
 
+void nh_words(const Intervals& iv, uint32_t* out) {
+  const uint64_t m = iv.nh.size();
+  for (uint64_t i = 0; i < m; i++)
+    out[i] = iv.nh[i] | ((i + 1 < m && lo64(iv.start[i + 1]) != 0) ? (1u << 16) : 0u);
+}
+
 void fill_f16hi(const Intervals& iv, const Layout& L, uint64_t* node_hi, uint64_t* node_lo) {
   fill_generic(iv, L, [node_hi, node_lo, k = L.k](uint64_t node, uint32_t slot, u128 key) {
     node_hi[node * k + slot] = hi64(key);

@@ -130,9 +130,6 @@ int check_device(int dev) {
 constexpr size_t kSmemBudget = 96 * 1024;   // per CTA; two hybrid CTAs fit one SM
 constexpr size_t kDirBudget = 16 * 1024;     // the hybrid index's radix directory (2^13 + 1 u16)
 constexpr size_t kSmem16Budget = 224 * 1024; // F16HI hybrid: one CTA per SM
-// F16HI hybrid: largest index (bytes of shared memory) with which the leaf ties are walked; above
-// it the SM's L1 cache is too small to keep the leaf lines the walk's reads hit
-constexpr size_t kWalkSmemMax = 128 * 1024;
 
 uint32_t auto_smem_levels(const planb::Layout& L, uint32_t format) {
   // whole tree when it is small, else the deepest prefix of levels within 64 KiB
@@ -250,7 +247,9 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   planb::DirParams dp;
   if (kernel == planb::kHybrid) dp.bits = planb::dir_bits_for(sidx_n);
   const size_t dirb = planb::dir_bytes(dp);
-  const size_t val_bytes = ((static_cast<size_t>(m) * 2 + 255) / 256) * 256;
+  // next hops: u16 per interval; F16HI: u32 words that also flag possible high-half ties
+  const size_t vw = format == PLANB_FMT_F16HI ? 4 : 2;
+  const size_t val_bytes = ((static_cast<size_t>(m) * vw + 255) / 256) * 256;
   const size_t model_bytes =
       learned ? ((static_cast<size_t>(model_leaves) * 18 + 255) / 256) * 256 : 0;
   std::vector<uint64_t> host;
@@ -301,7 +300,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   }
   char* base = static_cast<char*>(t->mem);
   const size_t head = node_bytes + lo_bytes + sidx_bytes + dirb;
-  t->dump_bytes = head + m * 2;
+  t->dump_bytes = head + m * vw;
   if (on_dev) {
     // the index region's rounding tail is zero, as in the host-filled image
     const size_t sidx_used = static_cast<size_t>(sidx_n) * 16;
@@ -312,7 +311,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
     rc = planb::gpu_fill(giv, t->L, format, s, sidx_n, base,
                          lo_bytes ? reinterpret_cast<uint64_t*>(base + node_bytes) : nullptr,
                          reinterpret_cast<uint64_t*>(base + node_bytes + lo_bytes),
-                         reinterpret_cast<uint16_t*>(base + head), bs->s);
+                         base + head, bs->s);
     if (rc) return fail_detail(rc, "device layout fill", cudaGetLastError());
     if (cudaStreamSynchronize(bs->s) != cudaSuccess)
       return fail_detail(PLANB_ECUDA, "device layout fill", cudaGetLastError());
@@ -329,10 +328,17 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                      cudaMemcpyHostToDevice) != cudaSuccess)
         return PLANB_ECUDA;
     }
-  } else if (cudaMemcpy(base, host.data(), head, cudaMemcpyHostToDevice) != cudaSuccess ||
-             cudaMemcpy(base + head, iv.nh.data(), m * 2, cudaMemcpyHostToDevice) !=
-                 cudaSuccess) {
-    return PLANB_ECUDA;
+  } else {
+    std::vector<uint32_t> words;
+    const void* vals = iv.nh.data();
+    if (format == PLANB_FMT_F16HI) {
+      words.resize(m);
+      planb::nh_words(iv, words.data());
+      vals = words.data();
+    }
+    if (cudaMemcpy(base, host.data(), head, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(base + head, vals, m * vw, cudaMemcpyHostToDevice) != cudaSuccess)
+      return PLANB_ECUDA;
   }
   if (learned) {
     char* mb = base + head + val_bytes;
@@ -366,11 +372,6 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   t->dt.smem_nodes = kernel == planb::kCoop
                          ? static_cast<uint32_t>(planb::smem_bytes_for(t->L, format, s) / 128)
                          : 0;
-  t->dt.leaf_walk = 0;
-  if (format == PLANB_FMT_F16HI && kernel == planb::kHybrid)
-    t->dt.leaf_walk = o.leaf_ties == PLANB_LEAF_TIES_WALK ||
-                      (o.leaf_ties == PLANB_LEAF_TIES_AUTO &&
-                       planb::hybrid_smem_bytes(t->dt) <= kWalkSmemMax);
   rc = planb::plan_launch(t->dt, device, o.block_threads, o.ctas_per_sm, t->cfg);
   if (rc) return rc;
   t->upload_ms = ms_since(t1);
@@ -498,7 +499,6 @@ int planb_build(const uint64_t* prefix_hi, const uint64_t* prefix_lo, const uint
   if (o.format == PLANB_FMT_F16HI && o.kernel > PLANB_KERNEL_HYBRID) return PLANB_EINVAL;
   if (o.model_leaves < 0 || o.model_leaves > 8192 || o.model_iters < -1) return PLANB_EINVAL;
   if (o.builder != PLANB_BUILDER_HOST && o.builder != PLANB_BUILDER_DEVICE) return PLANB_EINVAL;
-  if (o.leaf_ties < PLANB_LEAF_TIES_AUTO || o.leaf_ties > PLANB_LEAF_TIES_WALK) return PLANB_EINVAL;
   try {
     int dev = o.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return PLANB_ENODEV;
@@ -802,7 +802,7 @@ int planb_stats(const planb_fib* fib_c, planb_stats_t* out) {
   out->internal_nodes = t->L.internal_nodes;
   out->leaf_nodes = t->L.leaf_nodes;
   out->node_bytes = t->L.total_nodes() * 128 * (t->dt.format == PLANB_FMT_F16HI ? 2 : 1);
-  out->value_bytes = t->dt.n_intervals * 2;
+  out->value_bytes = t->dt.n_intervals * (t->dt.format == PLANB_FMT_F16HI ? 4 : 2);
   out->version = f->version;
   out->withdraw_absent = f->withdraw_absent;
   out->build_ms = t->build_ms;
@@ -812,8 +812,6 @@ int planb_stats(const planb_fib* fib_c, planb_stats_t* out) {
   out->threads = static_cast<uint32_t>(t->cfg.threads);
   out->ctas = static_cast<uint32_t>(t->cfg.blocks);
   out->smem_bytes = static_cast<uint32_t>(t->cfg.smem_bytes);
-  if (t->dt.format == PLANB_FMT_F16HI && t->dt.kernel == planb::kHybrid)
-    out->leaf_ties = t->dt.leaf_walk ? PLANB_LEAF_TIES_WALK : PLANB_LEAF_TIES_VOTE;
   if (t->dt.kernel == planb::kLearned) {
     out->model_leaves = t->model.P.leaves;
     out->model_iters = t->model.iters;

@@ -88,6 +88,96 @@ __device__ __forceinline__ uint32_t index_count_global(const ulonglong2* sidx, u
   return cnt;
 }
 
+// Entries of the staged high halves Uh[0..N) below the address's high half, started in the
+// address's bucket of the radix directory (the high-half-only count of the F16HI descent).
+__device__ __forceinline__ uint32_t index_count_hi(const uint64_t* Uh, uint32_t N,
+                                                   const uint16_t* Dir, uint32_t dir_bits,
+                                                   uint32_t dir_shift, uint64_t dir_base,
+                                                   uint64_t my_hi) {
+  uint32_t lo = 0, n = N;
+  if (dir_bits) {
+    const uint64_t v = my_hi >> dir_shift;
+    uint64_t bk = v > dir_base ? v - dir_base : 0ull;
+    const uint64_t last = (1ull << dir_bits) - 1ull;
+    bk = bk < last ? bk : last;
+    lo = Dir[bk];
+    n = Dir[bk + 1] - lo;
+  }
+  if (!n) return lo;
+  uint32_t b = lo;
+  while (n > 1) {
+    const uint32_t half = n >> 1;
+    b = Uh[b + half] < my_hi ? b + half : b;
+    n -= half;
+  }
+  return b + (Uh[b] < my_hi ? 1u : 0u);
+}
+
+// The same count read in place from the global index (entries of 16 bytes, high half first) and
+// directory, for launches too small to repay staging.
+__device__ __forceinline__ uint32_t index_count_hi_global(const ulonglong2* sidx, uint32_t N,
+                                                          const uint16_t* dir, uint32_t dir_bits,
+                                                          uint32_t dir_shift, uint64_t dir_base,
+                                                          uint64_t my_hi) {
+  uint32_t lo = 0, n = N;
+  if (dir_bits) {
+    const uint64_t v = my_hi >> dir_shift;
+    uint64_t bk = v > dir_base ? v - dir_base : 0ull;
+    const uint64_t last = (1ull << dir_bits) - 1ull;
+    bk = bk < last ? bk : last;
+    lo = __ldg(dir + bk);
+    n = __ldg(dir + bk + 1) - lo;
+  }
+  if (!n) return lo;
+  uint32_t b = lo;
+  while (n > 1) {
+    const uint32_t half = n >> 1;
+    b = __ldg(&sidx[b + half].x) < my_hi ? b + half : b;
+    n -= half;
+  }
+  return b + (__ldg(&sidx[b].x) < my_hi ? 1u : 0u);
+}
+
+// F16HI next-hop words: bits 0-15 the next hop of an interval, kTieBit set when the interval's key
+// (its inclusive end) has a low half other than all-ones. Only such a key can be below an address
+// whose high half it shares, so only there does a high-half-only count need a second look.
+constexpr uint32_t kTieBit = 1u << 16;
+
+// Settles a high-half-only count on the F16HI leaf level. `rank` counts the keys whose high half
+// is below the address's; `w` is the next-hop word at that rank. Keys whose high half equals the
+// address's follow in key order, sorted by low half, so the exact count adds the leading run of
+// them whose low half is below the address's: found by doubling steps and then halving (a long
+// run of /65+ boundaries inside one /64 costs a logarithmic number of reads). keys_hi / keys_lo
+// are the leaf level's halves (key r at index r), nk the number of keys; lo() yields the address's
+// low half. Returns the settled word and rank.
+template <class Lo>
+__device__ __forceinline__ uint32_t settle_tie(const uint64_t* keys_hi, const uint64_t* keys_lo,
+                                               uint64_t nk, const uint32_t* words,
+                                               uint64_t& rank, uint32_t w, uint64_t my_hi,
+                                               Lo lo) {
+  if (!(w & kTieBit) || __ldg(keys_hi + rank) != my_hi) return w;
+  const uint64_t ql = lo();
+  auto below = [&](uint64_t q) {
+    return q < nk && __ldg(keys_hi + q) == my_hi && __ldg(keys_lo + q) < ql;
+  };
+  if (!below(rank)) return w;
+  uint64_t good = rank, step = 1;
+  while (below(rank + step)) {
+    good = rank + step;
+    step <<= 1;
+  }
+  uint64_t bad = rank + step;
+  while (bad - good > 1) {
+    const uint64_t mid = good + (bad - good) / 2;
+    if (below(mid))
+      good = mid;
+    else
+      bad = mid;
+  }
+  rank = bad;
+  return __ldg(words + rank);
+}
+
 __device__ __forceinline__ uint32_t index_count(const uint64_t* Uh, uint32_t N,
                                                 const uint16_t* Dir, uint32_t dir_bits,
                                                 uint32_t dir_shift, uint64_t dir_base,

@@ -282,6 +282,14 @@ __global__ void k_fill_nodes(FillGeom g, const uint64_t* ihi, const uint64_t* il
   }
 }
 
+// F16HI next-hop words (nh_words): the next hop, and bit 16 when the next interval starts at a
+// nonzero low half (the interval's inclusive end then has a low half other than all-ones).
+__global__ void k_nh_words(uint64_t m, const uint64_t* ilo, const uint16_t* nh, uint32_t* out) {
+  GRID_LOOP(i, m) {
+    out[i] = nh[i] | ((i + 1 < m && ilo[i + 1] != 0) ? (1u << 16) : 0u);
+  }
+}
+
 __global__ void k_fill_sidx(uint64_t n, uint64_t span, const uint64_t* ihi, const uint64_t* ilo,
                             uint64_t n_keys, uint64_t m, uint64_t* out) {
   GRID_LOOP(q, n) {
@@ -536,7 +544,7 @@ int gpu_sweep(const Prefix* d_canon, uint64_t N, bool merge, void* stream, GpuIn
 }
 
 int gpu_fill(const GpuIntervals& iv, const Layout& L, uint32_t format, uint32_t S,
-             uint64_t sidx_n, void* nodes, uint64_t* nodes_lo, uint64_t* sidx, uint16_t* values,
+             uint64_t sidx_n, void* nodes, uint64_t* nodes_lo, uint64_t* sidx, void* values,
              void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaGetLastError();
@@ -575,8 +583,13 @@ int gpu_fill(const GpuIntervals& iv, const Layout& L, uint32_t format, uint32_t 
     }
     k_fill_sidx<<<blocks_for(sidx_n), 256, 0, st>>>(sidx_n, span, ih, il, L.n_keys, iv.m, sidx);
   }
-  if (iv.m && cudaMemcpyAsync(values, in, iv.m * 2, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+  if (format == PLANB_FMT_F16HI) {
+    if (iv.m)
+      k_nh_words<<<blocks_for(iv.m), 256, 0, st>>>(iv.m, il, in, static_cast<uint32_t*>(values));
+  } else if (iv.m &&
+             cudaMemcpyAsync(values, in, iv.m * 2, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
     return PLANB_ECUDA;
+  }
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

@@ -50,6 +50,7 @@ struct KParams {
   const uint64_t* nodes_lo;   // F16HI low halves
   const ulonglong2* sidx;     // hybrid top-of-tree index
   const uint16_t* values;
+  const uint32_t* nh_tie;     // F16HI: next-hop words (bits 0-15 next hop, kTieBit)
   const uint64_t* xhi;
   const uint64_t* xlo;
   uint16_t* out;
@@ -145,9 +146,10 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f8(const KParams p) {
 }
 
 // ------------------------------------------------------------------------------- coop F16HI
-// 16-lane groups, two addresses per warp step; a node is 16 high halves (one 128-byte line). A
-// lane whose high half equals the address's reads the matching low half from the parallel array;
-// the warp takes that branch only when some lane has such a tie.
+// 16-lane groups, two addresses per warp step; a node is 16 high halves (one 128-byte line). The
+// descent counts high halves only (the count of keys whose high half is below the address's); the
+// next-hop word at that count says whether a key sharing the address's high half could still be
+// below it, and settle_tie finishes the count in that rare case.
 template <int D>
 __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -163,6 +165,8 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
   const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
   const uint32_t S = p.smem_levels;
+  const uint64_t leaf_key0 = static_cast<uint64_t>(p.internal_nodes) * 16u;
+  const uint64_t nk = p.n_intervals - 1;
 
   const Seg seg = segment(p);
   for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
@@ -180,12 +184,7 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
       for (int l = 0; l < D; l++) {
         const uint64_t idx = static_cast<uint64_t>(node) * 16u + j;
         const uint64_t kh = (static_cast<uint32_t>(l) < S) ? sm[idx] : __ldg(p.nodes_hi + idx);
-        bool lt = kh < qh;
-        const bool eq = kh == qh;
-        if (__any_sync(kFull, eq)) {
-          if (eq) lt = __ldg(p.nodes_lo + idx) < ql;
-        }
-        const uint32_t m = __ballot_sync(kFull, lt);
+        const uint32_t m = __ballot_sync(kFull, kh < qh);
         c = __popc((m >> gshift) & 0xFFFFu);
         if (l + 1 < D) node = node * 17u + 1u + c;
       }
@@ -196,8 +195,10 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
         rank = 0;
       }
 #endif
-      const uint32_t v = __ldg(p.values + rank);
-      if (j == r) result = v;
+      uint32_t w = __ldg(p.nh_tie + rank);
+      w = settle_tie(p.nodes_hi + leaf_key0, p.nodes_lo + leaf_key0, nk, p.nh_tie, rank, w, qh,
+                     [ql] { return ql; });
+      if (j == r) result = w;
     }
     if (ok) store_out(p, seg.off + mine, static_cast<uint16_t>(result));
   }
@@ -417,9 +418,10 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
 // trip before the next hop instead of two. One 1024-thread CTA per SM holds the index; in phase B
 // lane j of an 8-lane group loads the high halves of keys 2j and 2j+1 (16 bytes, so the group's
 // loads are the node's one 128-byte line) and the count is the sum of two ballots.
-// WALK: the leaf level counts high halves only and each owner lane settles a tie afterwards (see
-// PLANB_LEAF_TIES_WALK); otherwise every level votes on possible ties.
-template <int DB, bool LAZY = false, bool WALK = false>
+// Every level, the index included, counts high halves only; the next-hop word at the resulting
+// count says whether a key sharing the address's high half could still be below the address, and
+// settle_tie finishes the count then. An address's low half is read only in that case.
+template <int DB>
 __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
@@ -438,51 +440,36 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   const uint32_t g = lane >> 3;
   const uint32_t j = lane & 7u;
   const uint32_t gshift = g * 8u;
-  const uint32_t gmask = 0xFFu << gshift;
+  // byte g of each of two ballots, twice: the population count of the word is twice the group's
   const uint32_t bsel = g | ((g + 4u) << 4) | (g << 8) | ((g + 4u) << 12);
   const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
   const ulonglong2* hi2 = reinterpret_cast<const ulonglong2*>(p.nodes_hi);
+  const uint64_t leaf_key0 = static_cast<uint64_t>(p.internal_nodes) * 16u;
+  const uint64_t nk = p.n_intervals - 1;
 
   const Seg seg = segment<false>(p);
-  // LAZY (addresses in host memory): low halves read only on a high-half tie, as lookup_hybrid
-  uint64_t nx_hi = 0, nx_lo = 0;
+  uint64_t nx_hi = 0;
   {
     const uint64_t first = warp * 32 + lane;
-    if (first < seg.n) {
-      nx_hi = p.xhi[first];
-      if (!LAZY) nx_lo = p.xlo[first];
-    }
+    if (first < seg.n) nx_hi = p.xhi[first];
   }
   for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
     const uint64_t mine = base + lane;
     const bool ok = mine < seg.n;
     const uint64_t my_hi = nx_hi;
-    LazyLo my_lo(ok);
-    if (!LAZY) {
-      my_lo.v = nx_lo;
-      my_lo.have = true;
-    }
     {
       const uint64_t next = mine + nwarps * 32;
       nx_hi = next < seg.n ? p.xhi[next] : 0ull;
-      if (!LAZY) nx_lo = next < seg.n ? p.xlo[next] : 0ull;
     }
     uint32_t cnt = 0;
     if (N && staged)
-      cnt = index_count(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, p.sidx, my_hi, my_lo,
-                        p.xlo + mine);
+      cnt = index_count_hi(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, my_hi);
     else if (N)
-      cnt = index_count_global(p.sidx, N, p.dir, p.dir_bits, p.dir_shift, p.dir_base, my_hi,
-                               my_lo, p.xlo + mine);
-    uint64_t my_rank = cnt;
+      cnt = index_count_hi_global(p.sidx, N, p.dir, p.dir_bits, p.dir_shift, p.dir_base, my_hi);
+    uint64_t rank = cnt;
     if constexpr (DB > 0) {
-      // A level compares full keys: the group votes on keys whose high half may equal the
-      // address's (equal low 32 bits), and where one does the low halves decide. Under WALK the
-      // leaf level counts high halves only, and the owner lane settles a tie afterwards: keys
-      // equal to the address in the high half follow the counted ones in key order, so the exact
-      // count adds those among them whose low half is below the address's.
-      uint32_t my_leaf = p.sidx_node + cnt;
+      uint32_t my_node = p.sidx_node + cnt;
       uint32_t my_c = 0;
 #pragma unroll
       for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
@@ -492,103 +479,40 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
         for (int i = 0; i < kRounds; i++) {
           const uint32_t src = gshift + r0 + i;
           qh[i] = __shfl_sync(kFull, my_hi, src);
-          nd[i] = __shfl_sync(kFull, my_leaf, src);
+          nd[i] = __shfl_sync(kFull, my_node, src);
         }
 #pragma unroll
         for (int l = 0; l < DB; l++) {
           ulonglong2 kh[kRounds];
 #pragma unroll
           for (int i = 0; i < kRounds; i++) kh[i] = __ldg(hi2 + static_cast<uint64_t>(nd[i]) * 8u + j);
-          bool tie = false;
-          if (l + 1 < DB || !WALK) {
-            // (few predicates live at once: the equalities are recomputed on the tie path)
-            bool anyeq = false;
-#pragma unroll
-            for (int i = 0; i < kRounds; i++) {
-              const uint32_t q32 = static_cast<uint32_t>(qh[i]);
-              anyeq |= (static_cast<uint32_t>(kh[i].x) == q32) |
-                       (static_cast<uint32_t>(kh[i].y) == q32);
-            }
-            tie = __any_sync(kFull, anyeq);
-          }
 #pragma unroll
           for (int i = 0; i < kRounds; i++) {
-            bool lt0 = kh[i].x < qh[i], lt1 = kh[i].y < qh[i];
-            if (tie) {
-              if (LAZY) {   // the owner of address i of each group reads its low half on a tie
-                const bool eq = (kh[i].x == qh[i]) | (kh[i].y == qh[i]);
-                const uint32_t need = __ballot_sync(kFull, eq) & gmask;
-                if (need && j == r0 + i) my_lo.get(p.xlo + mine);
-              }
-              const uint64_t ql = __shfl_sync(kFull, my_lo.v, gshift + r0 + i);
-              const uint64_t at = static_cast<uint64_t>(nd[i]) * 16u + 2u * j;
-              if (kh[i].x == qh[i]) lt0 = __ldg(p.nodes_lo + at) < ql;
-              if (kh[i].y == qh[i]) lt1 = __ldg(p.nodes_lo + at + 1u) < ql;
-            }
-            // the group's byte of both ballots in one word (twice), counted at once
-            const uint32_t c =
-                __popc(__byte_perm(__ballot_sync(kFull, lt0), __ballot_sync(kFull, lt1), bsel)) >> 1;
+            const uint32_t c = __popc(__byte_perm(__ballot_sync(kFull, kh[i].x < qh[i]),
+                                                  __ballot_sync(kFull, kh[i].y < qh[i]), bsel)) >>
+                               1;
             if (l + 1 < DB) {
               nd[i] = nd[i] * 17u + 1u + c;
             } else if (j == r0 + i) {
-              my_leaf = nd[i];
+              my_node = nd[i];
               my_c = c;
             }
           }
         }
       }
-      if constexpr (!WALK) {
-        my_rank = static_cast<uint64_t>(my_leaf - p.internal_nodes) * 16u + my_c;
-#ifdef PLANB_BOUNDS_CHECK
-        if (my_rank >= p.n_intervals) {
-          report(p.status, 4u);
-          my_rank = 0;
-        }
-#endif
-        const uint16_t v = __ldg(p.values + my_rank);
-        if (ok) p.out[mine] = v;
-        continue;
-      }
-      // settle a high-half tie at the leaf (the key after the counted ones, if any, is the
-      // candidate; it is read together with the next hop of the high-half count)
-      const uint64_t at = static_cast<uint64_t>(my_leaf) * 16u + (my_c < 16u ? my_c : 15u);
-      const uint64_t kc = __ldg(p.nodes_hi + at);
-      my_rank = static_cast<uint64_t>(my_leaf - p.internal_nodes) * 16u + my_c;
-#ifdef PLANB_BOUNDS_CHECK
-      if (my_rank >= p.n_intervals) {
-        report(p.status, 4u);
-        my_rank = 0;
-      }
-#endif
-      uint16_t v = __ldg(p.values + my_rank);
-      if (my_c < 16u && kc == my_hi) {
-        const uint64_t ql = my_lo.get(p.xlo + mine);
-        uint32_t c = my_c;
-        while (c < 16u && __ldg(p.nodes_hi + at + (c - my_c)) == my_hi &&
-               __ldg(p.nodes_lo + at + (c - my_c)) < ql)
-          c++;
-        if (c != my_c) {
-          my_rank += c - my_c;
-#ifdef PLANB_BOUNDS_CHECK
-          if (my_rank >= p.n_intervals) {
-            report(p.status, 4u);
-            my_rank = 0;
-          }
-#endif
-          v = __ldg(p.values + my_rank);
-        }
-      }
-      if (ok) p.out[mine] = v;
-    } else {
-#ifdef PLANB_BOUNDS_CHECK
-      if (my_rank >= p.n_intervals) {
-        report(p.status, 4u);
-        my_rank = 0;
-      }
-#endif
-      const uint16_t v = __ldg(p.values + my_rank);
-      if (ok) p.out[mine] = v;
+      rank = static_cast<uint64_t>(my_node - p.internal_nodes) * 16u + my_c;
     }
+#ifdef PLANB_BOUNDS_CHECK
+    if (rank >= p.n_intervals) {
+      report(p.status, 4u);
+      rank = 0;
+    }
+#endif
+    uint32_t w = __ldg(p.nh_tie + rank);
+    const uint64_t* lo_src = p.xlo + mine;
+    w = settle_tie(p.nodes_hi + leaf_key0, p.nodes_lo + leaf_key0, nk, p.nh_tie, rank, w, my_hi,
+                   [lo_src, ok] { return ok ? *lo_src : 0ull; });
+    if (ok) p.out[mine] = static_cast<uint16_t>(w);
   }
 }
 
@@ -651,24 +575,15 @@ KernelFn kernel_for(const DevTable& t, bool multi = false, bool lazy = false) {
   }
   static const KernelFn hyb_lazy[2][kMaxDepth + 1] = {PLANB_HYB_LAZY(false), PLANB_HYB_LAZY(true)};
 #undef PLANB_HYB_LAZY
-#define PLANB_HYB16(L, W)                                                                       \
-  {                                                                                               \
-    lookup_hybrid16<0, L, W>, lookup_hybrid16<1, L, W>, lookup_hybrid16<2, L, W>,                 \
-        lookup_hybrid16<3, L, W>, lookup_hybrid16<4, L, W>, lookup_hybrid16<5, L, W>,             \
-        lookup_hybrid16<6, L, W>, lookup_hybrid16<7, L, W>, lookup_hybrid16<8, L, W>,             \
-        lookup_hybrid16<9, L, W>, lookup_hybrid16<10, L, W>                                       \
-  }
-  // [lazy][leaf walk]
-  static const KernelFn hyb16[2][2][kMaxDepth + 1] = {
-      {PLANB_HYB16(false, false), PLANB_HYB16(false, true)},
-      {PLANB_HYB16(true, false), PLANB_HYB16(true, true)}};
-#undef PLANB_HYB16
+  // (reads an address's low half only to settle a tie, so it serves host-resident addresses too)
+  static const KernelFn hyb16[kMaxDepth + 1] = {
+      lookup_hybrid16<0>, lookup_hybrid16<1>, lookup_hybrid16<2>, lookup_hybrid16<3>,
+      lookup_hybrid16<4>, lookup_hybrid16<5>, lookup_hybrid16<6>, lookup_hybrid16<7>,
+      lookup_hybrid16<8>, lookup_hybrid16<9>, lookup_hybrid16<10>};
   const uint32_t D = t.depth;
   if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
   if (t.format == PLANB_FMT_F16HI && t.kernel == kHybrid)
-    return (!multi && t.smem_levels <= D)
-               ? hyb16[lazy ? 1 : 0][t.leaf_walk ? 1 : 0][D - t.smem_levels]
-               : nullptr;
+    return (!multi && t.smem_levels <= D) ? hyb16[D - t.smem_levels] : nullptr;
   if (t.format == PLANB_FMT_F16HI) return f16[D];
   const bool packed = t.format == PLANB_FMT_F8V7;
   if (t.kernel == kHybrid && multi)
@@ -720,12 +635,6 @@ int dynamic_smem_limit(const void* fn, int device, int* limit) {
   return *limit > 0 ? PLANB_OK : PLANB_EINVAL;
 }
 
-size_t hybrid_smem_bytes(const DevTable& t) {
-  return static_cast<size_t>((t.sidx_n + 1) & ~1ull) * 8u +
-         (t.dir_bits ? ((((1u << t.dir_bits) + 1u) + 7u) & ~7u) * 2u : 0u) +
-         (t.kernel == kLearned ? static_cast<size_t>(t.lp.leaves) * 18u : 0u);
-}
-
 int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, LaunchCfg& cfg) {
   KernelFn fn = kernel_for(t);
   if (!fn) return PLANB_EINVAL;
@@ -737,7 +646,9 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
   if (threads % 32 || threads > max_threads) return PLANB_EINVAL;
   cfg.threads = threads;
   if (hyb || hyb16)
-    cfg.smem_bytes = hybrid_smem_bytes(t);
+    cfg.smem_bytes = static_cast<size_t>((t.sidx_n + 1) & ~1ull) * 8u +
+                     (t.dir_bits ? ((((1u << t.dir_bits) + 1u) + 7u) & ~7u) * 2u : 0u) +
+                     (t.kernel == kLearned ? static_cast<size_t>(t.lp.leaves) * 18u : 0u);
   else if (t.kernel == kFlat && f8)
     cfg.smem_bytes = 0;
   else
@@ -783,6 +694,7 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   p.nodes_lo = t.nodes_lo;
   p.sidx = reinterpret_cast<const ulonglong2*>(t.sidx);
   p.values = t.values;
+  p.nh_tie = t.format == PLANB_FMT_F16HI ? reinterpret_cast<const uint32_t*>(t.values) : nullptr;
   p.xhi = d_hi;
   p.xlo = d_lo;
   p.out = d_out;

@@ -115,7 +115,8 @@ struct GpuIntervals {
 //   gpu_sweep         steps a2-a3 of a canonical device list: the intervals sweep() would give.
 //   gpu_fill          step a4 into a table's device allocation: the node array(s) (fill_f8x128,
 //                     fill_f8v7 or fill_f16hi), the top-of-tree index of level S (fill_sidx, when
-//                     sidx_n > 0) and the m next hops.
+//                     sidx_n > 0) and the m next hops (F16HI: the m next-hop words of
+//                     nh_words).
 //   gpu_download      the intervals back to the host.
 struct Layout;
 int gpu_canonicalise(const uint64_t* hi, const uint64_t* lo, const uint8_t* len,
@@ -123,7 +124,7 @@ int gpu_canonicalise(const uint64_t* hi, const uint64_t* lo, const uint8_t* len,
 int gpu_sweep(const Prefix* d_canon, uint64_t N, bool merge_equal_nh, void* stream,
               GpuIntervals& out);
 int gpu_fill(const GpuIntervals& iv, const Layout& L, uint32_t format, uint32_t S,
-             uint64_t sidx_n, void* nodes, uint64_t* nodes_lo, uint64_t* sidx, uint16_t* values,
+             uint64_t sidx_n, void* nodes, uint64_t* nodes_lo, uint64_t* sidx, void* values,
              void* stream);
 int gpu_download(const GpuIntervals& iv, void* stream, Intervals& out);
 
@@ -156,6 +157,11 @@ void fill_f8v7(const Intervals& iv, const Layout& L, uint64_t* nodes /* 2*8*tota
 
 // Step a4 for PLANB_FMT_F16HI: node-major hi halves (16 per node) and the parallel lo halves.
 void fill_f16hi(const Intervals& iv, const Layout& L, uint64_t* node_hi, uint64_t* node_lo);
+
+// The F16HI next-hop words: word i = nh[i] | 1 << 16 when interval i has a key (i < m - 1) whose
+// low half is not all-ones, i.e. when start[i+1] has a nonzero low half. The lookup counts keys
+// by high half only; only such a key can be below an address that shares its high half.
+void nh_words(const Intervals& iv, uint32_t* out /* m */);
 
 // Top-of-tree index for the hybrid kernel: entry q is the largest key of the subtree of the q-th
 // node on level S (the key at leaf position (q + 1) * k * b^(D-1-S) - 1), for every q whose entry
@@ -196,7 +202,8 @@ struct DevTable {
   uint64_t dir_base;
   uint32_t kernel;          // Kernel
   const uint64_t* nodes_lo; // F16HI: low halves, same shape; else null
-  const uint16_t* values;   // next hop per interval, n_intervals entries
+  const uint16_t* values;   // next hop per interval, n_intervals entries (F16HI: u32 next-hop
+                            // words, see nh_words)
   uint64_t n_intervals;
   uint64_t total_nodes;
   uint64_t internal_nodes;
@@ -207,12 +214,7 @@ struct DevTable {
   const LeafModel* leaves;  // learned: leaf models (device)
   const uint16_t* leaf_err; // learned: per-leaf window half-width (device)
   LearnedParams lp;         // learned: root weights and constants
-  uint32_t leaf_walk;       // F16HI hybrid: leaf ties settled by a walk (1) or a group vote (0)
 };
-
-// Dynamic shared memory of a hybrid or learned launch: the index's high halves, the radix
-// directory and the learned leaf models.
-size_t hybrid_smem_bytes(const DevTable& t);
 
 struct LaunchCfg {
   int threads = 256;

@@ -57,20 +57,13 @@ def boundary_probes(f):
 FORMATS = ["f8x128", "f16hi"]
 # (node format, kernel) pairs: every lookup kernel of the library
 VARIANTS = [("f8v7", "hybrid"), ("f8v7", "learned"), ("f8x128", "hybrid"), ("f8x128", "learned"),
-            ("f8x128", "coop"), ("f8x128", "flat"), ("f16hi", "coop"), ("f16hi", "hybrid:vote"),
-            ("f16hi", "hybrid:walk")]
+            ("f8x128", "coop"), ("f8x128", "flat"), ("f16hi", "coop"), ("f16hi", "hybrid")]
 VIDS = [f"{f}-{k}" for f, k in VARIANTS]
 
 
 def make(f, which, **kw):
-    """A table of format and kernel `which`; "hybrid:walk" / "hybrid:vote" also set the F16HI
-    hybrid's leaf tie handling (and check that it is the one in use)."""
     fmt, kernel = which
-    kernel, _, ties = kernel.partition(":")
-    fib = pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel, leaf_ties=ties or "auto", **kw)
-    if ties:
-        assert fib.stats()["leaf_ties"] == pb.LEAF_TIES[ties]
-    return fib
+    return pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel, **kw)
 
 
 @pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
@@ -248,7 +241,54 @@ def test_tables_sharing_a_kernel_with_different_shared_memory():
             assert np.array_equal(gpu_lookup(fib, xh, xl), expected(f, xh, xl))
 
 
-@pytest.mark.parametrize("fmt", ["f8x128", "f8v7"])
+@pytest.mark.parametrize("kernel", ["coop", "hybrid"])
+@pytest.mark.parametrize("builder", ["host", "device"])
+def test_f16hi_next_hop_words(kernel, builder):
+    """The F16HI next-hop words at the end of the table image: the next hop of interval i, plus
+    bit 16 exactly when interval i + 1 starts at a nonzero low half (interval i's key then has a
+    low half other than all-ones), from the intervals the host builder reports."""
+    f = synth.gen_fib(30_000, seed=921, nh_max=65535)
+    sh, sl, snh = pb.intervals(f.hi, f.lo, f.len, f.nh)
+    m = sh.size
+    want = snh.astype(np.uint32)
+    want[:-1] |= (sl[1:] != 0).astype(np.uint32) << 16
+    assert 0 < np.count_nonzero(want >> 16) < m // 4      # the /128s (and nothing else) flag
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format="f16hi", kernel=kernel, builder=builder) as fib:
+        assert fib.stats()["value_bytes"] == 4 * m
+        img = fib.table_dump()
+        assert np.array_equal(img[-4 * m:].view(np.uint32), want)
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_long_runs_of_shared_high_halves(variant):
+    """One /64 holding 3,000 /128 routes and nested /80../127 prefixes (thousands of keys with one
+    high half, spanning many leaves and index entries): the F16HI count over them is settled by
+    doubling and halving steps; every kernel agrees with the oracle on each route's address, its
+    neighbours and random addresses of the /64."""
+    f = synth.gen_fib(20_000, seed=931, nh_max=4095)
+    rng = np.random.default_rng(932)
+    h64 = np.uint64(f.hi[np.nonzero(f.len == 48)[0][0]] | np.uint64(0x1234))
+    lo128 = np.unique(rng.integers(0, 2 ** 63, size=3000, dtype=np.uint64) * np.uint64(2))
+    nest_len = rng.integers(80, 128, size=300)
+    nest_lo = rng.integers(0, 2 ** 63, size=300, dtype=np.uint64) * np.uint64(2)
+    eh = np.full(lo128.size + 300 + 1, h64, np.uint64)
+    el = np.concatenate([lo128, nest_lo, np.zeros(1, np.uint64)])
+    eL = np.concatenate([np.full(lo128.size, 128), nest_len, [64]]).astype(np.uint8)
+    en = rng.integers(1, 4096, size=eh.size).astype(np.uint16)
+    g = synth.Fib(np.concatenate([f.hi, eh]), np.concatenate([f.lo, el]),
+                  np.concatenate([f.len, eL]), np.concatenate([f.nh, en]), 0)
+    xl = np.concatenate([lo128, lo128 - np.uint64(1), lo128 + np.uint64(1),
+                         rng.integers(0, 2 ** 63, size=20_000, dtype=np.uint64) * np.uint64(2),
+                         np.array([0, M64], np.uint64)])
+    xh = np.full(xl.size, h64, np.uint64)
+    bh, bl = boundary_probes(g)
+    xh = np.concatenate([xh, bh])
+    xl = np.concatenate([xl, bl])
+    with make(g, variant) as fib:
+        assert np.array_equal(gpu_lookup(fib, xh, xl), expected(g, xh, xl))
+
+
+@pytest.mark.parametrize("fmt", ["f8x128", "f8v7", "f16hi"])
 def test_mapped_lookup_formats_and_ties(fmt):
     """The low half is read only on a tie of high halves: addresses inside /64 and longer prefixes
     (and the 30 % uniform ones) exercise both the tie path and the plain path."""
