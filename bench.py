@@ -598,7 +598,7 @@ def run_vrf64(args):
     choices, fibs = [], []
     t0 = time.perf_counter()
     for t, f in enumerate(fibs_in):
-        opts = {}
+        opts = dict(format=args.format)
         if not args.no_tune:
             idx = np.nonzero(tid == t)[0][: 1 << 21]
             sh = torch.from_numpy(xh[idx].view(np.int64)).cuda()
@@ -729,7 +729,8 @@ def run_serve(args):
     sizes = np.exp(rng.uniform(np.log(1e3), np.log(3e5), args.tables)).astype(int)
     fibs_in = [synth.gen_fib(int(sz), seed=args.seed + 1000 + t, nh_max=4095)
                for t, sz in enumerate(sizes)]
-    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, builder=args.builder) for f in fibs_in]
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format=args.format, builder=args.builder)
+            for f in fibs_in]
     pool = 1 << 17
     pools = [synth.gen_trace(f, pool, seed=args.seed + 3000 + t) for t, f in enumerate(fibs_in)]
     nreq = int(args.rate * args.duration)
@@ -854,7 +855,7 @@ def run_build(args):
             walls = []
             for rep in range(3):
                 t0 = time.perf_counter()
-                fib = pb.Fib(f.hi, f.lo, f.len, f.nh, builder=builder)
+                fib = pb.Fib(f.hi, f.lo, f.len, f.nh, format=args.format, builder=builder)
                 walls.append((time.perf_counter() - t0) * 1e3)
                 if rep < 2:
                     fib.close()

@@ -68,7 +68,8 @@ typedef struct CUstream_st *planb_stream_t; /* same type as cudaStream_t */
  * address's bucket of a radix directory; the remaining levels are descended cooperatively from L2
  * with several addresses per lane group in flight. With F16HI (16 keys per leaf) the index over
  * the leaves of a 200k-prefix table fits one CTA's shared memory, leaving the leaf line alone in
- * L2; such tables run one 1024-thread CTA per SM and cannot join a multi-table group. */
+ * L2; such tables run one 1024-thread CTA per SM (an index too large for the multi-table kernel's
+ * shared memory makes a multi-table group give that table a launch of its own). */
 #define PLANB_KERNEL_HYBRID 2
 /* flat (F8X128 only): per-thread binary search over the sorted interval keys in global memory;
  * the GPU analogue of the paper's ablation baseline (Section 4.5, std::lower_bound) */
@@ -274,8 +275,7 @@ typedef struct planb_multi planb_multi; /* several tables (VRFs) served by one c
  * outlive the group; updates to them are picked up by later lookups. max_batch: most addresses per
  * planb_multi_lookup call (< 2^32); the group owns about max_batch x 20.2 bytes of device scratch
  * (plus about 3 bytes per address per 1,000 tables).
- * Tables built with PLANB_KERNEL_LEARNED, or F16HI tables of the hybrid kernel, cannot join a
- * group. flags: 0, or an OR of the
+ * Tables built with PLANB_KERNEL_LEARNED cannot join a group. flags: 0, or an OR of the
  * PLANB_MULTI_* flags below. Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ECUDA.
  */
 #define PLANB_MULTI_NO_GRAPH 1u  /* flag: launch the pipeline directly instead of a captured graph */
@@ -288,12 +288,14 @@ int planb_multi_create(planb_fib *const *fibs, uint32_t n_tables, size_t max_bat
  * planb_multi_lookup — next hop of n addresses, address i looked up in table d_table[i]
  * (ids >= n_tables give 0). d_addr_hi, d_addr_lo: device u64 arrays; d_table: device u8 array;
  * d_out: device u16 array; all of n entries. The batch is grouped by table (a counting sort on the
- * device); when every table uses the hybrid kernel (F8X128 or F8V7) one persistent launch looks
- * up all groups — each CTA takes a contiguous piece of the grouped batch and stages the index of
- * each table it meets — else each table's group gets its own launch; results are gathered back
- * into the input order. The whole
- * pipeline is captured once as a CUDA graph and replayed while the buffers, n and the tables stay
- * the same; a table swapped by planb_update, or new buffers, cause one new capture. Enqueued on
+ * device); when every table uses the hybrid kernel (any format) and every index fits the shared
+ * memory of a 512-thread CTA, one persistent launch looks up all groups — the CTAs claim pieces
+ * of the grouped batch in order and stage the index of each table they meet — else each table's
+ * group gets its own launch; results are gathered back into the input order. The whole
+ * pipeline is captured once as a CUDA graph and replayed while the buffers and n stay the same;
+ * in the single-launch form a table swapped by planb_update reaches the replays through its
+ * descriptor (copied in stream order), while new buffers, a change of the launch's shape, or a
+ * swap under per-table launches cause one new capture. Enqueued on
  * `stream`; calls on one group are serialised on the host, and since the group's device scratch
  * is reused by every call, all calls on one group must use the same stream.
  * Errors: PLANB_EINVAL (null pointer, misalignment, n > max_batch), PLANB_ECUDA.

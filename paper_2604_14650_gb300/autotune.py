@@ -27,13 +27,15 @@ def size_class(n_intervals: int) -> float:
 
 def candidates(depth: int, auto_levels: int, persistent: bool = False) -> list[dict]:
     """Candidate option sets around the library's automatic choice. persistent=True keeps to the
-    configurations a multi-table group can run in its single persistent launch (hybrid F8X128 or
-    F8V7; that launch fixes threads and CTAs per SM, so only the format and the index depth vary)."""
+    configurations a multi-table group can run in its single persistent launch (the hybrid kernel
+    in any format; that launch fixes threads and CTAs per SM, so only the format and the index
+    depth vary; F16HI tables keep their automatic depth)."""
     out = []
     if persistent:
         for fmt in ("f8x128", "f8v7"):
             for s in sorted({auto_levels, max(auto_levels - 1, 0)}):
                 out.append(dict(format=fmt, kernel="hybrid", smem_levels=s))
+        out.append(dict(format="f16hi", kernel="hybrid", smem_levels=-1))
         return out
     for fmt in ("f8x128", "f8v7"):
         for s in sorted({auto_levels, max(auto_levels - 1, 0)}):

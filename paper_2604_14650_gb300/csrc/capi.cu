@@ -1093,8 +1093,7 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     if (!fibs[t] || fibs[t]->device != fibs[0]->device) return PLANB_EINVAL;
     std::lock_guard<std::mutex> lk(fibs[t]->cur_mu);
     const planb::DevTable& d = fibs[t]->cur->dt;
-    if (d.kernel == planb::kLearned || (d.format == PLANB_FMT_F16HI && d.kernel == planb::kHybrid))
-      return PLANB_EINVAL;   // no multi-table form
+    if (d.kernel == planb::kLearned) return PLANB_EINVAL;   // no multi-table form
   }
   try {
     std::unique_ptr<planb_multi> m(new planb_multi());
@@ -1179,7 +1178,9 @@ int planb_multi_lookup_devn(planb_multi* m, const uint64_t* d_addr_hi, const uin
 
 namespace {
 // Decides whether the current tables can share the single persistent launch (every one a hybrid
-// F8X128 or F8V7 table whose index fits the shared memory) and writes their descriptors.
+// table) and writes their descriptors. An index (with its directory) of at most kSmemBudget bytes
+// is staged in shared memory per CTA; a larger one (an F16HI table built for the single-table
+// kernel's 224 KB) is searched in place, so that it does not cost every table resident CTAs.
 // The descriptors are copied in stream order on st (from page-locked staging), so graphs already
 // queued on st read the old ones and later ones the new, without a host-side wait.
 int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cur,
@@ -1193,9 +1194,7 @@ int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>
   uint64_t max_n = 0;
   for (uint32_t t = 0; t < m->T; t++) {
     const planb::DevTable& d = cur[t]->dt;
-    if (d.kernel != planb::kHybrid ||
-        (d.format != PLANB_FMT_F8X128 && d.format != PLANB_FMT_F8V7) || d.depth < d.smem_levels)
-      return PLANB_OK;
+    if (d.kernel != planb::kHybrid || d.depth < d.smem_levels) return PLANB_OK;
     planb::MultiDesc& x = hd[t];
     x.nodes = d.nodes;
     x.sidx = d.sidx;
@@ -1210,10 +1209,13 @@ int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>
     x.dir_bits = d.dir_bits;
     x.dir_shift = d.dir_shift;
     x.dir_base = d.dir_base;
+    x.f16 = d.format == PLANB_FMT_F16HI ? 1u : 0u;
+    x.nodes_lo = d.nodes_lo;
     x.pad = 0;
     const uint64_t need = ((d.sidx_n + 1) & ~1ull) * 8u +
                           (d.dir_bits ? ((((1ull << d.dir_bits) + 1) + 7) & ~7ull) * 2u : 0u);
-    max_n = std::max<uint64_t>(max_n, need);
+    x.staged = need <= kSmemBudget ? 1u : 0u;
+    if (x.staged) max_n = std::max<uint64_t>(max_n, need);
   }
   // rounded up to 16 KB, so that a table growing a little keeps the captured launch's size,
   // unless the rounding would cost resident CTAs

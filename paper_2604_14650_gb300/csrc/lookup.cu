@@ -421,14 +421,16 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
 // Every level, the index included, counts high halves only; the next-hop word at the resulting
 // count says whether a key sharing the address's high half could still be below the address, and
 // settle_tie finishes the count then. An address's low half is read only in that case.
-template <int DB>
+// MULTI: one table's launch within a multi-table batch (device-side address range, results through
+// the permutation when one is given).
+template <int DB, bool MULTI = false>
 __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
   uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
   uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((N + 1u) & ~1u));
   // a small launch searches the index in place instead of staging it (decided by the host)
-  const bool staged = p.staged != 0;
+  const bool staged = MULTI || p.staged != 0;
   if (staged) {
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
     const uint32_t dn = p.dir_bits ? (1u << p.dir_bits) + 1u : 0u;
@@ -448,11 +450,13 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   const uint64_t leaf_key0 = static_cast<uint64_t>(p.internal_nodes) * 16u;
   const uint64_t nk = p.n_intervals - 1;
 
-  const Seg seg = segment<false>(p);
+  const Seg seg = segment<MULTI>(p);
+  const uint64_t* xhi = p.xhi + seg.off;
+  const uint64_t* xlo = p.xlo + seg.off;
   uint64_t nx_hi = 0;
   {
     const uint64_t first = warp * 32 + lane;
-    if (first < seg.n) nx_hi = p.xhi[first];
+    if (first < seg.n) nx_hi = xhi[first];
   }
   for (uint64_t base = warp * 32; base < seg.n; base += nwarps * 32) {
     const uint64_t mine = base + lane;
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
     const uint64_t my_hi = nx_hi;
     {
       const uint64_t next = mine + nwarps * 32;
-      nx_hi = next < seg.n ? p.xhi[next] : 0ull;
+      nx_hi = next < seg.n ? xhi[next] : 0ull;
     }
     uint32_t cnt = 0;
     if (N && staged)
@@ -509,10 +513,10 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
     }
 #endif
     uint32_t w = __ldg(p.nh_tie + rank);
-    const uint64_t* lo_src = p.xlo + mine;
+    const uint64_t* lo_src = xlo + mine;
     w = settle_tie(p.nodes_hi + leaf_key0, p.nodes_lo + leaf_key0, nk, p.nh_tie, rank, w, my_hi,
                    [lo_src, ok] { return ok ? *lo_src : 0ull; });
-    if (ok) p.out[mine] = static_cast<uint16_t>(w);
+    if (ok) store_out<MULTI>(p, seg.off + mine, static_cast<uint16_t>(w));
   }
 }
 
@@ -575,15 +579,21 @@ KernelFn kernel_for(const DevTable& t, bool multi = false, bool lazy = false) {
   }
   static const KernelFn hyb_lazy[2][kMaxDepth + 1] = {PLANB_HYB_LAZY(false), PLANB_HYB_LAZY(true)};
 #undef PLANB_HYB_LAZY
-  // (reads an address's low half only to settle a tie, so it serves host-resident addresses too)
-  static const KernelFn hyb16[kMaxDepth + 1] = {
-      lookup_hybrid16<0>, lookup_hybrid16<1>, lookup_hybrid16<2>, lookup_hybrid16<3>,
-      lookup_hybrid16<4>, lookup_hybrid16<5>, lookup_hybrid16<6>, lookup_hybrid16<7>,
-      lookup_hybrid16<8>, lookup_hybrid16<9>, lookup_hybrid16<10>};
+  // [multi] (reads an address's low half only to settle a tie, so it serves host-resident
+  // addresses too)
+#define PLANB_HYB16(M)                                                                          \
+  {                                                                                               \
+    lookup_hybrid16<0, M>, lookup_hybrid16<1, M>, lookup_hybrid16<2, M>, lookup_hybrid16<3, M>,   \
+        lookup_hybrid16<4, M>, lookup_hybrid16<5, M>, lookup_hybrid16<6, M>,                      \
+        lookup_hybrid16<7, M>, lookup_hybrid16<8, M>, lookup_hybrid16<9, M>,                      \
+        lookup_hybrid16<10, M>                                                                    \
+  }
+  static const KernelFn hyb16[2][kMaxDepth + 1] = {PLANB_HYB16(false), PLANB_HYB16(true)};
+#undef PLANB_HYB16
   const uint32_t D = t.depth;
   if (D < 1 || D > static_cast<uint32_t>(kMaxDepth)) return nullptr;
   if (t.format == PLANB_FMT_F16HI && t.kernel == kHybrid)
-    return (!multi && t.smem_levels <= D) ? hyb16[D - t.smem_levels] : nullptr;
+    return t.smem_levels <= D ? hyb16[multi ? 1 : 0][D - t.smem_levels] : nullptr;
   if (t.format == PLANB_FMT_F16HI) return f16[D];
   const bool packed = t.format == PLANB_FMT_F8V7;
   if (t.kernel == kHybrid && multi)

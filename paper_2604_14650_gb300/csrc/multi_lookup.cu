@@ -16,9 +16,10 @@ namespace {
 // counter, so the CTAs running at one time work on a narrow window of the grouped batch and only
 // two or three tables are live in L2 at once. A CTA stages the top-of-tree index (high halves) and
 // radix directory of each table it meets in shared memory — keeping them while its next item is
-// in the same table — and runs the hybrid descent of lookup_hybrid: phase A over the index, then
+// in the same table; an index larger than the launch's share is searched in place in global
+// memory instead — and runs the hybrid descent of lookup_hybrid: phase A over the index, then
 // the table's remaining DB levels from L2 by 8-lane groups, writing each result at its bucketed
-// position. The tile code is instantiated per (DB, packed) and picked per table; depths beyond
+// position. The tile code is instantiated per (DB, format) and picked per table; depths beyond
 // kMultiMaxDb take a run-time level loop. Addresses with an id beyond the tables (after range[T])
 // are left to the gather that follows.
 constexpr int kMultiMaxDb = 4;
@@ -44,10 +45,13 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
     const bool ok = mine < s1;
     const uint64_t my_hi = ok ? xhi[mine] : 0ull;
     LazyLo my_lo(ok);   // read on a high-half tie only
-    const uint32_t cnt =
-        N ? index_count(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, sidx, my_hi, my_lo,
-                        xlo + mine)
-          : 0u;
+    uint32_t cnt = 0;
+    if (N && d.staged)
+      cnt = index_count(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, sidx, my_hi, my_lo,
+                        xlo + mine);
+    else if (N)
+      cnt = index_count_global(sidx, N, d.dir, d.dir_bits, d.dir_shift, d.dir_base, my_hi, my_lo,
+                               xlo + mine);
     uint32_t result = 0;
     if (db == 0) {
       uint32_t rank = cnt;
@@ -135,6 +139,88 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
   }
 }
 
+// The same for an F16HI table (the descent of lookup_hybrid16): every level counts high halves only,
+// and the next-hop word at the count says when settle_tie must finish it.
+template <int DB>   // DB < 0: run-time depth d.db
+__device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* Uh,
+                                           const uint16_t* Dir, uint64_t s0, uint64_t s1,
+                                           const uint64_t* __restrict__ xhi,
+                                           const uint64_t* __restrict__ xlo,
+                                           uint16_t* __restrict__ out, uint32_t* status) {
+  const ulonglong2* hi2 = static_cast<const ulonglong2*>(d.nodes);
+  const uint64_t leaf_key0 = static_cast<uint64_t>(d.internal_nodes) * 16u;
+  const uint64_t* keys_hi = static_cast<const uint64_t*>(d.nodes) + leaf_key0;
+  const uint64_t* keys_lo = d.nodes_lo + leaf_key0;
+  const uint32_t* words = reinterpret_cast<const uint32_t*>(d.values);
+  const uint64_t nk = d.n_intervals - 1;
+  const uint32_t N = d.sidx_n;
+  const uint32_t db = DB >= 0 ? static_cast<uint32_t>(DB) : d.db;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t g = lane >> 3;
+  const uint32_t j = lane & 7u;
+  const uint32_t gshift = g * 8u;
+  const uint32_t bsel = g | ((g + 4u) << 4) | (g << 8) | ((g + 4u) << 12);
+  const uint32_t wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint64_t base = s0 + static_cast<uint64_t>(wid) * 32u; base < s1; base += nw * 32u) {
+    const uint64_t mine = base + lane;
+    const bool ok = mine < s1;
+    const uint64_t my_hi = ok ? xhi[mine] : 0ull;
+    uint32_t cnt = 0;
+    if (N && d.staged)
+      cnt = index_count_hi(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, my_hi);
+    else if (N)
+      cnt = index_count_hi_global(reinterpret_cast<const ulonglong2*>(d.sidx), N, d.dir,
+                                  d.dir_bits, d.dir_shift, d.dir_base, my_hi);
+    uint64_t rank = cnt;
+    if (db > 0) {
+      uint32_t my_node = d.sidx_node + cnt;
+      uint32_t my_c = 0;
+#pragma unroll
+      for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
+        uint64_t qh[kRounds];
+        uint32_t nd[kRounds];
+#pragma unroll
+        for (int i = 0; i < kRounds; i++) {
+          const uint32_t src = gshift + r0 + i;
+          qh[i] = __shfl_sync(kFull, my_hi, src);
+          nd[i] = __shfl_sync(kFull, my_node, src);
+        }
+#pragma unroll
+        for (uint32_t l = 0; l < db; l++) {
+          ulonglong2 kh[kRounds];
+#pragma unroll
+          for (int i = 0; i < kRounds; i++)
+            kh[i] = __ldg(hi2 + static_cast<uint64_t>(nd[i]) * 8u + j);
+#pragma unroll
+          for (int i = 0; i < kRounds; i++) {
+            const uint32_t c = __popc(__byte_perm(__ballot_sync(kFull, kh[i].x < qh[i]),
+                                                  __ballot_sync(kFull, kh[i].y < qh[i]), bsel)) >>
+                               1;
+            if (l + 1 < db) {
+              nd[i] = nd[i] * 17u + 1u + c;
+            } else if (j == r0 + i) {
+              my_node = nd[i];
+              my_c = c;
+            }
+          }
+        }
+      }
+      rank = static_cast<uint64_t>(my_node - d.internal_nodes) * 16u + my_c;
+    }
+#ifdef PLANB_BOUNDS_CHECK
+    if (rank >= d.n_intervals) {
+      report(status, 4u);
+      rank = 0;
+    }
+#endif
+    uint32_t w = __ldg(words + rank);
+    const uint64_t* lo_src = xlo + mine;
+    w = settle_tie(keys_hi, keys_lo, nk, words, rank, w, my_hi,
+                   [lo_src, ok] { return ok ? *lo_src : 0ull; });
+    if (ok) out[mine] = static_cast<uint16_t>(w);
+  }
+}
+
 __global__ void __launch_bounds__(512, 2)
     lookup_multi_persistent(const MultiDesc* __restrict__ desc, uint32_t T,
                             const uint64_t* __restrict__ range, const uint64_t* __restrict__ xhi,
@@ -175,16 +261,27 @@ __global__ void __launch_bounds__(512, 2)
         __syncthreads();   // the previous table's readers are done with Uh and d
         if (threadIdx.x == 0) d = desc[t];
         __syncthreads();
-        const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
-        for (uint32_t i = threadIdx.x; i < d.sidx_n; i += blockDim.x) Uh[i] = __ldg(&sidx[i].x);
-        Dir = reinterpret_cast<uint16_t*>(Uh + ((d.sidx_n + 1u) & ~1u));
-        const uint32_t dn = d.dir_bits ? (1u << d.dir_bits) + 1u : 0u;
-        for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(d.dir + i);
+        if (d.staged) {
+          const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
+          for (uint32_t i = threadIdx.x; i < d.sidx_n; i += blockDim.x) Uh[i] = __ldg(&sidx[i].x);
+          Dir = reinterpret_cast<uint16_t*>(Uh + ((d.sidx_n + 1u) & ~1u));
+          const uint32_t dn = d.dir_bits ? (1u << d.dir_bits) + 1u : 0u;
+          for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(d.dir + i);
+        }
         __syncthreads();
         staged = t;
       }
       const uint32_t sel = d.db <= static_cast<uint32_t>(kMultiMaxDb) ? d.db : 15u;
-      if (d.packed) {
+      if (d.f16) {
+        switch (sel) {
+          case 0: multi_tiles16<0>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 1: multi_tiles16<1>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 2: multi_tiles16<2>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 3: multi_tiles16<3>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 4: multi_tiles16<4>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          default: multi_tiles16<-1>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+        }
+      } else if (d.packed) {
         switch (sel) {
           case 0: multi_tiles<0, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
           case 1: multi_tiles<1, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;

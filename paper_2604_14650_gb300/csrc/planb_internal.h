@@ -232,7 +232,8 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   void* stream, const uint64_t* d_range = nullptr,
                   const uint32_t* d_perm = nullptr, bool lazy_lo = false);
 
-// One table of the single-launch multi-table kernel (F8X128 or F8V7 tables of the hybrid kernel).
+// One table of the single-launch multi-table kernel (F8X128, F8V7 or F16HI tables of the hybrid
+// kernel).
 struct MultiDesc {
   const void* nodes;         // node array
   const uint64_t* sidx;      // top-of-tree index, (hi, lo) per entry
@@ -247,7 +248,12 @@ struct MultiDesc {
   const uint16_t* dir;
   uint64_t dir_base;
   uint32_t dir_shift;
+  uint32_t f16;              // F16HI: 17-ary nodes of high halves, low halves in nodes_lo, and
+                             // values holding u32 next-hop words (see nh_words)
+  uint32_t staged;           // 1: index and directory staged in shared memory; 0: searched in
+                             // place in global memory (an index larger than the launch's share)
   uint32_t pad;
+  const uint64_t* nodes_lo;  // F16HI low halves
 };
 
 // The single-launch multi-table kernel: raises its shared-memory limit to the device maximum and

@@ -16,11 +16,13 @@ def test_candidates_cover_formats_depths_and_launch_shapes():
 
 def test_persistent_candidates_stay_in_the_single_launch():
     c = candidates(depth=6, auto_levels=4, persistent=True)
-    assert c and all(x["kernel"] == "hybrid" and x["format"] in ("f8x128", "f8v7") for x in c)
+    assert c and all(x["kernel"] == "hybrid" for x in c)
+    assert {x["format"] for x in c} == {"f8x128", "f8v7", "f16hi"}
     assert all("block_threads" not in x for x in c)
     assert candidates(depth=3, auto_levels=0, persistent=True) == [
         dict(format="f8x128", kernel="hybrid", smem_levels=0),
-        dict(format="f8v7", kernel="hybrid", smem_levels=0)]
+        dict(format="f8v7", kernel="hybrid", smem_levels=0),
+        dict(format="f16hi", kernel="hybrid", smem_levels=-1)]
 
 
 def test_size_classes_are_half_octaves():

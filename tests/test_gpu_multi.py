@@ -55,20 +55,20 @@ def expected(fibs, tid, xh, xl):
 
 @pytest.mark.parametrize("per_table", [False, True])
 @pytest.mark.parametrize("graph", [False, True])
-@pytest.mark.parametrize("kinds", [("f8x128", "hybrid"), ("f8v7", "hybrid"), ("mixed_hybrid", None),
-                                   ("mixed", None)])
+@pytest.mark.parametrize("kinds", [("f8x128", "hybrid"), ("f8v7", "hybrid"), ("f16hi", "hybrid"),
+                                   ("mixed_hybrid", None), ("mixed", None)])
 def test_multi_table_parity_and_replay(kinds, graph, per_table):
     sizes = [500, 3000, 20_000, 1000, 60_000, 7, 12_000, 2500]
     fibs_in, tid, xh, xl = workload(sizes, 600_000, seed=41)
     want = expected(fibs_in, tid, xh, xl)
-    choices = [("f8x128", "hybrid"), ("f8v7", "hybrid"), ("f8x128", "coop"), ("f8x128", "flat"),
-               ("f16hi", "coop")]
+    choices = [("f8x128", "hybrid"), ("f8v7", "hybrid"), ("f16hi", "hybrid"), ("f8x128", "coop"),
+               ("f8x128", "flat"), ("f16hi", "coop")]
     fibs = []
     for t, f in enumerate(fibs_in):
         if kinds[0] == "mixed":
             fmt, ker = choices[t % len(choices)]
-        elif kinds[0] == "mixed_hybrid":          # both hybrid formats, several index depths
-            fmt, ker = choices[t % 2]
+        elif kinds[0] == "mixed_hybrid":          # every hybrid format, several index depths
+            fmt, ker = choices[t % 3]
         else:
             fmt, ker = kinds
         smem = {2: 0, 5: 1}.get(t, -1) if kinds[0] == "mixed_hybrid" else -1
@@ -93,11 +93,12 @@ def test_multi_table_parity_and_replay(kinds, graph, per_table):
         f.close()
 
 
+@pytest.mark.parametrize("fmt", ["f8x128", "f16hi"])
 @pytest.mark.parametrize("per_table", [False, True])
-def test_multi_table_sees_updates(per_table):
+def test_multi_table_sees_updates(per_table, fmt):
     sizes = [5000, 20_000, 800]
     fibs_in, tid, xh, xl = workload(sizes, 300_000, seed=51)
-    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh) for f in fibs_in]
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) for f in fibs_in]
     with pb.MultiFib(fibs, max_batch=300_000, per_table=per_table) as mt:
         dh, dl, dt = dev(xh), dev(xl), dev(tid, np.uint8)
         out = mt.lookup(dh, dl, dt)
@@ -147,7 +148,7 @@ def test_multi_table_sees_updates(per_table):
         f.close()
 
 
-@pytest.mark.parametrize("fmt,kernel", [("f8x128", "learned"), ("f16hi", "hybrid")])
+@pytest.mark.parametrize("fmt,kernel", [("f8x128", "learned"), ("f8v7", "learned")])
 def test_tables_without_a_multi_form_cannot_join(fmt, kernel):
     f = synth.gen_fib(2000, seed=3)
     with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel) as fib:
@@ -155,12 +156,13 @@ def test_tables_without_a_multi_form_cannot_join(fmt, kernel):
             pb.MultiFib([fib], max_batch=1000)
 
 
+@pytest.mark.parametrize("fmt", ["f8x128", "f16hi"])
 @pytest.mark.parametrize("n", [1, 31, 33, 1000])
-def test_multi_table_tiny_batches(n):
+def test_multi_table_tiny_batches(n, fmt):
     """Batches smaller than the persistent grid: most CTAs get no addresses."""
     sizes = [3000, 40_000, 100]
     fibs_in, tid, xh, xl = workload(sizes, n, seed=61)
-    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh) for f in fibs_in]
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) for f in fibs_in]
     with pb.MultiFib(fibs, max_batch=4096) as mt:
         out = mt.lookup(dev(xh), dev(xl), dev(tid, np.uint8))
         torch.cuda.synchronize()
@@ -179,13 +181,30 @@ def test_autotuned_group_is_exact_and_persistent(tmp_path):
     for t, f in enumerate(fibs_in):
         sel = tid == t
         opts = tuner.best(f.hi, f.lo, f.len, f.nh, dev(xh[sel]), dev(xl[sel]))
-        assert opts["kernel"] == "hybrid" and opts["format"] in ("f8x128", "f8v7")
+        assert opts["kernel"] == "hybrid" and opts["format"] in ("f8x128", "f8v7", "f16hi")
         fibs.append(pb.Fib(f.hi, f.lo, f.len, f.nh, **opts))
     # a second tuner on the same cache answers from it
     again = Autotuner(cache_path=str(tmp_path / "tune.json"), persistent=True)
     assert again.best(fibs_in[1].hi, fibs_in[1].lo, fibs_in[1].len, fibs_in[1].nh, None, None) == \
         tuner.best(fibs_in[1].hi, fibs_in[1].lo, fibs_in[1].len, fibs_in[1].nh, None, None)
     with pb.MultiFib(fibs, max_batch=200_000) as mt:
+        out = mt.lookup(dev(xh), dev(xl), dev(tid, np.uint8))
+        torch.cuda.synchronize()
+        assert mt.persistent
+        assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
+    for f in fibs:
+        f.close()
+
+
+def test_large_index_is_searched_in_place():
+    """An F16HI table built for the single-table kernel (index over its leaves, about 160 KB of
+    shared memory) joins the single persistent launch beside small tables: its index is searched in
+    place in global memory rather than staged, and every result stays exact."""
+    sizes = [160_000, 2000, 30_000]
+    fibs_in, tid, xh, xl = workload(sizes, 400_000, seed=81)
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format="f16hi") for f in fibs_in]
+    assert fibs[0].stats()["smem_bytes"] > 96 * 1024 > fibs[1].stats()["smem_bytes"]
+    with pb.MultiFib(fibs, max_batch=400_000) as mt:
         out = mt.lookup(dev(xh), dev(xl), dev(tid, np.uint8))
         torch.cuda.synchronize()
         assert mt.persistent

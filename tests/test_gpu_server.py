@@ -25,10 +25,11 @@ def built():
     pb.build()
 
 
-def test_requests_in_the_mix_equal_alone():
+@pytest.mark.parametrize("fmt", ["f8x128", "f16hi"])
+def test_requests_in_the_mix_equal_alone(fmt):
     sizes = [3000, 40_000, 700, 12_000, 90_000, 5000]
     fibs_in = [synth.gen_fib(s, seed=600 + t, nh_max=4095) for t, s in enumerate(sizes)]
-    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh) for f in fibs_in]
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) for f in fibs_in]
     rng = np.random.default_rng(7)
     reqs = []
     for i in range(240):
@@ -78,10 +79,12 @@ def test_admission_by_memory_budget():
             assert srv.stats()["tables"] == 1
 
 
-def test_updates_while_serving_are_seen():
+@pytest.mark.parametrize("fmt", ["f8x128", "f16hi"])
+def test_updates_while_serving_are_seen(fmt):
     f = synth.gen_fib(30_000, seed=77, nh_max=4095)
     xh, xl = synth.gen_trace(f, 20_000, seed=78)
-    with pb.Fib(f.hi, f.lo, f.len, f.nh) as fib, pb.Server(slots=2, update_period_us=2000) as srv:
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) as fib, \
+            pb.Server(slots=2, update_period_us=2000) as srv:
         t = srv.add_table(fib)
         out = np.zeros(xh.size, np.uint16)
         srv.wait(srv.submit(t, xh, xl, out), WAIT_US)
