@@ -485,7 +485,7 @@ def run_planb(args):
     kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
     # the kernel's name as ncu prints it
     if kname == "hybrid" and args.format == "f16hi":
-        kernel = f"lookup_hybrid16<{st['depth'] - st['smem_levels']}>"
+        kernel = f"lookup_hybrid16<{st['depth'] - st['smem_levels']}, 0>"
     elif kname == "hybrid":
         kernel = (f"lookup_hybrid<{st['depth'] - st['smem_levels']}, "
                   f"{1 if args.format == 'f8v7' else 0}, 0, 0, 0>")

@@ -475,23 +475,27 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
     if constexpr (DB > 0) {
       uint32_t my_node = p.sidx_node + cnt;
       uint32_t my_c = 0;
+      // all eight addresses of a group in flight when only the leaf level is left; deeper
+      // descents carry node indexes across levels and take four at a time (register budget)
+      constexpr uint32_t R = DB == 1 ? 8u : static_cast<uint32_t>(kRounds);
 #pragma unroll
-      for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
-        uint64_t qh[kRounds];
-        uint32_t nd[kRounds];
+      for (uint32_t r0 = 0; r0 < 8; r0 += R) {
+        uint64_t qh[R];
+        uint32_t nd[R];
 #pragma unroll
-        for (int i = 0; i < kRounds; i++) {
+        for (int i = 0; i < static_cast<int>(R); i++) {
           const uint32_t src = gshift + r0 + i;
           qh[i] = __shfl_sync(kFull, my_hi, src);
           nd[i] = __shfl_sync(kFull, my_node, src);
         }
 #pragma unroll
         for (int l = 0; l < DB; l++) {
-          ulonglong2 kh[kRounds];
+          ulonglong2 kh[R];
 #pragma unroll
-          for (int i = 0; i < kRounds; i++) kh[i] = __ldg(hi2 + static_cast<uint64_t>(nd[i]) * 8u + j);
+          for (int i = 0; i < static_cast<int>(R); i++)
+            kh[i] = __ldg(hi2 + static_cast<uint64_t>(nd[i]) * 8u + j);
 #pragma unroll
-          for (int i = 0; i < kRounds; i++) {
+          for (int i = 0; i < static_cast<int>(R); i++) {
             const uint32_t c = __popc(__byte_perm(__ballot_sync(kFull, kh[i].x < qh[i]),
                                                   __ballot_sync(kFull, kh[i].y < qh[i]), bsel)) >>
                                1;
