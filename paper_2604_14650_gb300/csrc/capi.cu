@@ -1107,6 +1107,7 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess)
       return PLANB_ECUDA;
+    if (int rc = planb::bucketing_setup()) return rc;
     // bucketing chunks: eight per SM for large batches, but no more than one 2,048-address tile
     // each at max_batch, so a group sized for small batches (a serving slot) launches few blocks
     const size_t by_batch = (max_batch + 2047) / 2048;

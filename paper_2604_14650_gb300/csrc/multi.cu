@@ -104,15 +104,35 @@ __global__ void mt_tablescan_kernel(const uint64_t* __restrict__ totals, uint32_
   }
 }
 
+// Asynchronous global-to-shared copies (cp.async): a tile's address halves land in shared memory
+// without passing through registers, one tile ahead of their use.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // The scatter works through its chunk in tiles of kTile addresses: the tile is ranked per table
-// in shared memory (lanes with the same table are grouped by a warp match, so one shared atomic
-// serves the group), staged in table order, and written out as one contiguous run per table, so
-// the global writes are coalesced; each address's bucketed position goes to where[i] in input
-// order. Positions within one table's run follow the atomics' order, not the input order: the
-// recorded positions make the order immaterial.
+// in shared memory (one shared atomic per address: lanes of a warp that hit one table's counter are
+// serialised by the hardware, cheaper than grouping them first with a warp match), staged in table
+// order, and written out as one contiguous run per table, so the global writes are coalesced; each
+// address's bucketed position goes to where[i] in input order. Positions within one table's run
+// follow the atomics' order, not the input order: the recorded positions make the order
+// immaterial. The tile's high and low halves are copied into
+// shared memory one tile ahead (double-buffered cp.async) and its table ids read into registers
+// one tile ahead, so the ranking of a tile overlaps the loads of the next; staging records for
+// each slot which input address fills it, and the write reads the halves from there.
 constexpr int kScatterThreads = 256;
 constexpr int kScatterItems = 8;
 constexpr int kTile = kScatterThreads * kScatterItems;
+constexpr size_t kScatterSmem =
+    2 * 2 * kTile * sizeof(uint64_t) + kTile * sizeof(uint16_t) + kTile * sizeof(uint8_t);
 
 __global__ void __launch_bounds__(kScatterThreads)
     mt_scatter_kernel(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo,
@@ -124,41 +144,58 @@ __global__ void __launch_bounds__(kScatterThreads)
   typedef cub::BlockScan<uint32_t, kScatterThreads> Scan;
   __shared__ typename Scan::TempStorage scan_tmp;
   __shared__ uint32_t cur[256], cnt[256], base[256];
-  __shared__ uint64_t s_hi[kTile], s_lo[kTile];
-  __shared__ uint8_t s_t[kTile];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* s_in = reinterpret_cast<uint64_t*>(smem_raw);   // [buffer][high, low][kTile]
+  uint16_t* s_src = reinterpret_cast<uint16_t*>(s_in + 4 * kTile);   // input index per slot
+  uint8_t* s_t = reinterpret_cast<uint8_t*>(s_src + kTile);           // table per slot
   batch_shape(d_n, n, chunk);
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t lt_mask = (1u << lane) - 1u;
   for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x)
     cur[t] = static_cast<uint32_t>(range[t]) + offsets[t * gridDim.x + blockIdx.x];
   const uint64_t b0 = static_cast<uint64_t>(blockIdx.x) * chunk;
   const uint64_t b1 = b0 + chunk < n ? b0 + chunk : n;
   const uint64_t tiles_per_chunk = (chunk + kTile - 1) / kTile;
   uint64_t tile = static_cast<uint64_t>(blockIdx.x) * tiles_per_chunk;
-  for (uint64_t tb = b0; tb < b1; tb += kTile, tile++) {
-    for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) cnt[t] = 0;
-    __syncthreads();
-    uint32_t tt[kScatterItems], rank[kScatterItems];
-    uint64_t vh[kScatterItems], vl[kScatterItems];
+  // copies of tile [tb, tb + kTile) into buffer b; every thread commits one group per call
+  auto issue = [&](uint64_t tb, uint32_t b) {
+    if (tb < b1) {
+      const uint64_t m = b1 - tb < static_cast<uint64_t>(kTile) ? b1 - tb : kTile;
+      uint64_t* dh = s_in + (2u * b) * kTile;
+      uint64_t* dl = dh + kTile;
+      for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+        cp_async8(dh + k, hi + tb + k);
+        cp_async8(dl + k, lo + tb + k);
+      }
+    }
+    cp_async_commit();
+  };
+  // table ids of tile tb (0xFFFF: no address, a group of its own that takes no slot)
+  auto ids = [&](uint64_t tb, uint32_t (&out)[kScatterItems]) {
 #pragma unroll
     for (int k = 0; k < kScatterItems; k++) {
       const uint64_t e = tb + static_cast<uint64_t>(k) * kScatterThreads + threadIdx.x;
-      const bool ok = e < b1;
-      uint32_t t = 0xFFFFu;   // no address: a group of its own that takes no slot
-      if (ok) {
+      uint32_t t = 0xFFFFu;
+      if (e < b1) {
         const uint32_t t0 = tid[e];
         t = t0 < T ? t0 : T;
-        vh[k] = hi[e];
-        vl[k] = lo[e];
       }
-      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, t);
-      const uint32_t leader = __ffs(peers) - 1u;
-      uint32_t first = 0;
-      if (ok && lane == leader) first = atomicAdd(&cnt[t], __popc(peers));
-      first = __shfl_sync(0xFFFFFFFFu, first, leader);
-      tt[k] = t;
-      rank[k] = first + __popc(peers & lt_mask);
+      out[k] = t;
     }
+  };
+  uint32_t tn[kScatterItems];
+  issue(b0, 0);
+  ids(b0, tn);
+  uint32_t buf = 0;
+  for (uint64_t tb = b0; tb < b1; tb += kTile, tile++, buf ^= 1u) {
+    uint32_t tt[kScatterItems], rank[kScatterItems];
+#pragma unroll
+    for (int k = 0; k < kScatterItems; k++) tt[k] = tn[k];
+    issue(tb + kTile, buf ^ 1u);   // its buffer's last readers passed the previous tile's barrier
+    ids(tb + kTile, tn);
+    for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) cnt[t] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScatterItems; k++)
+      rank[k] = tt[k] != 0xFFFFu ? atomicAdd(&cnt[tt[k]], 1u) : 0u;
     __syncthreads();
     {
       uint32_t v = threadIdx.x <= T ? cnt[threadIdx.x] : 0u, excl = 0;
@@ -173,28 +210,31 @@ __global__ void __launch_bounds__(kScatterThreads)
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kScatterItems; k++) {
-      const uint64_t e = tb + static_cast<uint64_t>(k) * kScatterThreads + threadIdx.x;
-      if (e < b1) {
-        const uint32_t t = tt[k];
-        const uint32_t slot = base[t] + rank[k];
-        s_hi[slot] = vh[k];
-        s_lo[slot] = vl[k];
-        s_t[slot] = static_cast<uint8_t>(t);
-        where[e] = static_cast<uint16_t>(slot);
+      const uint32_t local = static_cast<uint32_t>(k) * kScatterThreads + threadIdx.x;
+      if (tt[k] != 0xFFFFu) {
+        const uint32_t slot = base[tt[k]] + rank[k];
+        s_src[slot] = static_cast<uint16_t>(local);
+        s_t[slot] = static_cast<uint8_t>(tt[k]);
+        where[tb + local] = static_cast<uint16_t>(slot);
       }
     }
+    cp_async_wait<1>();   // this tile's copies (all groups but the newest) have landed
     __syncthreads();
     const uint32_t m = static_cast<uint32_t>(b1 - tb < kTile ? b1 - tb : kTile);
+    const uint64_t* sh = s_in + (2u * buf) * kTile;
+    const uint64_t* sl = sh + kTile;
     for (uint32_t slot = threadIdx.x; slot < m; slot += blockDim.x) {
       const uint32_t t = s_t[slot];
       const uint32_t pos = cur[t] + (slot - base[t]);
-      bhi[pos] = s_hi[slot];
-      blo[pos] = s_lo[slot];
+      const uint32_t src = s_src[slot];
+      bhi[pos] = sh[src];
+      blo[pos] = sl[src];
     }
     __syncthreads();
     for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) cur[t] += cnt[t];
     // the next tile's first barrier orders these updates before their next use
   }
+  cp_async_wait<0>();
 }
 
 // The gather, tile by tile in the scatter's decomposition: a tile's results are its tables' runs
@@ -249,6 +289,14 @@ __global__ void __launch_bounds__(kGatherThreads)
 
 }  // namespace
 
+int bucketing_setup() {
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(mt_scatter_kernel),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kScatterSmem)) == cudaSuccess
+             ? PLANB_OK
+             : PLANB_ECUDA;
+}
+
 size_t bucketing_tiles(size_t cap, uint32_t G) {
   const size_t chunk = cap ? (cap + G - 1) / G : 1;
   return static_cast<size_t>(G) * ((chunk + kTile - 1) / kTile);
@@ -269,9 +317,9 @@ int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* 
   mt_rowscan_kernel<<<T + 1, kScanThreads, 0, st>>>(d_counts, G, totals);
   mt_tablescan_kernel<<<1, 256, 0, st>>>(
       totals, T, d_range, reinterpret_cast<unsigned long long*>(d_range + 2 * T + 3));
-  mt_scatter_kernel<<<G, kScatterThreads, 0, st>>>(d_hi, d_lo, d_tid, n, T, chunk, d_counts,
-                                                    d_range, d_bhi, d_blo, d_where, d_tile_start,
-                                                    d_tile_base, d_n);
+  mt_scatter_kernel<<<G, kScatterThreads, kScatterSmem, st>>>(
+      d_hi, d_lo, d_tid, n, T, chunk, d_counts, d_range, d_bhi, d_blo, d_where, d_tile_start,
+      d_tile_base, d_n);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

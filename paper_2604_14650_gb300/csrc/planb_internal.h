@@ -280,6 +280,9 @@ int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t*
 // (T+1) entries. n < 2^32. With d_n the kernels read the batch size from device memory (n then
 // only bounds it).
 size_t bucketing_tiles(size_t cap, uint32_t G);
+// Raises the scatter kernel's dynamic shared-memory limit (once per device, before any launch or
+// capture of launch_bucketing).
+int bucketing_setup();
 int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
                      uint32_t T, uint32_t G, uint32_t* d_counts, uint64_t* d_range,
                      uint64_t* d_bhi, uint64_t* d_blo, uint16_t* d_where,
