@@ -25,17 +25,28 @@ def size_class(n_intervals: int) -> float:
     return round(math.log2(max(int(n_intervals), 2)) * 2) / 2
 
 
-def candidates(depth: int, auto_levels: int, persistent: bool = False) -> list[dict]:
-    """Candidate option sets around the library's automatic choice. persistent=True keeps to the
-    configurations a multi-table group can run in its single persistent launch (the hybrid kernel
-    in any format; that launch fixes threads and CTAs per SM, so only the format and the index
-    depth vary; F16HI tables keep their automatic depth)."""
+# Index (+ directory) bytes a multi-table group's persistent launch stages per CTA; a larger index
+# is searched in place there, which is slower than staging a shallower one.
+PERSISTENT_STAGE_BYTES = 96 * 1024
+
+
+def candidates(depth: int, auto_levels: int, persistent: bool = False,
+               auto16: int | None = None) -> list[dict]:
+    """Candidate option sets around the library's automatic choice (depth and auto_levels of the
+    F8X128 layout; auto16 the F16HI layout's automatic index depth, when known). persistent=True
+    keeps to the configurations a multi-table group can run in its single persistent launch (the
+    hybrid kernel in any format; that launch fixes threads and CTAs per SM, so only the format and
+    the index depth vary)."""
     out = []
     if persistent:
         for fmt in ("f8x128", "f8v7"):
             for s in sorted({auto_levels, max(auto_levels - 1, 0)}):
                 out.append(dict(format=fmt, kernel="hybrid", smem_levels=s))
-        out.append(dict(format="f16hi", kernel="hybrid", smem_levels=-1))
+        if auto16 is None:
+            out.append(dict(format="f16hi", kernel="hybrid", smem_levels=-1))
+        else:
+            for s in sorted({auto16, max(auto16 - 1, 0)}):
+                out.append(dict(format="f16hi", kernel="hybrid", smem_levels=s))
         return out
     for fmt in ("f8x128", "f8v7"):
         for s in sorted({auto_levels, max(auto_levels - 1, 0)}):
@@ -92,10 +103,17 @@ class Autotuner:
         out = torch.empty(sample_hi.numel(), dtype=torch.int16, device=sample_hi.device)
         with Fib(hi, lo, ln, nh, device=device) as probe:
             st = probe.stats()
+        auto16 = None
+        if self.persistent:
+            with Fib(hi, lo, ln, nh, format="f16hi", kernel="hybrid", device=device) as p16:
+                auto16 = p16.stats()["smem_levels"]
         results = []
-        for opts in candidates(st["depth"], st["smem_levels"], self.persistent):
+        for opts in candidates(st["depth"], st["smem_levels"], self.persistent, auto16):
             try:
                 with Fib(hi, lo, ln, nh, device=device, **opts) as fib:
+                    # the persistent launch would search a larger index in place: leave it out
+                    if self.persistent and fib.stats()["smem_bytes"] > PERSISTENT_STAGE_BYTES:
+                        continue
                     t = self._time(fib, sample_hi, sample_lo, out)
             except Exception:           # a configuration the table cannot take (e.g. no room)
                 continue

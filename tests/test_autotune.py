@@ -23,6 +23,10 @@ def test_persistent_candidates_stay_in_the_single_launch():
         dict(format="f8x128", kernel="hybrid", smem_levels=0),
         dict(format="f8v7", kernel="hybrid", smem_levels=0),
         dict(format="f16hi", kernel="hybrid", smem_levels=-1)]
+    # with the F16HI layout's automatic depth known, that depth and one shallower
+    c16 = [x for x in candidates(depth=6, auto_levels=4, persistent=True, auto16=4)
+           if x["format"] == "f16hi"]
+    assert [x["smem_levels"] for x in c16] == [3, 4]
 
 
 def test_size_classes_are_half_octaves():
