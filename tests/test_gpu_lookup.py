@@ -259,6 +259,23 @@ def test_f16hi_next_hop_words(kernel, builder):
         assert np.array_equal(img[-4 * m:].view(np.uint32), want)
 
 
+def test_f16hi_without_long_prefixes_sets_no_flag():
+    """With no prefix longer than /64 every boundary has an all-ones low half below it, no
+    next-hop word carries the flag, and the high-half-only lookup (the paper's 64-bit key scheme)
+    is the whole lookup: still equal to the oracle, at every boundary and its neighbours."""
+    f = synth.gen_fib(30_000, seed=941, nh_max=4095)
+    keep = f.len <= 64
+    g = synth.Fib(f.hi[keep], f.lo[keep], f.len[keep], f.nh[keep], 0)
+    m = pb.intervals(g.hi, g.lo, g.len, g.nh)[0].size
+    bh, bl = boundary_probes(g)
+    xh, xl = synth.gen_trace(g, 200_000, seed=942)
+    xh, xl = np.concatenate([bh, xh]), np.concatenate([bl, xl])
+    for kernel in ("hybrid", "coop"):
+        with pb.Fib(g.hi, g.lo, g.len, g.nh, format="f16hi", kernel=kernel) as fib:
+            assert not np.any(fib.table_dump()[-4 * m:].view(np.uint32) >> 16)
+            assert np.array_equal(gpu_lookup(fib, xh, xl), expected(g, xh, xl))
+
+
 @pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
 def test_long_runs_of_shared_high_halves(variant):
     """One /64 holding 3,000 /128 routes and nested /80../127 prefixes (thousands of keys with one
