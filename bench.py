@@ -426,7 +426,23 @@ def run_planb(args):
         stream.synchronize()
         us = sorted(1e3 * a.elapsed_time(b) for a, b in evs)
         lat = {"batch": bs, "batches": nb, "p50_us": us[len(us) // 2],
-               "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))], "max_us": us[-1]}
+               "p99_us": us[min(len(us) - 1, int(0.99 * len(us)))], "max_us": us[-1],
+               "what": "each launch event-timed as the host submits it: the interval holds the "
+                       "host's submission of the launch (the GPU waits for it) and the kernel"}
+        # the same batches queued behind ~36 ms of earlier lookups, so that the GPU runs them back
+        # to back and each interval holds the kernel alone
+        for _ in range(10):
+            fib.lookup_ptr(hp, lp, n, op, stream)
+        for i in range(nb):
+            off = (i * bs) % max(n - bs, 1)
+            a, b = evs[i]
+            a.record(stream)
+            fib.lookup_ptr(hp + 8 * off, lp + 8 * off, bs, op + 2 * off, stream)
+            b.record(stream)
+        stream.synchronize()
+        qs = sorted(1e3 * a.elapsed_time(b) for a, b in evs)
+        lat["queued"] = {"p50_us": qs[len(qs) // 2],
+                         "p99_us": qs[min(len(qs) - 1, int(0.99 * len(qs)))], "max_us": qs[-1]}
 
     # ablation (the GPU analogue of the paper's Section 4.5 study): every lookup kernel on the same
     # device-resident addresses
