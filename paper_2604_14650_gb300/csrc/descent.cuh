@@ -114,9 +114,7 @@ __device__ __forceinline__ uint32_t index_count_hi(const uint64_t* Uh, uint32_t 
 }
 
 // The same count read in place from the global index (entries of 16 bytes, high half first) and
-// directory, for launches too small to repay staging. Every read here is a dependent trip to L2,
-// so the first four entries of the bucket (most buckets hold fewer) are read at once and counted
-// directly; only a longer bucket continues with the halving search over the rest.
+// directory, for launches too small to repay staging.
 __device__ __forceinline__ uint32_t index_count_hi_global(const ulonglong2* sidx, uint32_t N,
                                                           const uint16_t* dir, uint32_t dir_bits,
                                                           uint32_t dir_shift, uint64_t dir_base,
@@ -131,18 +129,6 @@ __device__ __forceinline__ uint32_t index_count_hi_global(const ulonglong2* sidx
     n = __ldg(dir + bk + 1) - lo;
   }
   if (!n) return lo;
-  {
-    constexpr uint32_t kFirst = 4;
-    uint64_t e[kFirst];
-#pragma unroll
-    for (uint32_t k = 0; k < kFirst; k++) e[k] = k < n ? __ldg(&sidx[lo + k].x) : ~0ull;
-    uint32_t c = 0;
-#pragma unroll
-    for (uint32_t k = 0; k < kFirst; k++) c += e[k] < my_hi ? 1u : 0u;
-    if (c < kFirst || n <= kFirst) return lo + c;
-    lo += kFirst;   // every one of the first four is below: search the rest
-    n -= kFirst;
-  }
   uint32_t b = lo;
   while (n > 1) {
     const uint32_t half = n >> 1;
