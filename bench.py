@@ -266,7 +266,7 @@ def run_reference(args):
     import oracle
     import synth
     fib = synth.gen_fib(args.prefixes, seed=args.seed, nh_max=4095)
-    sample = 1 << 22
+    sample = min(1 << 22, args.lookups)   # a bounded sample of the workload's trace per step
     xh, xl = synth.gen_trace(fib, sample, seed=args.seed + 1)
     trie = oracle.Trie(fib.hi, fib.lo, fib.len, fib.nh)
     threads = os.cpu_count() or 1
