@@ -97,7 +97,8 @@ typedef struct planb_fib planb_fib; /* opaque; owns all host and device memory o
 
 typedef struct {
     uint32_t struct_size;   /* sizeof(planb_opts); lets the library accept older callers        */
-    int32_t format;         /* PLANB_FMT_*; default PLANB_FMT_F8X128                            */
+    int32_t format;         /* PLANB_FMT_*; default PLANB_FMT_F8X128 (every kernel takes it);
+                               PLANB_FMT_F16HI with the hybrid kernel is the fastest lookup     */
     int32_t merge_equal_nh; /* 1: merge neighbouring intervals with equal next hops (Section 3
                                intro allows compressing routes that share a next hop); results
                                are unchanged. Default 0.                                        */
