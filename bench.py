@@ -610,7 +610,7 @@ def run_vrf64(args):
     d_t = torch.from_numpy(tid).cuda()
     d_out = torch.empty(n, dtype=torch.int16, device="cuda")
     # tuned within the configurations the single persistent launch runs
-    tuner = Autotuner(cache_path=os.path.join(ROOT, "gpurun_out", "autotune.json"), persistent=True)
+    tuner = Autotuner(persistent=True)   # cache: the library's default location
     choices, fibs = [], []
     t0 = time.perf_counter()
     for t, f in enumerate(fibs_in):

@@ -535,14 +535,15 @@ int planb_debug_kernel_info(const planb_fib *fib, int multi, int *out6);
  * library holds it until the process exits. The call allocates nothing: no cudaMalloc, no
  * cudaFree, no allocating library routine. Its first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.
+ * any stream capture. The address is kept per device for the rest of the process, which assumes
+ * the device's primary context lives as long: do not call this after a cudaDeviceReset.
  *   addr_hi, addr_lo: host arrays of n uint64_t; out: host array of n uint16_t. The call copies
  *   them in, runs the lookup kernel and copies the results out on `stream`, and returns after the
  *   stream has finished them (synchronous). Pinned host buffers copy fastest.
  *   The array keeps the previous call's contents; nothing in it needs to start at zero, since each
  *   call writes the n entries it reads. Calls from any thread share the one array, so two calls
  *   that overlapped on the GPU would race on it: the library serialises them with a process-wide
- *   lock held until the call's copies are done.
+ *   lock held until the call's copies and kernel are done, on success and on every failure.
  * Errors: PLANB_EINVAL (null pointer with n > 0, n > PLANB_NOALLOC_MAX_KEYS), PLANB_ECUDA.
  */
 #define PLANB_NOALLOC_MAX_KEYS 262144

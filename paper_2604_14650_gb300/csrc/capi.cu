@@ -1418,12 +1418,15 @@ extern "C" int planb_lookup_host_noalloc(const planb_fib* fib_c, const uint64_t*
   uint64_t* dl = dh + kNoAllocMaxKeys;
   uint16_t* dout = reinterpret_cast<uint16_t*>(dl + kNoAllocMaxKeys);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // Once the first copy is queued, every return drains the stream first, so the lock is never
+  // released while this call's copies or kernel may still touch the shared array.
+  rc = PLANB_OK;
   if (cudaMemcpyAsync(dh, addr_hi, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(dl, addr_lo, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return PLANB_ECUDA;
-  rc = planb::launch_lookup(t->dt, t->cfg, dh, dl, n, dout, f->d_status, stream);
-  if (rc) return rc;
-  if (cudaMemcpyAsync(out, dout, n * 2, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return PLANB_ECUDA;
-  return cudaStreamSynchronize(st) == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+    rc = PLANB_ECUDA;
+  if (!rc) rc = planb::launch_lookup(t->dt, t->cfg, dh, dl, n, dout, f->d_status, stream);
+  if (!rc && cudaMemcpyAsync(out, dout, n * 2, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    rc = PLANB_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = PLANB_ECUDA;
+  return rc;
 }

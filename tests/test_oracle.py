@@ -288,3 +288,22 @@ def test_o3_chain_partition_from_ipaddress():
     k = len(bad) // 2
     bad[k] = (bad[k][0], (bad[k][1] + 1) % 65536)
     assert check(pfx, bad) is not None
+
+
+def test_o3_interval_count_bound_counts_distinct_prefixes():
+    """Section 3.1: N prefixes give at most 2N+1 elementary intervals. N disjoint, non-adjacent
+    prefixes with no default reach the bound exactly (each adds its start and its end), which O3
+    accepts; an array one entry longer fails on the bound itself, and N counts distinct
+    (prefix, length) pairs, so repeating a prefix in the input does not loosen it."""
+    A = 0x2001_0DB8 << 96
+    pfx = [(A + (2 * j) * (1 << 96), 32, 10 + j) for j in range(3)]
+    tight = [(0, 0)]
+    for p, L, h in pfx:
+        tight += [(p, h), (p + (1 << (128 - L)), 0)]
+    assert len(tight) == 2 * len(pfx) + 1
+    assert check(pfx, tight) is None
+    over = tight + [(ALL128 - 5, 0)]
+    msg = check(pfx, over)
+    assert msg is not None and msg.startswith("more than 2N+1 intervals")
+    msg = check(pfx + [pfx[0], pfx[1]], over)          # five input rows, still N = 3
+    assert msg is not None and msg.startswith("more than 2N+1 intervals")
