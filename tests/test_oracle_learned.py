@@ -73,3 +73,102 @@ def test_adam_matches_closed_form_first_step():
     g = np.array([0.5, -2.0, 1e-3])
     th, m, v = L.adam_step(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.1, eps=0.0)
     assert np.allclose(th, -0.1 * np.sign(g))
+
+
+def test_two_float_input_is_the_sum():
+    """A float64 input split into a float32 and the float32 rest gives the same network output and
+    gradient as the input itself (to float64 rounding): the split carries the value."""
+    rng = np.random.default_rng(11)
+    H = 16
+    theta = rng.normal(size=3 * H + 1)
+    cap = rng.random(H) + 0.05
+    x = rng.random(300)
+    hi = x.astype(np.float32).astype(np.float64)
+    lo = (x - hi).astype(np.float32).astype(np.float64)
+    assert np.all(hi + lo == x) or np.max(np.abs(hi + lo - x)) < 1e-15
+    t = np.sort(rng.random(300))
+    assert np.allclose(L.forward(theta, hi, H, cap, ulo=lo), L.forward(theta, x, H, cap),
+                       rtol=0, atol=1e-13)
+    l1, g1 = L.grad(theta, hi, t, H, cap, ulo=lo)
+    l0, g0 = L.grad(theta, x, t, H, cap)
+    assert abs(l1 - l0) < 1e-13 and np.max(np.abs(g1 - g0)) < 1e-12
+    # the low part matters: dropping it changes the output where the input is steep
+    assert np.max(np.abs(lo)) > 0
+
+
+def test_two_float_gradient_matches_central_differences():
+    rng = np.random.default_rng(12)
+    H = 16
+    theta = rng.normal(size=3 * H + 1)
+    cap = rng.random(H) * 1.5 + 0.05
+    u = rng.random(400)
+    ulo = rng.normal(size=400) * 1e-4
+    t = np.sort(rng.random(400))
+    _, g = L.grad(theta, u, t, H, cap, ulo=ulo)
+    eps = 1e-6
+    for k in range(theta.size):
+        d = np.zeros_like(theta)
+        d[k] = eps
+        num = (L.loss(theta + d, u, t, H, cap, ulo=ulo)
+               - L.loss(theta - d, u, t, H, cap, ulo=ulo)) / (2 * eps)
+        assert abs(num - g[k]) <= 1e-6 * max(1.0, abs(num)), k
+
+
+def knots_and_data(seed, n=3000):
+    rng = np.random.default_rng(seed)
+    H = 16
+    u = np.sort(rng.random(n) ** 2)                 # a CDF far from linear
+    c = np.quantile(u, np.linspace(0, 1, H + 1))
+    c = np.maximum.accumulate(c + np.arange(H + 1) * 1e-9)
+    v = np.sort(rng.random(H + 1))
+    t = (np.arange(n) + 0.5) / n
+    return H, u, c, v, t
+
+
+def test_knot_theta_is_the_interpolating_spline():
+    """knot_theta's network equals numpy.interp through (c_h, v_h) on [c_0, c_H]."""
+    H, u, c, v, _ = knots_and_data(13)
+    theta, cap = L.knot_theta(v, c, H)
+    x = np.random.default_rng(14).uniform(c[0], c[-1], 2000)
+    assert np.allclose(L.forward(theta, x, H, cap), np.interp(x, c, v), rtol=0, atol=1e-12)
+
+
+def test_knot_gradient_matches_central_differences():
+    """dL/dv by the chain rule equals central differences of L(v) = loss(knot_theta(v))."""
+    H, u, c, v, t = knots_and_data(15)
+    ulo = np.random.default_rng(16).normal(size=u.size) * 1e-7
+    _, gv = L.knot_grad(v, c, u, t, H, ulo=ulo)
+    eps = 1e-7
+    for k in range(H + 1):
+        d = np.zeros(H + 1)
+        d[k] = eps
+        th_p, cap = L.knot_theta(v + d, c, H)
+        th_m, _ = L.knot_theta(v - d, c, H)
+        num = (L.loss(th_p, u, t, H, cap, ulo=ulo) - L.loss(th_m, u, t, H, cap, ulo=ulo)) / (2 * eps)
+        assert abs(num - gv[k]) <= 1e-6 * max(1.0, abs(num)), k
+
+
+def test_knot_gradient_vanishes_at_the_least_squares_values():
+    """For fixed knots the spline is linear in v: numpy's least-squares v (basis: the hat
+    functions, obtained as the spline of each unit vector) has zero knot gradient."""
+    H, u, c, _, t = knots_and_data(17)
+    B = np.column_stack([np.interp(u, c, np.eye(H + 1)[k]) for k in range(H + 1)])
+    v_opt, *_ = np.linalg.lstsq(B, t, rcond=None)
+    _, gv = L.knot_grad(v_opt, c, u, t, H)
+    assert np.max(np.abs(gv)) < 1e-10
+
+
+def test_knot_adam_first_step_closed_form():
+    """Adam's first step on v moves each knot value by lr against the sign of its gradient
+    (bias-corrected moments; eps negligible), and the step lowers the loss for small lr."""
+    H, u, c, v, t = knots_and_data(18)
+    L0, gv = L.knot_grad(v, c, u, t, H)
+    lr = 1e-3
+    v1, m1, q1, l_at_v = L.knot_adam_step(v, np.zeros(H + 1), np.zeros(H + 1), 1, c, u, t, lr, H)
+    assert l_at_v == L0
+    # eps = 1e-8 against |dL/dv| >= 1e-4 moves the step by at most 1e-4 of lr
+    assert np.min(np.abs(gv)) > 1e-4
+    assert np.allclose(v1, v - lr * np.sign(gv), rtol=0, atol=1e-4 * lr)
+    assert np.allclose(m1, 0.1 * gv) and np.allclose(q1, 0.001 * gv * gv)
+    th1, cap = L.knot_theta(v1, c, H)
+    assert L.loss(th1, u, t, H, cap) < L0
