@@ -580,20 +580,7 @@ def vrf_tables(args):
     """64 table sizes log-uniform over [1e3, 3e5] (seeded), the tables, and a tagged trace whose
     table ids are drawn proportional to table size."""
     import synth
-    rng = np.random.default_rng(args.seed)
-    sizes = np.exp(rng.uniform(np.log(1e3), np.log(3e5), args.tables)).astype(int)
-    fibs = [synth.gen_fib(int(sz), seed=args.seed + 1000 + t, nh_max=4095)
-            for t, sz in enumerate(sizes)]
-    n = args.lookups
-    p = sizes / sizes.sum()
-    tid = rng.choice(args.tables, size=n, p=p).astype(np.uint8)
-    xh = np.empty(n, np.uint64)
-    xl = np.empty(n, np.uint64)
-    for t, f in enumerate(fibs):
-        idx = np.nonzero(tid == t)[0]
-        h, l = synth.gen_trace(f, idx.size, seed=args.seed + 2000 + t)
-        xh[idx], xl[idx] = h, l
-    return sizes, fibs, tid, xh, xl
+    return synth.gen_vrf_workload(args.tables, args.lookups, args.seed)
 
 
 def run_vrf64(args):

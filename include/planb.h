@@ -430,6 +430,33 @@ int planb_mlp_grad(const float *d_u, const float *d_t, size_t n, const float *w,
                    double *loss, planb_stream_t stream);
 
 /*
+ * planb_mlp_grad_split — planb_mlp_grad on the two-float input the training uses: entry i of the
+ * root's input is the unevaluated sum d_u[i] + d_ulo[i] (the range-reduced key carried to about
+ * 48 bits), and the first layer adds the parts as the lookup's model evaluation does. Arguments and
+ * errors as planb_mlp_grad; d_ulo is a device float array of n entries.
+ */
+int planb_mlp_grad_split(const float *d_u, const float *d_ulo, const float *d_t, size_t n,
+                         const float *w, float *grad, double *loss, planb_stream_t stream);
+
+/*
+ * planb_mlp_knot_step — one iteration of the root's training loop as the table build runs it: the
+ * full-batch gradient kernel, then the knot-value Adam kernel. The root is the linear spline
+ * through the points (knots[h], v[h]), h = 0..16 (unit input weights, b1[h] = -knots[h], caps
+ * knots[h+1] - knots[h] except the last unit's): w2[h] = (v[h+1] - v[h]) / (knots[h+1] - knots[h]),
+ * b2 = v[0]. The kernel carries dL/dw2 and dL/db2 to dL/dv by the chain rule and applies Adam
+ * (Kingma and Ba; beta1 0.9, beta2 0.999, eps 1e-8) to v.
+ *   d_u, d_ulo (nullable: single-float input), d_t: device float arrays of n entries.
+ *   w: host float[65] (w1, b1, w2, b2, cap), rewritten with the new w2 and b2; knots: host
+ *   float[17]; v, m, q: host float[17] (knot values and Adam's two moments), rewritten; step: the
+ *   steps already taken (this one is step + 1); lr: the learning rate; *loss: the loss before the
+ *   update. Synchronous on `stream`; uses the current device. The paper has no learned part.
+ * Errors: PLANB_EINVAL (null pointer, step < 0, n >= 2^32), PLANB_ENOMEM, PLANB_ECUDA.
+ */
+int planb_mlp_knot_step(const float *d_u, const float *d_ulo, const float *d_t, size_t n,
+                        float *w, const float *knots, float *v, float *m, float *q, int32_t step,
+                        float lr, double *loss, planb_stream_t stream);
+
+/*
  * planb_mlp_forward — y(u) for every entry of the device array d_u (n floats) into d_y (device);
  * w (65 floats) as in planb_mlp_grad. Asynchronous on `stream`.
  * Errors: PLANB_EINVAL, PLANB_ECUDA.

@@ -5,7 +5,8 @@ Prefixes become sorted elementary intervals (Section 3.1), laid out as a lineari
 lives in ``libplanb.so`` (C ABI in ``include/planb.h``); this package is its Python binding.
 """
 from .binding import (FORMATS, KERNELS, Fib, MultiFib, Server, PlanbError, child_index, debug_inject, intervals,  # noqa: F401
-                      layout_info, library_path, load, mlp_forward, mlp_grad, version)
+                      layout_info, library_path, load, mlp_forward, mlp_grad, mlp_grad_split,
+                      mlp_knot_step, version)
 
 
 def build(force: bool = False):

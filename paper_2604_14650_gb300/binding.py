@@ -103,6 +103,9 @@ _SIGS = {
                                          C.POINTER(_sz)]),
     "planb_mlp_grad": (C.c_int, [_vp, _vp, _sz, _vp, _vp, C.POINTER(C.c_double), _vp]),
     "planb_mlp_forward": (C.c_int, [_vp, _sz, _vp, _vp, _vp]),
+    "planb_mlp_grad_split": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _vp, C.POINTER(C.c_double), _vp]),
+    "planb_mlp_knot_step": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, C.c_int32,
+                                      C.c_float, C.POINTER(C.c_double), _vp]),
     "planb_multi_create": (C.c_int, [_vp, C.c_uint32, _sz, C.c_uint32, C.POINTER(_vp)]),
     "planb_multi_lookup": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_multi_destroy": (None, [_vp]),
@@ -230,6 +233,39 @@ def mlp_grad(u, t, w, stream=None):
                                  _ptr(wv), _ptr(g), C.byref(loss), _stream_handle(stream)),
            "planb_mlp_grad")
     return loss.value, g
+
+
+def mlp_grad_split(u, ulo, t, w, stream=None):
+    """mlp_grad on the two-float input u + ulo (CUDA float32 tensors u, ulo, t)."""
+    wv = np.ascontiguousarray(w, dtype=np.float32)
+    if wv.size != 65:
+        raise ValueError("w holds 65 floats: w1, b1, w2, b2, cap")
+    g = np.zeros(49, dtype=np.float32)
+    loss = C.c_double(0.0)
+    _check(load().planb_mlp_grad_split(C.c_void_p(u.data_ptr()), C.c_void_p(ulo.data_ptr()),
+                                       C.c_void_p(t.data_ptr()), u.numel(), _ptr(wv), _ptr(g),
+                                       C.byref(loss), _stream_handle(stream)),
+           "planb_mlp_grad_split")
+    return loss.value, g
+
+
+def mlp_knot_step(u, ulo, t, w, knots, v, m, q, step: int, lr: float, stream=None):
+    """One training iteration in knot-value form by the library's kernels (gradient, then Adam on
+    the knot values). u, ulo (or None), t: CUDA float32 tensors; w (65), knots, v, m, q (17):
+    host arrays. Returns (loss before the step, new w, new v, new m, new q) as float32 arrays."""
+    wv = np.array(w, dtype=np.float32)
+    kv = np.ascontiguousarray(knots, dtype=np.float32)
+    vv, mv, qv = (np.array(a, dtype=np.float32) for a in (v, m, q))
+    if wv.size != 65 or kv.size != 17 or vv.size != 17 or mv.size != 17 or qv.size != 17:
+        raise ValueError("w holds 65 floats; knots, v, m, q 17 each")
+    loss = C.c_double(0.0)
+    _check(load().planb_mlp_knot_step(C.c_void_p(u.data_ptr()),
+                                      C.c_void_p(ulo.data_ptr()) if ulo is not None else None,
+                                      C.c_void_p(t.data_ptr()), u.numel(), _ptr(wv), _ptr(kv),
+                                      _ptr(vv), _ptr(mv), _ptr(qv), int(step), float(lr),
+                                      C.byref(loss), _stream_handle(stream)),
+           "planb_mlp_knot_step")
+    return loss.value, wv, vv, mv, qv
 
 
 def mlp_forward(u, w, out=None, stream=None):

@@ -964,7 +964,32 @@ int planb_mlp_grad(const float* d_u, const float* d_t, size_t n, const float* w,
                    double* loss, planb_stream_t stream) {
   if ((n && (!d_u || !d_t)) || !w || !grad || !loss) return PLANB_EINVAL;
   try {
-    return planb::mlp_grad_host(d_u, d_t, n, w, grad, loss, reinterpret_cast<cudaStream_t>(stream));
+    return planb::mlp_grad_host(d_u, nullptr, d_t, n, w, grad, loss,
+                                reinterpret_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return PLANB_ENOMEM;
+  }
+}
+
+int planb_mlp_grad_split(const float* d_u, const float* d_ulo, const float* d_t, size_t n,
+                         const float* w, float* grad, double* loss, planb_stream_t stream) {
+  if ((n && (!d_u || !d_ulo || !d_t)) || !w || !grad || !loss) return PLANB_EINVAL;
+  try {
+    return planb::mlp_grad_host(d_u, d_ulo, d_t, n, w, grad, loss,
+                                reinterpret_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    return PLANB_ENOMEM;
+  }
+}
+
+int planb_mlp_knot_step(const float* d_u, const float* d_ulo, const float* d_t, size_t n,
+                        float* w, const float* knots, float* v, float* m, float* q, int32_t step,
+                        float lr, double* loss, planb_stream_t stream) {
+  if ((n && (!d_u || !d_t)) || !w || !knots || !v || !m || !q || !loss || step < 0)
+    return PLANB_EINVAL;
+  try {
+    return planb::knot_step_host(d_u, d_ulo, d_t, n, w, knots, v, m, q, step, lr, loss,
+                                 reinterpret_cast<cudaStream_t>(stream));
   } catch (const std::bad_alloc&) {
     return PLANB_ENOMEM;
   }

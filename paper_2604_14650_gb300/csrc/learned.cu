@@ -188,8 +188,8 @@ void init_weights(MlpWeights& w) {
 
 }  // namespace
 
-int mlp_grad_host(const float* d_u, const float* d_t, size_t n, const float* w_host,
-                  float* grad_host, double* loss_host, cudaStream_t st) {
+int mlp_grad_host(const float* d_u, const float* d_ulo, const float* d_t, size_t n,
+                  const float* w_host, float* grad_host, double* loss_host, cudaStream_t st) {
   if (n >= (size_t(1) << 32)) return PLANB_EINVAL;
   DevBuf part, wb, gb, lb;
   if (!part.alloc(kGradBlocks * kRow * sizeof(float), nullptr) ||
@@ -201,7 +201,7 @@ int mlp_grad_host(const float* d_u, const float* d_t, size_t n, const float* w_h
   if (cudaMemcpyAsync(wb.p, w_host, kMlpWeights * sizeof(float), cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return PLANB_ECUDA;
-  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(d_u, nullptr, d_t,
+  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(d_u, d_ulo, d_t,
                                                         static_cast<uint32_t>(n), wb.as<float>(),
                                                         part.as<float>());
   reduce_kernel<<<1, 64, 0, st>>>(part.as<float>(), kGradBlocks, static_cast<uint32_t>(n),
@@ -209,6 +209,46 @@ int mlp_grad_host(const float* d_u, const float* d_t, size_t n, const float* w_h
   if (cudaGetLastError() != cudaSuccess) return PLANB_ECUDA;
   if (cudaMemcpyAsync(grad_host, gb.p, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, st) !=
           cudaSuccess ||
+      cudaMemcpyAsync(loss_host, lb.p, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return PLANB_ECUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+int knot_step_host(const float* d_u, const float* d_ulo, const float* d_t, size_t n,
+                   float* w_host, const float* c_host, float* v_host, float* m_host,
+                   float* q_host, int32_t step, float lr, double* loss_host, cudaStream_t st) {
+  if (n >= (size_t(1) << 32) || step < 0) return PLANB_EINVAL;
+  constexpr size_t kK = kMlpHidden + 1;
+  DevBuf part, wb, vb, mb, qb, cb, sb, lb;
+  if (!part.alloc(kGradBlocks * kRow * sizeof(float), nullptr) ||
+      !wb.alloc(kMlpWeights * sizeof(float), nullptr) || !vb.alloc(kK * sizeof(float), nullptr) ||
+      !mb.alloc(kK * sizeof(float), nullptr) || !qb.alloc(kK * sizeof(float), nullptr) ||
+      !cb.alloc(kK * sizeof(float), nullptr) || !sb.alloc(sizeof(int), nullptr) ||
+      !lb.alloc(sizeof(double), nullptr)) {
+    cudaGetLastError();
+    return PLANB_ENOMEM;
+  }
+  const int s0 = step;
+  const bool ok =
+      cudaMemcpyAsync(wb.p, w_host, kMlpWeights * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+      cudaMemcpyAsync(vb.p, v_host, kK * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+      cudaMemcpyAsync(mb.p, m_host, kK * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+      cudaMemcpyAsync(qb.p, q_host, kK * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+      cudaMemcpyAsync(cb.p, c_host, kK * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+      cudaMemcpyAsync(sb.p, &s0, sizeof(int), cudaMemcpyHostToDevice, st) == cudaSuccess;
+  if (!ok) return PLANB_ECUDA;
+  // one iteration of the training graph: the gradient, then the knot-value Adam update
+  mlp_grad_kernel<<<kGradBlocks, kGradThreads, 0, st>>>(d_u, d_ulo, d_t, static_cast<uint32_t>(n),
+                                                        wb.as<float>(), part.as<float>());
+  knot_adam_kernel<<<1, 64, 0, st>>>(part.as<float>(), kGradBlocks, static_cast<uint32_t>(n),
+                                     wb.as<float>(), vb.as<float>(), mb.as<float>(),
+                                     qb.as<float>(), cb.as<float>(), sb.as<int>(), lr,
+                                     lb.as<double>());
+  if (cudaGetLastError() != cudaSuccess) return PLANB_ECUDA;
+  if (cudaMemcpyAsync(w_host, wb.p, kMlpWeights * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(v_host, vb.p, kK * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(m_host, mb.p, kK * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(q_host, qb.p, kK * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaMemcpyAsync(loss_host, lb.p, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PLANB_ECUDA;
   return cudaStreamSynchronize(st) == cudaSuccess ? PLANB_OK : PLANB_ECUDA;

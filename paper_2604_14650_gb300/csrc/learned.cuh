@@ -99,13 +99,22 @@ int build_learned(const Intervals& iv, uint32_t span, uint32_t leaves, uint32_t 
                   uint32_t max_window, LearnedBuild& out);
 
 // Full-batch gradient (and loss) of the root's mean squared error on device arrays u, t of n
-// entries, for weights w (host, 49 floats in the order w1, b1, w2, b2); synchronous on `st`.
-int mlp_grad_host(const float* d_u, const float* d_t, size_t n, const float* w_host,
-                  float* grad_host, double* loss_host, cudaStream_t st);
+// entries (input u + ulo when d_ulo is given), for weights w (host, 65 floats: w1, b1, w2, b2, cap);
+// synchronous on `st`.
+int mlp_grad_host(const float* d_u, const float* d_ulo, const float* d_t, size_t n,
+                  const float* w_host, float* grad_host, double* loss_host, cudaStream_t st);
+
+// One iteration of the training loop in knot-value form (the gradient kernel, then the knot-value
+// Adam kernel) on host copies of the state: w (65) is read and rewritten (w2, b2 from the new knot
+// values), v, m, q (17 each) are read and rewritten, c (17 knots) is read; `step` is the number of
+// steps already taken. Synchronous on `st`.
+int knot_step_host(const float* d_u, const float* d_ulo, const float* d_t, size_t n,
+                   float* w_host, const float* c_host, float* v_host, float* m_host,
+                   float* q_host, int32_t step, float lr, double* loss_host, cudaStream_t st);
 
 // y = root(u) for device arrays; asynchronous on `st`.
 int mlp_forward_host(const float* d_u, size_t n, const float* w_host, float* d_y, cudaStream_t st);
 
-// (the two gradient/forward entry points take a single-float input: ul = 0)
+// (the forward entry point takes a single-float input: ul = 0)
 
 }  // namespace planb

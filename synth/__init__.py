@@ -324,3 +324,27 @@ def gen_updates(fib: Fib, n: int, seed: int, withdraw_frac: float = 0.5, nh_max:
     inh = (1 + below(u64(seed, U_NH, start, ni), nh_max)).astype(np.uint16)
     return (ihi, ilo, lens.astype(np.uint8), inh,
             fib.hi[w].copy(), fib.lo[w].copy(), fib.len[w].copy())
+
+
+# ---------------------------------------------------------------------------- multi-table (VRF)
+
+def gen_vrf_workload(n_tables: int, n: int, seed: int, min_prefixes: int = 1000,
+                     max_prefixes: int = 300_000, nh_max: int = 4095):
+    """``n_tables`` tables whose sizes are log-uniform over [min_prefixes, max_prefixes] (each built
+    like ``gen_fib``, with its own seed) and a trace of ``n`` addresses, each tagged with a u8 table
+    id drawn proportional to table size; every address follows its table's traffic mix.
+
+    Returns (sizes, fibs, tid, hi, lo). Sizes and ids come from numpy's seeded PCG64 stream (no
+    lookup arithmetic here either)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(min_prefixes), np.log(max_prefixes), n_tables)).astype(int)
+    fibs = [gen_fib(int(sz), seed=seed + 1000 + t, nh_max=nh_max) for t, sz in enumerate(sizes)]
+    p = sizes / sizes.sum()
+    tid = rng.choice(n_tables, size=n, p=p).astype(np.uint8)
+    hi = np.empty(n, np.uint64)
+    lo = np.empty(n, np.uint64)
+    for t, f in enumerate(fibs):
+        idx = np.nonzero(tid == t)[0]
+        h, l = gen_trace(f, idx.size, seed=seed + 2000 + t)
+        hi[idx], lo[idx] = h, l
+    return sizes, fibs, tid, hi, lo

@@ -1,0 +1,127 @@
+"""GPU parity at the full sizes of the grown workloads, bit-exact against the O2 trie oracle,
+element by element, in the launch configurations the benchmark times:
+
+* 1,000,000 prefixes (+ ::/0) and 2^28 addresses, every node format and kernel (the learned
+  position model included): at this size the F16HI hybrid descends two levels from L2 below its
+  shared-memory index and the learned F8 tables three;
+* 64 tables (VRFs) of log-uniform size between 1,000 and 300,000 prefixes and 2^27 addresses
+  tagged with a table id drawn proportional to table size, in the single persistent launch and
+  with one launch per table, for F16HI and F8X128 tables;
+* the 200,000-prefix table under the locality-skewed trace (Zipf(1.1) over 10^5 hot /64 blocks).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2604_14650_gb300 as pb  # noqa: E402
+
+THREADS = os.cpu_count() or 1
+VARIANTS = [("f8v7", "hybrid"), ("f8v7", "learned"), ("f8x128", "hybrid"), ("f8x128", "learned"),
+            ("f8x128", "coop"), ("f8x128", "flat"), ("f16hi", "coop"), ("f16hi", "hybrid")]
+VIDS = [f"{f}-{k}" for f, k in VARIANTS]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pb.build()
+
+
+def dev(a, dtype=np.int64):
+    return torch.from_numpy(np.ascontiguousarray(a).view(dtype)).cuda()
+
+
+def lookup_all(fib, xh, xl):
+    dh, dl = dev(xh), dev(xl)
+    out = fib.lookup(dh, dl)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint16)
+    del dh, dl, out
+    return got
+
+
+@pytest.fixture(scope="module")
+def grown():
+    """1,000,000 prefixes (the length mix scaled up, 1 % /128) and 2^28 addresses; the oracle's
+    answer for every address is computed once."""
+    f = synth.gen_fib(1_000_000, seed=2604, nh_max=4095)
+    n = 1 << 28
+    xh, xl = synth.gen_trace(f, n, seed=2605)
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl, threads=THREADS)
+    return f, xh, xl, want
+
+
+@pytest.mark.parametrize("variant", VARIANTS, ids=VIDS)
+def test_million_prefix_full_size_parity(grown, variant):
+    f, xh, xl, want = grown
+    fmt, kernel = variant
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel) as fib:
+        st = fib.stats()
+        if (fmt, kernel) == ("f16hi", "hybrid"):
+            assert st["depth"] - st["smem_levels"] == 2        # two L2 levels below the index
+        if kernel == "learned":
+            assert st["model_iters"] > 0 and st["model_covered"] > 0.5
+        got = lookup_all(fib, xh, xl)
+    bad = int(np.count_nonzero(got != want))
+    assert bad == 0, f"{bad} of {want.size} differ"
+
+
+@pytest.fixture(scope="module")
+def vrf64():
+    """64 VRF tables and 2^27 tagged addresses (the benchmark's multi-table workload, same seed);
+    the oracle answers each address with its own table's trie."""
+    sizes, fibs, tid, xh, xl = synth.gen_vrf_workload(64, 1 << 27, 2604)
+    order = np.argsort(tid, kind="stable")
+    bounds = np.searchsorted(tid[order], np.arange(65))
+    want = np.zeros(tid.size, np.uint16)
+    for t, f in enumerate(fibs):
+        idx = order[bounds[t]:bounds[t + 1]]
+        want[idx] = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh[idx], xl[idx], threads=THREADS)
+    return sizes, fibs, tid, xh, xl, want
+
+
+@pytest.mark.parametrize("per_table", [False, True], ids=["persistent", "per_table"])
+@pytest.mark.parametrize("fmt", ["f16hi", "f8x128"])
+def test_vrf64_full_size_parity(vrf64, fmt, per_table):
+    sizes, fibs_in, tid, xh, xl, want = vrf64
+    assert sizes.sum() > 2_000_000 and tid.size == 1 << 27
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) for f in fibs_in]
+    try:
+        with pb.MultiFib(fibs, max_batch=tid.size, per_table=per_table) as mt:
+            dh, dl, dt = dev(xh), dev(xl), dev(tid, np.uint8)
+            out = torch.empty(tid.size, dtype=torch.int16, device="cuda")
+            for _ in range(2):                 # the capture, then a replay of the graph
+                out.fill_(-1)
+                mt.lookup(dh, dl, dt, out=out)
+                torch.cuda.synchronize()
+                got = out.cpu().numpy().view(np.uint16)
+                bad = int(np.count_nonzero(got != want))
+                assert bad == 0, f"{bad} of {want.size} differ"
+            assert mt.persistent == (not per_table)
+            del dh, dl, dt, out
+    finally:
+        for f in fibs:
+            f.close()
+
+
+@pytest.mark.parametrize("variant", [("f16hi", "hybrid"), ("f8x128", "hybrid")],
+                         ids=["f16hi-hybrid", "f8x128-hybrid"])
+def test_backbone_zipf_parity(variant):
+    """200,000 prefixes, 2^26 addresses of the locality-skewed trace (the benchmark's Zipf
+    variant)."""
+    f = synth.gen_fib(200_000, seed=2604, nh_max=4095)
+    xh, xl = synth.gen_trace_zipf(f, 1 << 26, seed=2605)
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh, xl, threads=THREADS)
+    fmt, kernel = variant
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel) as fib:
+        got = lookup_all(fib, xh, xl)
+    assert np.array_equal(got, want)

@@ -63,6 +63,69 @@ def test_gradient_matches_oracle(n, seed):
     assert np.max(np.abs(g - ref)) <= tol, (np.max(np.abs(g - ref)), tol)
 
 
+def split_input(x):
+    """float64 values in [0, 1) as the two-float input the training feeds: (float32 of x, float32
+    of the rest)."""
+    u = x.astype(np.float32)
+    return u, (x - u.astype(np.float64)).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,seed", [(777, 21), (200_000, 22), (1_000_003, 23)])
+def test_gradient_split_input_matches_oracle(n, seed):
+    """The gradient kernel on the two-float input u + ulo (the form the table build trains on)
+    equals the float64 chain rule on the summed input, within the FP32 summation bound above."""
+    rng = np.random.default_rng(seed)
+    w = weights(rng)
+    x = np.sort(rng.random(n) ** 2)
+    u, ulo = split_input(x)
+    assert np.any(ulo != 0)
+    t = ((np.arange(n) + 0.5) / n).astype(np.float32)
+    loss, g = pb.mlp_grad_split(torch.from_numpy(u).cuda(), torch.from_numpy(ulo).cuda(),
+                                torch.from_numpy(t).cuda(), w)
+    th, cap = split(w)
+    ref_loss, ref = OL.grad(th, u, t.astype(np.float64), H, cap, ulo=ulo)
+    assert abs(loss - ref_loss) <= 1e-5 * max(ref_loss, 1e-12)
+    tol = 1e-4 * np.max(np.abs(ref)) + 1e-7
+    assert np.max(np.abs(g - ref)) <= tol, (np.max(np.abs(g - ref)), tol)
+
+
+@pytest.mark.parametrize("n,seed", [(100_000, 2), (1_000_003, 5)])
+def test_knot_step_matches_oracle(n, seed):
+    """Five training iterations by the library's kernels (gradient, then Adam on the knot values
+    through the chain rule) track five float64 steps of the oracle's knot-value Adam: the moments
+    within FP32 gradient accuracy (1e-4 of the largest), the knot values within 1e-3 of the
+    learning rate per step (every |dL/dv| is above 0.1 of the largest at the start, so no step
+    can change sign), and the returned weights are the spline of the returned knot values."""
+    rng = np.random.default_rng(seed)
+    x = np.sort(rng.random(n) ** 2)
+    u, ulo = split_input(x)
+    t = ((np.arange(n) + 0.5) / n).astype(np.float32)
+    idx = np.minimum(n - 1, (np.arange(H + 1) * n) // H)
+    c = (u[idx].astype(np.float64) + ulo[idx]).astype(np.float32)
+    for h in range(1, H + 1):
+        if not c[h] > c[h - 1]:
+            c[h] = np.nextafter(c[h - 1], np.float32(2))
+    v = (t[idx] + 0.05 * rng.choice([-1, 1], H + 1)).astype(np.float32)
+    th0, cap = OL.knot_theta(v.astype(np.float64), c.astype(np.float64), H)
+    w = np.concatenate([th0, cap]).astype(np.float32)
+    _, gv0 = OL.knot_grad(v.astype(np.float64), c.astype(np.float64), u, t, H, ulo=ulo)
+    assert np.min(np.abs(gv0)) > 0.1 * np.max(np.abs(gv0))
+    du, dl, dt = (torch.from_numpy(a).cuda() for a in (u, ulo, t))
+    lr = 1e-3
+    m = q = np.zeros(H + 1, np.float32)
+    rv, rm, rq = v.astype(np.float64), np.zeros(H + 1), np.zeros(H + 1)
+    for step in range(5):
+        loss, w, v, m, q = pb.mlp_knot_step(du, dl, dt, w, c, v, m, q, step, lr)
+        rv, rm, rq, rloss = OL.knot_adam_step(rv, rm, rq, step + 1, c.astype(np.float64), u, t,
+                                              lr, H, ulo=ulo)
+        assert abs(loss - rloss) <= 1e-5 * rloss + 1e-12, step
+        assert np.max(np.abs(m - rm)) <= 1e-4 * np.max(np.abs(rm)) + 1e-9, step
+        assert np.max(np.abs(q - rq)) <= 2e-4 * np.max(np.abs(rq)) + 1e-12, step
+        assert np.max(np.abs(v - rv)) <= 1e-3 * lr * (step + 1) + 2e-7, step
+        th, _ = OL.knot_theta(v.astype(np.float64), c.astype(np.float64), H)
+        assert np.allclose(w[2 * H:3 * H + 1], th[2 * H:], rtol=1e-5, atol=1e-6), step
+
+
 def test_gradient_descent_direction():
     """A small step against the library's gradient lowers the oracle's loss."""
     rng = np.random.default_rng(5)
