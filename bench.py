@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
     ap.add_argument("--update-rate", type=float, default=1000.0, help="serve: route changes/s")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default run: skip the learned1m, vrf64 and zipf blocks")
+    ap.add_argument("--extra-steps", type=int, default=5,
+                    help="timed steps of each extra block (after 3 warm-up steps)")
     return ap.parse_args()
 
 
@@ -225,9 +229,10 @@ def workload_name(args):
             f"({t})")
 
 
-def cpu_oracle_rate(fib, xh, xl, seconds, threads=None):
-    """The oracle (O2 binary trie, as it stands) on the host cores (all of them by default) over a
-    bounded sample."""
+def cpu_oracle_rate(fib, xh, xl, seconds, threads=None, runs=5):
+    """The oracle (O2 binary trie, as it stands) on the host cores (all of them by default): the
+    median rate of `runs` timed passes over one bounded sample, sized so that all passes take
+    about `seconds`. Returns (rate, threads used, sample, seconds per pass, every pass's rate)."""
     import oracle
     trie = oracle.Trie(fib.hi, fib.lo, fib.len, fib.nh)
     threads = threads or os.cpu_count() or 1
@@ -235,26 +240,62 @@ def cpu_oracle_rate(fib, xh, xl, seconds, threads=None):
     t0 = time.perf_counter()
     trie.lookup(xh[:probe], xl[:probe], threads=threads)
     dt = max(time.perf_counter() - t0, 1e-6)
-    sample = int(min(xh.size, max(probe, probe * seconds / dt)))
+    sample = int(min(xh.size, max(probe, probe * seconds / runs / dt)))
     out = np.empty(sample, np.uint16)
-    t0 = time.perf_counter()
-    trie.lookup(xh[:sample], xl[:sample], threads=threads, out=out)
-    dt = time.perf_counter() - t0
-    return sample / dt, trie.last_threads, sample, dt
+    rates = []
+    for _ in range(runs):
+        t0 = time.perf_counter()
+        trie.lookup(xh[:sample], xl[:sample], threads=threads, out=out)
+        rates.append(sample / (time.perf_counter() - t0))
+    rate = statistics.median(rates)
+    return rate, trie.last_threads, sample, sample / rate, rates
 
 
 def host_info():
+    """ISA, CPU model and core count of the host (lscpu's model name where it has one: on Arm
+    hosts /proc/cpuinfo names only the implementer and part numbers)."""
     import platform
-    model = platform.processor() or platform.machine()
+    model, vendor = None, None
     try:
-        with open("/proc/cpuinfo") as f:
-            for line in f:
-                if line.lower().startswith(("model name", "cpu model")):
-                    model = line.split(":", 1)[1].strip()
-                    break
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and not model:
+                model = v.strip()
+            elif k.strip() == "Vendor ID" and not vendor:
+                vendor = v.strip()
+    except (OSError, subprocess.SubprocessError):
         pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    model = model or platform.processor() or platform.machine()
+    if vendor and vendor not in model:
+        model = f"{vendor} {model}"
     return {"arch": platform.machine(), "model": model, "nproc": os.cpu_count()}
+
+
+def low_half_fraction(pb, fib_in, xh):
+    """Share of addresses whose F16HI lookup reads the address's low half: those whose high-half
+    count lands on an interval whose key (its inclusive end) shares the address's high half and
+    has a low half other than all-ones (the next-hop word's flag). Counted on the host from the
+    library's own interval list, for stating the bytes that cross the host link."""
+    sh, sl, _ = pb.intervals(fib_in.hi, fib_in.lo, fib_in.len, fib_in.nh)
+    if sh.size < 2:
+        return 0.0
+    nxt_h, nxt_l = sh[1:], sl[1:]
+    key_hi = np.where(nxt_l == 0, nxt_h - np.uint64(1), nxt_h)     # high half of start[i+1] - 1
+    flag = nxt_l != 0
+    r = np.searchsorted(key_hi, xh, side="left")
+    inside = r < key_hi.size
+    rr = np.minimum(r, key_hi.size - 1)
+    return float(np.mean(inside & flag[rr] & (key_hi[rr] == xh)))
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -369,8 +410,22 @@ def run_planb(args):
         torch.cuda.synchronize()
         barrier(dist, local)
         dt = max_over_ranks(dist, time.perf_counter() - t0, True)
+        # bytes that cross the host link per step: every address's 8-byte high half, the 8-byte
+        # low half only where an F16HI count needs settling (other formats read both halves), and
+        # the 2-byte next hop back
+        if args.format == "f16hi":
+            frac_lo = low_half_fraction(pb, fib_in, xh[idx])
+            h2d = int(round(8 * n + 8 * frac_lo * n))
+        else:
+            frac_lo, h2d = 1.0, 16 * n
         e2e = {"value": n * world * args.e2e_steps / dt / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 2 * n,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 2 * n,
+               "h2d_bytes_interface": 16 * n,
+               "low_halves_read_fraction": frac_lo,
+               "bytes_note": "h2d counts the bytes the zero-copy kernel reads over the host link "
+                             "(8 B high half per address, plus the low half of the sampled share "
+                             "of addresses whose count needs it); the interface holds 16 B per "
+                             "address",
                "api": "planb_lookup_host (pinned host buffers: the lookup kernel reads the "
                       "addresses and writes the next hops over the host link)"}
         if not np.array_equal(po.numpy().view(np.uint16)[idx], want):
@@ -390,7 +445,7 @@ def run_planb(args):
         barrier(dist, local)
         dt = max_over_ranks(dist, time.perf_counter() - t0, True)
         e2e["mapped"] = {"value": n * world * args.e2e_steps / dt / 1e9, "unit": UNIT,
-                         "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 2 * n,
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 2 * n,
                          "api": "planb_lookup_mapped (pinned host buffers read and written by "
                                 "the lookup kernel over the host link)"}
         # the host link's own rate for a plain pinned-to-device copy of the high halves: the
@@ -489,13 +544,18 @@ def run_planb(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, cores, sample, secs = cpu_oracle_rate(fib_in, xh, xl, args.cpu_seconds)
-        rate1, _, sample1, secs1 = cpu_oracle_rate(fib_in, xh, xl, args.cpu_seconds / 4, threads=1)
+        rate, cores, sample, secs, rates = cpu_oracle_rate(fib_in, xh, xl, args.cpu_seconds)
+        rate1, _, sample1, secs1, rates1 = cpu_oracle_rate(fib_in, xh, xl, args.cpu_seconds / 4,
+                                                           threads=1)
         cpu = {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"first {sample} addresses of the same trace, binary trie, {secs:.1f} s",
+               "sample": f"first {sample} addresses of the same trace, binary trie, median of "
+                         f"{len(rates)} passes of {secs:.2f} s",
+               "runs_B_lookups_per_s": [r / 1e9 for r in rates],
                "host": host_info(),
                "one_core": {"value": rate1 / 1e9, "unit": UNIT, "cores": 1,
-                            "sample": f"first {sample1} addresses, {secs1:.1f} s"}}
+                            "sample": f"first {sample1} addresses, median of {len(rates1)} "
+                                      f"passes of {secs1:.2f} s",
+                            "runs_B_lookups_per_s": [r / 1e9 for r in rates1]}}
 
     peak, peak_kind = measured_peaks()
     kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
@@ -531,6 +591,16 @@ def run_planb(args):
                  # against 4 schedulers x SMs x the SM clock sampled under load
                  "issue": None,
                  "source": "profiles/traffic.json (ncu --set full capture of this kernel)"}
+    # the grown workloads, each with its own value, roofline and sampled parity (rank 0, N = 1)
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra and args.workload == "backbone":
+        del d_hi, d_lo, d_out
+        torch.cuda.empty_cache()
+        es, ew = args.extra_steps, 3
+        extra = {"learned1m": block_learned1m(args, stream, es, ew),
+                 "vrf64": block_vrf64(args, stream, es, ew),
+                 "zipf": block_zipf(args, stream, es, ew, fib_in=fib_in)}
+        torch.cuda.empty_cache()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -556,9 +626,17 @@ def run_planb(args):
                               "paper_plain_tree_coop_B_lookups_per_s":
                                   ablation["f8x128/coop"]["B_lookups_per_s"]}
                              if ablation else None),
+        "workloads": extra,
         "clocks": clk,
         "gpu_launches": args.steps,
     }
+    if extra and line["learned_vs_plain"] is not None:
+        L1 = extra["learned1m"]
+        line["learned_vs_plain"]["grown_1m_prefixes"] = {
+            "learned_B_lookups_per_s": L1["value"],
+            "plain_tree_best": L1["best_plain"],
+            "plain_tree_best_B_lookups_per_s": L1["best_plain_B_lookups_per_s"],
+            "model_max_err": L1["variants"]["learned_f8x128"]["model"]["max_err"]}
     if roofs is not None and rec.get("warp_inst_per_lookup"):
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = (clk or {}).get("sm_mhz") or measured_peaks_mhz()
@@ -672,6 +750,156 @@ def run_vrf64(args):
     for f in fibs:
         f.close()
     return 0
+
+
+def _timed_ms(launch, stream, steps, warmup):
+    """Mean ms per launch of `launch()` over `steps` launches after `warmup`, CUDA events on
+    `stream`."""
+    import torch
+    for _ in range(warmup):
+        launch()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        launch()
+    b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def _hbm_roofline(bytes_per_lookup, n, ms, kernel):
+    peak, kind = measured_peaks()
+    ach = bytes_per_lookup * n / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": None, "kernel": kernel, "peak_source": kind,
+            "algorithmic_bytes_per_launch": bytes_per_lookup * n}
+
+
+def block_learned1m(args, stream, steps, warmup, lookups=1 << 28):
+    """1,000,000 prefixes (1 % /128) and 2^28 device-resident addresses: the learned position
+    model against the plain tree on the same table and addresses, each timed by CUDA events,
+    every variant's results equal, a 2^16 sample equal to the oracle."""
+    import torch
+    import paper_2604_14650_gb300 as pb
+    import synth
+    import oracle
+    f = synth.gen_fib(1_000_000, seed=args.seed, nh_max=4095)
+    n = lookups
+    xh, xl = synth.gen_trace(f, n, seed=args.seed + 1)
+    d_hi = torch.from_numpy(xh.view(np.int64)).cuda()
+    d_lo = torch.from_numpy(xl.view(np.int64)).cuda()
+    d_out = torch.empty(n, dtype=torch.int16, device="cuda")
+    res, ref = {}, None
+    for name, kw in (("learned_f8x128", dict(kernel="learned")),
+                     ("plain_f8x128_hybrid", dict(kernel="hybrid")),
+                     ("plain_f16hi_hybrid", dict(format="f16hi", kernel="hybrid")),
+                     ("plain_f8x128_coop", dict(kernel="coop"))):
+        with pb.Fib(f.hi, f.lo, f.len, f.nh, **kw) as fib:
+            ms = _timed_ms(lambda: fib.lookup_ptr(d_hi.data_ptr(), d_lo.data_ptr(), n,
+                                                  d_out.data_ptr(), stream), stream, steps, warmup)
+            st = fib.stats()
+            res[name] = {"B_lookups_per_s": n / ms / 1e6, "ms_per_launch": ms,
+                         "depth": st["depth"], "smem_levels": st["smem_levels"],
+                         "levels_from_l2": st["depth"] - st["smem_levels"]}
+            if kw.get("kernel") == "learned":
+                res[name]["model"] = {k[6:]: st[k] for k in st if k.startswith("model_")}
+            if ref is None:
+                ref = d_out.clone()
+            res[name]["same_results_as_learned"] = bool(torch.equal(ref, d_out))
+    idx = np.random.default_rng(2).integers(0, n, 1 << 16)
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh[idx], xl[idx])
+    parity = bool(np.array_equal(ref.cpu().numpy().view(np.uint16)[idx], want))
+    lv = res["learned_f8x128"]
+    best_plain = max((k for k in res if k.startswith("plain")),
+                     key=lambda k: res[k]["B_lookups_per_s"])
+    del d_hi, d_lo, d_out, ref
+    return {"workload": f"1,000,000-prefix synthetic FIB (1 % /128), {n} device-resident lookups",
+            "value": lv["B_lookups_per_s"], "unit": UNIT, "steps": steps, "warmup": warmup,
+            "what": "learned position model (F8X128) beside the plain tree forms",
+            "best_plain": best_plain,
+            "best_plain_B_lookups_per_s": res[best_plain]["B_lookups_per_s"],
+            "roofline": _hbm_roofline(HBM_BYTES_PER_LOOKUP, n, lv["ms_per_launch"],
+                                      "lookup_hybrid<3, 0, 1, 0, 0>"),
+            "variants": res, "sampled_parity_vs_oracle": parity,
+            "all_variants_equal": all(v["same_results_as_learned"] for v in res.values())}
+
+
+def block_zipf(args, stream, steps, warmup, fib_in=None, lookups=1 << 28):
+    """The 200,000-prefix table under the locality-skewed trace (Zipf(1.1) over 10^5 hot /64
+    blocks), 2^28 addresses, the headline kernel (F16HI hybrid)."""
+    import torch
+    import paper_2604_14650_gb300 as pb
+    import synth
+    import oracle
+    f = fib_in if fib_in is not None else synth.gen_fib(200_000, seed=args.seed, nh_max=4095)
+    n = lookups
+    xh, xl = synth.gen_trace_zipf(f, n, seed=args.seed + 1)
+    d_hi = torch.from_numpy(xh.view(np.int64)).cuda()
+    d_lo = torch.from_numpy(xl.view(np.int64)).cuda()
+    d_out = torch.empty(n, dtype=torch.int16, device="cuda")
+    with pb.Fib(f.hi, f.lo, f.len, f.nh, format="f16hi", kernel="hybrid") as fib:
+        ms = _timed_ms(lambda: fib.lookup_ptr(d_hi.data_ptr(), d_lo.data_ptr(), n,
+                                              d_out.data_ptr(), stream), stream, steps, warmup)
+        st = fib.stats()
+    idx = np.random.default_rng(3).integers(0, n, 1 << 16)
+    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh[idx], xl[idx])
+    parity = bool(np.array_equal(d_out.cpu().numpy().view(np.uint16)[idx], want))
+    del d_hi, d_lo, d_out
+    kernel = f"lookup_hybrid16<{st['depth'] - st['smem_levels']}, 0>"
+    return {"workload": f"200,000-prefix FIB, {n} lookups, Zipf(1.1) over 1e5 hot /64 blocks",
+            "value": n / ms / 1e6, "unit": UNIT, "steps": steps, "warmup": warmup,
+            "ms_per_launch": ms, "roofline": _hbm_roofline(HBM_BYTES_PER_LOOKUP, n, ms, kernel),
+            "sampled_parity_vs_oracle": parity}
+
+
+def block_vrf64(args, stream, steps, warmup, lookups=1 << 27, fmt="f16hi"):
+    """64 VRF tables (sizes log-uniform over 1e3..3e5 prefixes) and 2^27 addresses tagged with a
+    table id drawn proportional to table size: the whole multi-table pipeline (one captured graph
+    per step) in the single persistent launch and with one launch per table."""
+    import torch
+    import paper_2604_14650_gb300 as pb
+    import synth
+    import oracle
+    sizes, fibs_in, tid, xh, xl = synth.gen_vrf_workload(64, lookups, args.seed)
+    n = xh.size
+    d_hi = torch.from_numpy(xh.view(np.int64)).cuda()
+    d_lo = torch.from_numpy(xl.view(np.int64)).cuda()
+    d_t = torch.from_numpy(tid).cuda()
+    d_out = torch.empty(n, dtype=torch.int16, device="cuda")
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) for f in fibs_in]
+    ptrs = (d_hi.data_ptr(), d_lo.data_ptr(), d_t.data_ptr(), n, d_out.data_ptr())
+    sample = np.random.default_rng(1).integers(0, n, 1 << 16)
+    want = np.zeros(sample.size, np.uint16)
+    for t, f in enumerate(fibs_in):
+        sel = tid[sample] == t
+        want[sel] = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh[sample][sel], xl[sample][sel])
+    res = {}
+    try:
+        for mode, per_table in (("persistent", False), ("per_table", True)):
+            with pb.MultiFib(fibs, max_batch=n, per_table=per_table) as mt:
+                d_out.fill_(-1)
+                mt.lookup_ptr(*ptrs, stream)
+                stream.synchronize()
+                got = d_out.cpu().numpy().view(np.uint16)[sample]
+                ms = _timed_ms(lambda: mt.lookup_ptr(*ptrs, stream), stream, steps, warmup)
+                res[mode] = {"B_lookups_per_s": n / ms / 1e6, "ms_per_step": ms,
+                             "sampled_parity_vs_oracle": bool(np.array_equal(got, want)),
+                             "single_launch": bool(mt.persistent)}
+    finally:
+        for f in fibs:
+            f.close()
+    del d_hi, d_lo, d_t, d_out
+    p = res["persistent"]
+    return {"workload": f"64 VRF tables, {int(sizes.sum())} prefixes in all, {n} lookups "
+                        "tagged with a u8 table id drawn proportional to table size",
+            "value": p["B_lookups_per_s"], "unit": UNIT, "steps": steps, "warmup": warmup,
+            "format": fmt,
+            "roofline": dict(_hbm_roofline(19, n, p["ms_per_step"], "multi-table pipeline"),
+                             note="19 B per lookup (16 B address + 1 B table id + 2 B result) over "
+                                  "the whole captured pipeline of one step"),
+            "modes": res,
+            "sampled_parity_vs_oracle": all(r["sampled_parity_vs_oracle"] for r in res.values())}
 
 
 def run_learned1m(args):
