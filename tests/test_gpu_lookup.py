@@ -366,3 +366,40 @@ def test_small_and_large_launches_agree(fmt):
             out = fib.lookup(dh[:k], dl[:k])
             torch.cuda.synchronize()
             assert np.array_equal(out.cpu().numpy().view(np.uint16), want[:k]), k
+
+
+@pytest.mark.parametrize("spread", [False, True], ids=["dense", "sparse_wide"])
+def test_f16hi_index_clusters_in_one_bucket(spread):
+    """A cluster of 100 /64 routes whose high halves differ only in their low 8 bits (with /128
+    routes inside some of them) puts many index entries into one radix-directory bucket, in a
+    dense table and in a small table spread over the whole space (buckets tens of bits wide);
+    every boundary, its neighbours and random addresses of the cluster are looked up in a launch
+    large enough to stage the index in shared memory."""
+    rng = np.random.default_rng(951)
+    H = np.uint64(0x2001_0DB8_0000_0000)                      # 256-aligned high half
+    ch = H + np.arange(100, dtype=np.uint64) * np.uint64(2)
+    cl = np.zeros(100, np.uint64)
+    cL = np.full(100, 64, np.uint8)
+    # /128 routes inside a few of the /64s (flagged keys sharing the address's high half)
+    hh = ch[::10]
+    hl = rng.integers(1, 2 ** 63, size=hh.size, dtype=np.uint64)
+    if spread:
+        far = synth.gen_fib(12, seed=952, nh_max=4095, default=False)
+    else:
+        far = synth.gen_fib(20_000, seed=953, nh_max=4095, default=False)
+    z64 = np.zeros(1, np.uint64)
+    hi = np.concatenate([far.hi, ch, hh, z64])
+    lo = np.concatenate([far.lo, cl, hl, z64])
+    ln = np.concatenate([far.len, cL, np.full(hh.size, 128, np.uint8), np.zeros(1, np.uint8)])
+    nh = rng.integers(1, 4096, size=hi.size).astype(np.uint16)
+    g = synth.Fib(hi, lo, ln, nh, 0)
+    bh, bl = boundary_probes(g)
+    k = 400_000                                               # large enough to stage the index
+    ih = H + rng.integers(0, 256, size=k // 2, dtype=np.uint64)
+    il = rng.integers(0, 2 ** 63, size=k // 2, dtype=np.uint64) * np.uint64(2)
+    th, tl = synth.gen_trace(g, k // 2, seed=954)
+    xh = np.concatenate([bh, ih, th])
+    xl = np.concatenate([bl, il, tl])
+    with pb.Fib(g.hi, g.lo, g.len, g.nh, format="f16hi", kernel="hybrid") as fib:
+        assert fib.stats()["smem_levels"] >= 1
+        assert np.array_equal(gpu_lookup(fib, xh, xl), expected(g, xh, xl))
