@@ -214,10 +214,15 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   uint32_t model_leaves = 0;
   if (learned) {
     // leaf models: about one per 128 keys, a power of two in [64, 2048], then the index gets the
-    // rest of the shared-memory budget
+    // rest of the shared-memory budget; a table of a million keys or more gets 4096 (past about
+    // 512 keys per leaf a line no longer keeps every rank within the 64-rank window: at 1M
+    // prefixes, 2048 leaves recorded a largest bound of 88 ranks, 4096 leaves 63; 74 KB of shared
+    // memory, still two CTAs per SM)
     uint32_t want = o.model_leaves > 0 ? static_cast<uint32_t>(o.model_leaves) : 64u;
-    if (o.model_leaves <= 0)
+    if (o.model_leaves <= 0) {
       while (want < 2048u && static_cast<uint64_t>(want) * 128u < m) want <<= 1;
+      if (want == 2048u && m >= (uint64_t(1) << 20)) want = 4096u;
+    }
     model_leaves = std::min<uint32_t>(want, 8192u);
     const size_t leaf_bytes = static_cast<size_t>(model_leaves) * 18u;
     const size_t budget = kSmemBudget > leaf_bytes + 8192 ? kSmemBudget - leaf_bytes : 8192;

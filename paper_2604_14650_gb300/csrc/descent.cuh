@@ -138,6 +138,33 @@ __device__ __forceinline__ uint32_t index_count_hi_global(const ulonglong2* sidx
   return b + (__ldg(&sidx[b].x) < my_hi ? 1u : 0u);
 }
 
+// Four consecutive high halves of a 128-byte F16HI node line (32 bytes, 32-byte aligned), read
+// with one 256-bit load through the read-only path.
+struct Quad {
+  uint64_t a, b, c, d;
+};
+__device__ __forceinline__ Quad ldg_quad(const uint64_t* p) {
+  Quad q;
+  asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];"
+      : "=l"(q.a), "=l"(q.b), "=l"(q.c), "=l"(q.d)
+      : "l"(p));
+  return q;
+}
+
+// Keys of a 16-key node below q for a 4-lane group (lane j of the group holds keys 4j .. 4j+3 in
+// k): one ballot per key slot; bit 4g + j of ballot s is key 4j + s of group g, so the group's
+// nibble of each of the four ballots, gathered into one word by byte permutes (`sel` picks byte
+// g / 2 of two ballots, `nib` keeps the group's nibble of each byte), holds one bit per key below.
+__device__ __forceinline__ uint32_t quad_count(const Quad& k, uint64_t q, uint32_t sel,
+                                               uint32_t nib) {
+  const uint32_t b0 = __ballot_sync(kFull, k.a < q);
+  const uint32_t b1 = __ballot_sync(kFull, k.b < q);
+  const uint32_t b2 = __ballot_sync(kFull, k.c < q);
+  const uint32_t b3 = __ballot_sync(kFull, k.d < q);
+  const uint32_t x = __byte_perm(__byte_perm(b0, b1, sel), __byte_perm(b2, b3, sel), 0x5410u);
+  return __popc(x & nib);
+}
+
 // F16HI next-hop words: bits 0-15 the next hop of an interval, kTieBit set when the interval's key
 // (its inclusive end) has a low half other than all-ones. Only such a key can be below an address
 // whose high half it shares, so only there does a high-half-only count need a second look.

@@ -427,16 +427,38 @@ int build_learned(const Intervals& iv, uint32_t span, uint32_t leaves, uint32_t 
     const double y = static_cast<double>(i);
     sx[l] += x; sy[l] += y; sxx[l] += x * x; sxy[l] += x * y; cnt[l]++;
   }
+  std::vector<double> la(P.leaves, 0.0), ls(P.leaves, 0.0);
+  for (uint32_t l = 0; l < P.leaves; l++) {
+    if (!cnt[l]) continue;
+    const double c = cnt[l];
+    const double var = sxx[l] - sx[l] * sx[l] / c;
+    const double slope = var > 0 ? std::max((sxy[l] - sx[l] * sy[l] / c) / var, 0.0) : 0.0;
+    ls[l] = slope;
+    la[l] = (sy[l] - slope * sx[l]) / c;
+  }
+  // The bound a leaf records is its largest |predicted - true rank|: shift each least-squares line
+  // to the middle of its residuals' range, which halves the spread the bound must cover when the
+  // residuals are lopsided (a step in the key distribution).
+  std::vector<double> rmin(P.leaves, 0.0), rmax(P.leaves, 0.0);
+  std::vector<uint8_t> seen(P.leaves, 0);
+  for (uint32_t i = 0; i < n; i++) {
+    const uint32_t l = leaf[i];
+    const double r = static_cast<double>(i) -
+                     (la[l] + ls[l] * static_cast<double>(khi[i] - base[l]));
+    if (!seen[l]) {
+      rmin[l] = rmax[l] = r;
+      seen[l] = 1;
+    } else {
+      rmin[l] = std::min(rmin[l], r);
+      rmax[l] = std::max(rmax[l], r);
+    }
+  }
   for (uint32_t l = 0; l < P.leaves; l++) {
     LeafModel& lm = out.leaves[l];
     if (!cnt[l]) continue;
     lm.base = base[l];
-    const double c = cnt[l];
-    const double var = sxx[l] - sx[l] * sx[l] / c;
-    const double slope = var > 0 ? (sxy[l] - sx[l] * sy[l] / c) / var : 0.0;
-    lm.s = static_cast<float>(std::max(slope, 0.0));
-    lm.a = static_cast<float>((sy[l] - slope * sx[l]) / c);
-    if (!(var > 0)) lm.a = static_cast<float>(sy[l] / c);
+    lm.s = static_cast<float>(ls[l]);
+    lm.a = static_cast<float>(la[l] + 0.5 * (rmin[l] + rmax[l]));
   }
   if (cudaMemcpyAsync(dleaves.p, out.leaves.data(), P.leaves * sizeof(LeafModel),
                       cudaMemcpyHostToDevice, st) != cudaSuccess ||

@@ -27,7 +27,8 @@
 //           high halves; the remaining D - S levels, read from L2, are descended by 8-lane
 //           groups with four addresses per group in flight, so a warp keeps 16 node fetches
 //           outstanding. The address-to-group broadcast of the paper's vector broadcast (Listing
-//           1's set1) is a warp shuffle.
+//           1's set1) is a warp shuffle. On F16HI tables (16 high halves per line) the groups are
+//           four lanes wide, each lane comparing four keys from one 32-byte load.
 //   flat    per-thread lower bound over the whole sorted key array in global memory: the GPU
 //           analogue of the paper's ablation baseline (Section 4.5, std::lower_bound).
 // All are persistent: a grid of a few CTAs per SM strides over 32-address tiles; each lane owns
@@ -416,8 +417,9 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
 // array). 16 keys per leaf make the leaf level small enough that the index over it fits one CTA's
 // shared memory at backbone size, so phase B is often the leaf line alone: one dependent L2 round
 // trip before the next hop instead of two. One 1024-thread CTA per SM holds the index; in phase B
-// lane j of an 8-lane group loads the high halves of keys 2j and 2j+1 (16 bytes, so the group's
-// loads are the node's one 128-byte line) and the count is the sum of two ballots.
+// lane j of a 4-lane group loads the high halves of keys 4j .. 4j+3 with one 32-byte load (the
+// group's four loads are the node's one 128-byte line), so one warp-wide load serves eight
+// addresses, and the count is the population of the group's nibble of four ballots.
 // Every level, the index included, counts high halves only; the next-hop word at the resulting
 // count says whether a key sharing the address's high half could still be below the address, and
 // settle_tie finishes the count then. An address's low half is read only in that case.
@@ -439,14 +441,14 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   }
 
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t g = lane >> 3;
-  const uint32_t j = lane & 7u;
-  const uint32_t gshift = g * 8u;
-  // byte g of each of two ballots, twice: the population count of the word is twice the group's
-  const uint32_t bsel = g | ((g + 4u) << 4) | (g << 8) | ((g + 4u) << 12);
+  // phase B by 4-lane groups: lane j of group g holds keys 4j .. 4j+3 of a node (one 32-byte load),
+  // so a warp works on eight nodes per load and each group has its four addresses in flight
+  const uint32_t g = lane >> 2;
+  const uint32_t j = lane & 3u;
+  const uint32_t sel = (g >> 1) | ((4u + (g >> 1)) << 4);
+  const uint32_t nib = (g & 1u) ? 0xF0F0F0F0u : 0x0F0F0F0Fu;
   const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
-  const ulonglong2* hi2 = reinterpret_cast<const ulonglong2*>(p.nodes_hi);
   const uint64_t leaf_key0 = static_cast<uint64_t>(p.internal_nodes) * 16u;
   const uint64_t nk = p.n_intervals - 1;
 
@@ -475,34 +477,32 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
     if constexpr (DB > 0) {
       uint32_t my_node = p.sidx_node + cnt;
       uint32_t my_c = 0;
-      // all eight addresses of a group in flight when only the leaf level is left; deeper
-      // descents carry node indexes across levels and take four at a time (register budget)
-      constexpr uint32_t R = DB == 1 ? 8u : static_cast<uint32_t>(kRounds);
+      // all four addresses of a group in flight when only the leaf level is left; deeper descents
+      // carry node indexes across levels and take two at a time (register budget)
+      constexpr int R = DB == 1 ? 4 : 2;
 #pragma unroll
-      for (uint32_t r0 = 0; r0 < 8; r0 += R) {
+      for (int r0 = 0; r0 < 4; r0 += R) {
         uint64_t qh[R];
         uint32_t nd[R];
 #pragma unroll
-        for (int i = 0; i < static_cast<int>(R); i++) {
-          const uint32_t src = gshift + r0 + i;
+        for (int i = 0; i < R; i++) {
+          const uint32_t src = g * 4u + r0 + i;
           qh[i] = __shfl_sync(kFull, my_hi, src);
           nd[i] = __shfl_sync(kFull, my_node, src);
         }
 #pragma unroll
         for (int l = 0; l < DB; l++) {
-          ulonglong2 kh[R];
+          Quad kq[R];
 #pragma unroll
-          for (int i = 0; i < static_cast<int>(R); i++)
-            kh[i] = __ldg(hi2 + static_cast<uint64_t>(nd[i]) * 8u + j);
+          for (int i = 0; i < R; i++)
+            kq[i] = ldg_quad(p.nodes_hi + static_cast<uint64_t>(nd[i]) * 16u + j * 4u);
 #pragma unroll
-          for (int i = 0; i < static_cast<int>(R); i++) {
-            const uint32_t c = __popc(__byte_perm(__ballot_sync(kFull, kh[i].x < qh[i]),
-                                                  __ballot_sync(kFull, kh[i].y < qh[i]), bsel)) >>
-                               1;
+          for (int i = 0; i < R; i++) {
+            const uint32_t c = quad_count(kq[i], qh[i], sel, nib);
             if (l + 1 < DB) {
               nd[i] = nd[i] * 17u + 1u + c;
-            } else if (j == r0 + i) {
-              my_node = nd[i];
+            } else if (j == static_cast<uint32_t>(r0 + i)) {
+              if (DB > 1) my_node = nd[i];   // (one level: the lane's own node already)
               my_c = c;
             }
           }
