@@ -18,8 +18,8 @@ namespace {
 // radix directory of each table it meets in shared memory — keeping them while its next item is
 // in the same table; an index larger than the launch's share is searched in place in global
 // memory instead — and runs the hybrid descent of lookup_hybrid: phase A over the index, then
-// the table's remaining DB levels from L2 by 8-lane groups, writing each result at its bucketed
-// position. The tile code is instantiated per (DB, format) and picked per table; depths beyond
+// the table's remaining DB levels from L2 by lane groups (8 lanes on F8 tables, 4 lanes with
+// 32-byte loads on F16HI tables), writing each result at its bucketed position. The tile code is instantiated per (DB, format) and picked per table; depths beyond
 // kMultiMaxDb take a run-time level loop. Addresses with an id beyond the tables (after range[T])
 // are left to the gather that follows.
 constexpr int kMultiMaxDb = 4;
@@ -147,7 +147,6 @@ __device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* U
                                            const uint64_t* __restrict__ xhi,
                                            const uint64_t* __restrict__ xlo,
                                            uint16_t* __restrict__ out, uint32_t* status) {
-  const ulonglong2* hi2 = static_cast<const ulonglong2*>(d.nodes);
   const uint64_t leaf_key0 = static_cast<uint64_t>(d.internal_nodes) * 16u;
   const uint64_t* keys_hi = static_cast<const uint64_t*>(d.nodes) + leaf_key0;
   const uint64_t* keys_lo = d.nodes_lo + leaf_key0;
@@ -156,10 +155,12 @@ __device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* U
   const uint32_t N = d.sidx_n;
   const uint32_t db = DB >= 0 ? static_cast<uint32_t>(DB) : d.db;
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t g = lane >> 3;
-  const uint32_t j = lane & 7u;
-  const uint32_t gshift = g * 8u;
-  const uint32_t bsel = g | ((g + 4u) << 4) | (g << 8) | ((g + 4u) << 12);
+  // 4-lane groups: lane j of group g holds keys 4j .. 4j+3 of a node (one 32-byte load)
+  const uint32_t g = lane >> 2;
+  const uint32_t j = lane & 3u;
+  const uint32_t sel = (g >> 1) | ((4u + (g >> 1)) << 4);
+  const uint32_t nib = (g & 1u) ? 0xF0F0F0F0u : 0x0F0F0F0Fu;
+  const uint64_t* keys16 = static_cast<const uint64_t*>(d.nodes);
   const uint32_t wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (uint64_t base = s0 + static_cast<uint64_t>(wid) * 32u; base < s1; base += nw * 32u) {
     const uint64_t mine = base + lane;
@@ -175,30 +176,30 @@ __device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* U
     if (db > 0) {
       uint32_t my_node = d.sidx_node + cnt;
       uint32_t my_c = 0;
+      // one level left: all four addresses of a group in flight; deeper: two at a time
+      constexpr int R = DB == 1 ? 4 : 2;
 #pragma unroll
-      for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
-        uint64_t qh[kRounds];
-        uint32_t nd[kRounds];
+      for (int r0 = 0; r0 < 4; r0 += R) {
+        uint64_t qh[R];
+        uint32_t nd[R];
 #pragma unroll
-        for (int i = 0; i < kRounds; i++) {
-          const uint32_t src = gshift + r0 + i;
+        for (int i = 0; i < R; i++) {
+          const uint32_t src = g * 4u + r0 + i;
           qh[i] = __shfl_sync(kFull, my_hi, src);
           nd[i] = __shfl_sync(kFull, my_node, src);
         }
 #pragma unroll
         for (uint32_t l = 0; l < db; l++) {
-          ulonglong2 kh[kRounds];
+          Quad kq[R];
 #pragma unroll
-          for (int i = 0; i < kRounds; i++)
-            kh[i] = __ldg(hi2 + static_cast<uint64_t>(nd[i]) * 8u + j);
+          for (int i = 0; i < R; i++)
+            kq[i] = ldg_quad(keys16 + static_cast<uint64_t>(nd[i]) * 16u + j * 4u);
 #pragma unroll
-          for (int i = 0; i < kRounds; i++) {
-            const uint32_t c = __popc(__byte_perm(__ballot_sync(kFull, kh[i].x < qh[i]),
-                                                  __ballot_sync(kFull, kh[i].y < qh[i]), bsel)) >>
-                               1;
+          for (int i = 0; i < R; i++) {
+            const uint32_t c = quad_count(kq[i], qh[i], sel, nib);
             if (l + 1 < db) {
               nd[i] = nd[i] * 17u + 1u + c;
-            } else if (j == r0 + i) {
+            } else if (j == static_cast<uint32_t>(r0 + i)) {
               my_node = nd[i];
               my_c = c;
             }
