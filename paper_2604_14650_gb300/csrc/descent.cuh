@@ -23,6 +23,42 @@ __device__ __forceinline__ void report(uint32_t* status, uint32_t code) {
 }
 #endif
 
+// Copies the high halves of index entries [0, n) (16-byte (high, low) entries in global memory)
+// and the radix directory (dn u16 words) into shared memory, each thread with eight loads in
+// flight, so an index of a few hundred KB arrives in a few L2 round trips rather than one per
+// 8 bytes a thread copies. Ends with a barrier.
+__device__ __forceinline__ void stage_index(uint64_t* Uh, const ulonglong2* sidx, uint32_t n,
+                                            uint16_t* Dir, const uint16_t* dir, uint32_t dn) {
+  constexpr uint32_t U = 8;
+  for (uint32_t i0 = threadIdx.x; i0 < n; i0 += U * blockDim.x) {
+    uint64_t v[U];
+#pragma unroll
+    for (uint32_t k = 0; k < U; k++) {
+      const uint32_t i = i0 + k * blockDim.x;
+      v[k] = i < n ? __ldg(&sidx[i].x) : 0ull;
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < U; k++) {
+      const uint32_t i = i0 + k * blockDim.x;
+      if (i < n) Uh[i] = v[k];
+    }
+  }
+  for (uint32_t i0 = threadIdx.x; i0 < dn; i0 += U * blockDim.x) {
+    uint16_t v[U];
+#pragma unroll
+    for (uint32_t k = 0; k < U; k++) {
+      const uint32_t i = i0 + k * blockDim.x;
+      v[k] = i < dn ? __ldg(dir + i) : uint16_t(0);
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < U; k++) {
+      const uint32_t i = i0 + k * blockDim.x;
+      if (i < dn) Dir[i] = v[k];
+    }
+  }
+  __syncthreads();
+}
+
 // Number of entries of the sorted array a[0..n) that are below x (n >= 1), branch-free with a
 // trip count that depends on n only (Khuong and Morin's branchless binary search).
 template <class Load>

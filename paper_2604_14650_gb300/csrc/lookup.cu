@@ -233,12 +233,9 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   // a small launch searches the index in place instead of staging it (decided by the host;
   // the learned and multi-table forms always stage)
   const bool staged = LEARNED || MULTI || p.staged != 0;
-  if (staged)
-    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
   uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((N + 1u) & ~1u));
   const uint32_t dn = p.dir_bits ? (1u << p.dir_bits) + 1u : 0u;
-  if (staged)
-    for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(p.dir + i);
+  if (staged) stage_index(Uh, p.sidx, N, Dir, p.dir, dn);
   LeafModel* Lm = reinterpret_cast<LeafModel*>(Dir + ((dn + 7u) & ~7u));
   uint16_t* Le = reinterpret_cast<uint16_t*>(Lm + (LEARNED ? p.lp.leaves : 0u));
   if (LEARNED) {
@@ -433,12 +430,8 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
   uint16_t* Dir = reinterpret_cast<uint16_t*>(Uh + ((N + 1u) & ~1u));
   // a small launch searches the index in place instead of staging it (decided by the host)
   const bool staged = MULTI || p.staged != 0;
-  if (staged) {
-    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) Uh[i] = __ldg(&p.sidx[i].x);
-    const uint32_t dn = p.dir_bits ? (1u << p.dir_bits) + 1u : 0u;
-    for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(p.dir + i);
-    __syncthreads();
-  }
+  if (staged)
+    stage_index(Uh, p.sidx, N, Dir, p.dir, p.dir_bits ? (1u << p.dir_bits) + 1u : 0u);
 
   const uint32_t lane = threadIdx.x & 31u;
   // phase B by 4-lane groups: lane j of group g holds keys 4j .. 4j+3 of a node (one 32-byte load),

@@ -263,13 +263,12 @@ __global__ void __launch_bounds__(512, 2)
         if (threadIdx.x == 0) d = desc[t];
         __syncthreads();
         if (d.staged) {
-          const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
-          for (uint32_t i = threadIdx.x; i < d.sidx_n; i += blockDim.x) Uh[i] = __ldg(&sidx[i].x);
           Dir = reinterpret_cast<uint16_t*>(Uh + ((d.sidx_n + 1u) & ~1u));
-          const uint32_t dn = d.dir_bits ? (1u << d.dir_bits) + 1u : 0u;
-          for (uint32_t i = threadIdx.x; i < dn; i += blockDim.x) Dir[i] = __ldg(d.dir + i);
+          stage_index(Uh, reinterpret_cast<const ulonglong2*>(d.sidx), d.sidx_n, Dir, d.dir,
+                      d.dir_bits ? (1u << d.dir_bits) + 1u : 0u);
+        } else {
+          __syncthreads();
         }
-        __syncthreads();
         staged = t;
       }
       const uint32_t sel = d.db <= static_cast<uint32_t>(kMultiMaxDb) ? d.db : 15u;
