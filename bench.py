@@ -820,7 +820,7 @@ def block_learned1m(args, stream, steps, warmup, lookups=1 << 28):
             "best_plain": best_plain,
             "best_plain_B_lookups_per_s": res[best_plain]["B_lookups_per_s"],
             "roofline": _hbm_roofline(HBM_BYTES_PER_LOOKUP, n, lv["ms_per_launch"],
-                                      "lookup_hybrid<3, 0, 1, 0, 0>"),
+                                      f"lookup_hybrid<{lv['levels_from_l2']}, 0, 1, 0, 0>"),
             "variants": res, "sampled_parity_vs_oracle": parity,
             "all_variants_equal": all(v["same_results_as_learned"] for v in res.values())}
 
@@ -903,48 +903,19 @@ def block_vrf64(args, stream, steps, warmup, lookups=1 << 27, fmt="f16hi"):
 
 
 def run_learned1m(args):
-    """Config L: 1M prefixes (1 % /128), 2^28 lookups; learned kernel against the plain tree."""
+    """Config L: 1M prefixes (1 % /128), 2^28 lookups; the learned kernel against the plain tree
+    forms on the same table and addresses (the block the default line carries, as its own line)."""
     import torch
-    import paper_2604_14650_gb300 as pb
-    import synth
     torch.cuda.set_device(0)
-    f = synth.gen_fib(1_000_000, seed=args.seed, nh_max=4095)
-    n = args.lookups
-    xh, xl = synth.gen_trace(f, n, seed=args.seed + 1)
-    d_hi = torch.from_numpy(xh.view(np.int64)).cuda()
-    d_lo = torch.from_numpy(xl.view(np.int64)).cuda()
-    d_out = torch.empty(n, dtype=torch.int16, device="cuda")
     stream = torch.cuda.Stream()
-    res = {}
-    ref = None
-    for name, kw in (("learned", dict(kernel="learned")), ("plain_hybrid", dict(kernel="hybrid")),
-                     ("plain_coop", dict(kernel="coop"))):
-        with pb.Fib(f.hi, f.lo, f.len, f.nh, **kw) as fib:
-            for _ in range(args.warmup):
-                fib.lookup_ptr(d_hi.data_ptr(), d_lo.data_ptr(), n, d_out.data_ptr(), stream)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(args.steps):
-                fib.lookup_ptr(d_hi.data_ptr(), d_lo.data_ptr(), n, d_out.data_ptr(), stream)
-            b.record(stream)
-            stream.synchronize()
-            st = fib.stats()
-            res[name] = {"B_lookups_per_s": n * args.steps / a.elapsed_time(b) / 1e6,
-                         "depth": st["depth"], "smem_levels": st["smem_levels"],
-                         **{k: st[k] for k in st if k.startswith("model_")}}
-            if ref is None:
-                ref = d_out.clone()
-            res[name]["same_results_as_learned"] = bool(torch.equal(ref, d_out))
-    import oracle
-    idx = np.random.default_rng(2).integers(0, n, 1 << 16)
-    want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh[idx], xl[idx])
-    parity = bool(np.array_equal(ref.cpu().numpy().view(np.uint16)[idx], want))
+    b = block_learned1m(args, stream, args.steps, args.warmup, lookups=args.lookups)
     print(json.dumps({"metric": "B lookups/s, 1M-prefix FIB, learned vs plain tree",
-                      "value": res["learned"]["B_lookups_per_s"], "unit": UNIT, "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-                      "dtype": "u64", "data": "synthetic (seeded)",
-                      "config": {"workload": f"1,000,000-prefix synthetic FIB, {n} lookups"},
-                      "variants": res, "sampled_parity_vs_oracle": parity}), flush=True)
+                      "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "higher_is_better": True, "dtype": "u64",
+                      "data": "synthetic (seeded)", "config": {"workload": b["workload"]},
+                      **{k: v for k, v in b.items() if k not in ("workload", "value", "unit",
+                                                                 "steps", "warmup")}}),
+          flush=True)
     return 0
 
 
