@@ -599,7 +599,8 @@ def run_planb(args):
         es, ew = args.extra_steps, 3
         extra = {"learned1m": block_learned1m(args, stream, es, ew),
                  "vrf64": block_vrf64(args, stream, es, ew),
-                 "zipf": block_zipf(args, stream, es, ew, fib_in=fib_in)}
+                 "zipf": block_zipf(args, stream, es, ew, fib_in=fib_in),
+                 "serve": block_serve(args)}
         torch.cuda.empty_cache()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -919,7 +920,7 @@ def run_learned1m(args):
     return 0
 
 
-def run_serve(args):
+def serve_line(args):
     """Serving: Poisson arrivals of requests (32..65,536 addresses, log-uniform) over the 64 VRF
     tables (table drawn proportional to size), route updates at --update-rate changes per second
     applied while serving, latency from submit to results in place."""
@@ -944,12 +945,38 @@ def run_serve(args):
     budget = int(sum(f.stats()["node_bytes"] + f.stats()["value_bytes"] for f in fibs) * 1.05)
     srv = pb.Server(slots=4, max_batch=1 << 18, mem_budget=budget, per_table=args.per_table)
     try:
-        return _serve_loop(args, srv, fibs, fibs_in, pools, nreq, tabs, lens, offs, gaps, rng,
+        line = _serve_loop(args, srv, fibs, fibs_in, pools, nreq, tabs, lens, offs, gaps, rng,
                            budget)
     finally:
         srv.close()
         for f in fibs:
             f.close()
+    return line
+
+
+def block_serve(args, rate=20000.0, duration=2.0, warmup=0.5):
+    """The serving loop on the 64 VRF tables (device builder for the rebuilds), Poisson arrivals at
+    `rate` requests per second for `duration` seconds after `warmup` seconds of the same load,
+    1,000 route changes per second applied while serving."""
+    import copy
+    a = copy.copy(args)
+    a.rate, a.duration, a.serve_warmup, a.update_rate = rate, duration, warmup, 1000.0
+    a.builder, a.per_table, a.format, a.tables = "device", False, "f16hi", 64
+    line = serve_line(a)
+    return {"workload": line["config"]["workload"], "value": line["value"], "unit": UNIT,
+            "latency_us": line["latency_us"], "batch_us": line["batch_us"],
+            "requests_per_s": line["requests_per_s"], "mean_batch": line["mean_batch"],
+            "updates_applied": line["updates_applied"], "rebuilds": line["rebuilds"],
+            "rebuild_ms_mean": line["rebuild_ms_mean"], "graph_captures": line["graph_captures"],
+            "requests_not_completed": line["requests_not_completed"],
+            "last_error": line["last_error"],
+            "parity": "each result equal alone, in the mix and to the oracle: "
+                      "tests/test_gpu_server.py"}
+
+
+def run_serve(args):
+    print(json.dumps(serve_line(args)), flush=True)
+    return 0
 
 
 def _serve_loop(args, srv, fibs, fibs_in, pools, nreq, tabs, lens, offs, gaps, rng, budget):
@@ -1035,8 +1062,7 @@ def _serve_loop(args, srv, fibs, fibs_in, pools, nreq, tabs, lens, offs, gaps, r
             "updates_applied": st["updates"], "rebuilds": st["update_batches"],
             "rebuild_ms_mean": st["rebuild_ms_mean"], "last_error": st["last_error"],
             "last_error_detail": detail, "requests_not_completed": failed}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_build(args):

@@ -274,7 +274,7 @@ typedef struct planb_multi planb_multi; /* several tables (VRFs) served by one c
  * addresses each carry a u8 table id. The paper serves one table; many tables per box are the
  * same lookup applied per table. fibs: n_tables table handles (1..255), not owned: they must
  * outlive the group; updates to them are picked up by later lookups. max_batch: most addresses per
- * planb_multi_lookup call (< 2^32); the group owns about max_batch x 20.2 bytes of device scratch
+ * planb_multi_lookup call (< 2^32); the group owns about max_batch x 16.2 bytes of device scratch
  * (plus about 3 bytes per address per 1,000 tables).
  * Tables built with PLANB_KERNEL_LEARNED cannot join a group. flags: 0, or an OR of the
  * PLANB_MULTI_* flags below. Errors: PLANB_EINVAL, PLANB_ENOMEM, PLANB_ECUDA.

@@ -1035,7 +1035,8 @@ struct planb_multi {
   size_t cap = 0;
   uint32_t G = 0;                // bucketing chunks
   void* mem = nullptr;
-  uint64_t *bhi = nullptr, *blo = nullptr, *range = nullptr;
+  uint64_t *bhi = nullptr, *range = nullptr;
+  uint32_t* bsrc = nullptr;       // input position of each bucketed address
   uint16_t* where = nullptr;      // each address's slot in its bucketing tile
   uint32_t* counts = nullptr;
   uint32_t* tile_start = nullptr; // per bucketing tile and table: run start in the bucketed arrays
@@ -1071,9 +1072,9 @@ namespace {
 int multi_pipeline(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cur,
                    const uint64_t* d_addr_hi, const uint64_t* d_addr_lo, const uint8_t* d_table,
                    size_t n, uint16_t* d_out, cudaStream_t s, const uint64_t* d_n, bool fork) {
-  int rc = planb::launch_bucketing(d_addr_hi, d_addr_lo, d_table, n, m->T, m->G, m->counts,
-                                   m->range, m->bhi, m->blo, m->where, m->tile_start,
-                                   m->tile_base, s, d_n);
+  int rc = planb::launch_bucketing(d_addr_hi, d_table, n, m->T, m->G, m->counts, m->range,
+                                   m->bhi, m->bsrc, m->where, m->tile_start, m->tile_base, s,
+                                   d_n);
   if (rc) return fail_detail(rc, "multi: bucketing", cudaGetLastError());
   cudaError_t e = cudaSuccess;
   fork = fork && !m->persist;
@@ -1085,15 +1086,16 @@ int multi_pipeline(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cu
   }
   if (m->persist) {
     rc = planb::launch_multi_persistent(
-        m->desc, m->T, m->range, m->bhi, m->blo, m->bres,
+        m->desc, m->T, m->range, m->bhi, d_addr_lo, m->bsrc, m->bres,
         reinterpret_cast<unsigned long long*>(m->range + 2 * m->T + 3), m->fibs[0]->d_status,
         m->persist_ctas, m->persist_smem, s);
     if (rc) return fail_detail(rc, "multi: persistent lookup", cudaGetLastError());
   } else {
     for (uint32_t t = 0; t < m->T; t++) {
-      rc = planb::launch_lookup(cur[t]->dt, cur[t]->cfg, m->bhi, m->blo, n, m->bres,
+      rc = planb::launch_lookup(cur[t]->dt, cur[t]->cfg, m->bhi, d_addr_lo, n, m->bres,
                                 m->fibs[t]->d_status,
-                                fork ? m->side[t % planb_multi::kBranches] : s, m->range + t);
+                                fork ? m->side[t % planb_multi::kBranches] : s, m->range + t,
+                                m->bsrc);
       if (rc) return fail_detail(rc, "multi: table lookup", cudaGetLastError());
     }
   }
@@ -1145,7 +1147,7 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     const size_t cap = max_batch;
     auto up = [](size_t x) { return ((x + 255) / 256) * 256; };
     const size_t tiles = planb::bucketing_tiles(cap, m->G) * (m->T + 1);
-    const size_t where_off = cap * 16, bres_off = where_off + up(cap * 2),
+    const size_t where_off = up(cap * 12), bres_off = where_off + up(cap * 2),
                  counts_off = bres_off + up(cap * 2),
                  range_off = counts_off + up(static_cast<size_t>(m->T + 1) * m->G * 4);
     const size_t desc_off = range_off + up((2 * m->T + 4) * 8);
@@ -1159,7 +1161,7 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     }
     char* b = static_cast<char*>(m->mem);
     m->bhi = reinterpret_cast<uint64_t*>(b);
-    m->blo = m->bhi + cap;
+    m->bsrc = reinterpret_cast<uint32_t*>(b + up(cap * 8));
     m->where = reinterpret_cast<uint16_t*>(b + where_off);
     m->tile_start = reinterpret_cast<uint32_t*>(b + tstart_off);
     m->tile_base = reinterpret_cast<uint16_t*>(b + tbase_off);

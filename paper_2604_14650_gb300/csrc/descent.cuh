@@ -81,13 +81,23 @@ __device__ __forceinline__ uint32_t count_below(Load load, uint32_t n, uint64_t 
 // An address's low half, read from memory the first time a comparison needs it (only when a key's
 // high half equals the address's, which is rare), so the common lookup reads 8 bytes of address.
 // (The address of the low half is passed to each get() rather than kept, to spare registers.)
+// Where an address's low half lives: entry j of lo, or — for a multi-table launch over bucketed
+// addresses — entry src[j] of the batch's input-order low halves, the bucketing having recorded
+// each bucketed slot's input position instead of copying its low half. Only ptr() touches src.
+struct LoRef {
+  const uint64_t* lo;
+  const uint32_t* src;
+  uint64_t j;
+  __device__ __forceinline__ const uint64_t* ptr() const { return lo + (src ? src[j] : j); }
+};
+
 struct LazyLo {
   uint64_t v;
   bool have;
   __device__ __forceinline__ explicit LazyLo(bool ok) : v(0), have(!ok) {}
-  __device__ __forceinline__ uint64_t get(const uint64_t* src) {
+  __device__ __forceinline__ uint64_t get(const LoRef& r) {
     if (!have) {
-      v = *src;
+      v = *r.ptr();
       have = true;
     }
     return v;
@@ -100,7 +110,7 @@ __device__ __forceinline__ uint32_t index_count_global(const ulonglong2* sidx, u
                                                        const uint16_t* dir, uint32_t dir_bits,
                                                        uint32_t dir_shift, uint64_t dir_base,
                                                        uint64_t my_hi, LazyLo& my_lo,
-                                                       const uint64_t* lo_src) {
+                                                       const LoRef& lo_src) {
   uint32_t lo = 0, n = N;
   if (dir_bits) {
     const uint64_t v = my_hi >> dir_shift;
@@ -245,7 +255,7 @@ __device__ __forceinline__ uint32_t index_count(const uint64_t* Uh, uint32_t N,
                                                 const uint16_t* Dir, uint32_t dir_bits,
                                                 uint32_t dir_shift, uint64_t dir_base,
                                                 const ulonglong2* sidx, uint64_t my_hi,
-                                                LazyLo& my_lo, const uint64_t* lo_src) {
+                                                LazyLo& my_lo, const LoRef& lo_src) {
   uint32_t lo = 0, n = N;
   if (dir_bits) {
     const uint64_t v = my_hi >> dir_shift;

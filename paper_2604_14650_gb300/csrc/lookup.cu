@@ -73,7 +73,8 @@ struct KParams {
   uint32_t dir_bits, dir_shift;
   uint64_t dir_base;
   const uint64_t* range;      // multi-table: device [begin, end) of this launch's addresses
-  const uint32_t* perm;       // multi-table: result of address j goes to out[perm[j]]
+  const uint32_t* src;        // multi-table: input position of bucketed address j; xlo is then
+                              // the batch's input-order low halves, read at src[j] on a tie
 };
 
 // The addresses a launch handles: [0, n), or the device-side range a bucketing pass wrote.
@@ -90,7 +91,13 @@ __device__ __forceinline__ Seg segment(const KParams& p) {
 
 template <bool MULTI = true>
 __device__ __forceinline__ void store_out(const KParams& p, uint64_t j, uint16_t v) {
-  p.out[(MULTI && p.perm) ? p.perm[j] : j] = v;
+  p.out[j] = v;
+}
+
+// The low half of address j of a launch (j counted from the start of the address arrays).
+template <bool MULTI>
+__device__ __forceinline__ LoRef lo_ref(const KParams& p, uint64_t j) {
+  return LoRef{p.xlo, MULTI ? p.src : nullptr, j};
 }
 
 // ------------------------------------------------------------------------------- coop F8X128
@@ -115,7 +122,7 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f8(const KParams p) {
     const uint64_t mine = base + lane;
     const bool ok = mine < seg.n;
     const uint64_t my_hi = ok ? p.xhi[seg.off + mine] : 0ull;
-    const uint64_t my_lo = ok ? p.xlo[seg.off + mine] : 0ull;
+    const uint64_t my_lo = ok ? *lo_ref<true>(p, seg.off + mine).ptr() : 0ull;
     uint32_t result = 0;
 #pragma unroll
     for (uint32_t r = 0; r < 8; r++) {
@@ -174,7 +181,7 @@ __global__ void __launch_bounds__(256, 4) lookup_coop_f16(const KParams p) {
     const uint64_t mine = base + lane;
     const bool ok = mine < seg.n;
     const uint64_t my_hi = ok ? p.xhi[seg.off + mine] : 0ull;
-    const uint64_t my_lo = ok ? p.xlo[seg.off + mine] : 0ull;
+    const uint64_t my_lo = ok ? *lo_ref<true>(p, seg.off + mine).ptr() : 0ull;
     uint32_t result = 0;
 #pragma unroll 4
     for (uint32_t r = 0; r < 16; r++) {
@@ -281,7 +288,7 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
       my_lo.v = nx_lo;
       my_lo.have = true;
     }
-    const uint64_t* lo_src = p.xlo + seg.off + mine;
+    const LoRef lo_src = lo_ref<MULTI>(p, seg.off + mine);
     {
       const uint64_t next = mine + nwarps * 32;
       nx_hi = next < seg.n ? p.xhi[seg.off + next] : 0ull;
@@ -460,7 +467,6 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
 
   const Seg seg = segment<MULTI>(p);
   const uint64_t* xhi = p.xhi + seg.off;
-  const uint64_t* xlo = p.xlo + seg.off;
   uint64_t nx_hi = 0;
   {
     const uint64_t first = warp * 32 + lane;
@@ -523,9 +529,9 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
     }
 #endif
     uint32_t w = __ldg(p.nh_tie + rank);
-    const uint64_t* lo_src = xlo + mine;
+    const LoRef lo_src = lo_ref<MULTI>(p, seg.off + mine);
     w = settle_tie(p.nodes_hi + leaf_key0, p.nodes_lo + leaf_key0, nk, p.nh_tie, rank, w, my_hi,
-                   [lo_src, ok] { return ok ? *lo_src : 0ull; });
+                   [&lo_src, ok] { return ok ? *lo_src.ptr() : 0ull; });
     if (ok) store_out<MULTI>(p, seg.off + mine, static_cast<uint16_t>(w));
   }
 }
@@ -539,7 +545,7 @@ __global__ void __launch_bounds__(256) lookup_flat(const KParams p) {
   const Seg seg = segment(p);
   for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < seg.n;
        i += stride) {
-    const uint64_t xh = p.xhi[seg.off + i], xl = p.xlo[seg.off + i];
+    const uint64_t xh = p.xhi[seg.off + i], xl = *lo_ref<true>(p, seg.off + i).ptr();
     uint32_t rank = nk ? count_below(gload, nk, xh, xl) : 0u;
 #ifdef PLANB_BOUNDS_CHECK
     if (rank >= p.n_intervals) {
@@ -575,9 +581,21 @@ KernelFn kernel_for(const DevTable& t, bool multi = false, bool lazy = false) {
   static const KernelFn hyb[2][2][kMaxDepth + 1] = {
       {PLANB_HYB(false, false, false), PLANB_HYB(false, true, false)},
       {PLANB_HYB(true, false, false), PLANB_HYB(true, true, false)}};
-  static const KernelFn hyb_multi[2][kMaxDepth + 1] = {PLANB_HYB(false, false, true),
-                                                       PLANB_HYB(true, false, true)};
 #undef PLANB_HYB
+#define PLANB_HYB_MULTI(P)                                                                      \
+  {                                                                                               \
+    lookup_hybrid<0, P, false, true, true>, lookup_hybrid<1, P, false, true, true>,              \
+        lookup_hybrid<2, P, false, true, true>, lookup_hybrid<3, P, false, true, true>,          \
+        lookup_hybrid<4, P, false, true, true>, lookup_hybrid<5, P, false, true, true>,          \
+        lookup_hybrid<6, P, false, true, true>, lookup_hybrid<7, P, false, true, true>,          \
+        lookup_hybrid<8, P, false, true, true>, lookup_hybrid<9, P, false, true, true>,          \
+        lookup_hybrid<10, P, false, true, true>                                                   \
+  }
+  // multi-table launches read an address's low half only on a tie (through the bucketing's
+  // input positions), as the host-memory form does
+  static const KernelFn hyb_multi[2][kMaxDepth + 1] = {PLANB_HYB_MULTI(false),
+                                                       PLANB_HYB_MULTI(true)};
+#undef PLANB_HYB_MULTI
 #define PLANB_HYB_LAZY(P)                                                                       \
   {                                                                                               \
     lookup_hybrid<0, P, false, false, true>, lookup_hybrid<1, P, false, false, true>,            \
@@ -700,10 +718,10 @@ int plan_launch(const DevTable& t, int device, int threads, int ctas_per_sm, Lau
 
 int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   const uint64_t* d_lo, size_t n, uint16_t* d_out, uint32_t* d_status,
-                  void* stream, const uint64_t* d_range, const uint32_t* d_perm,
+                  void* stream, const uint64_t* d_range, const uint32_t* d_src,
                   bool lazy_lo) {
   if (n == 0) return PLANB_OK;
-  const bool multi = d_range != nullptr || d_perm != nullptr;
+  const bool multi = d_range != nullptr;
   if (multi && t.kernel == kLearned) return PLANB_EINVAL;   // no multi-table form
   KernelFn fn = kernel_for(t, multi, lazy_lo && !multi);
   if (!fn) return PLANB_EINVAL;
@@ -735,7 +753,7 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   p.dir_shift = t.dir_shift;
   p.dir_base = t.dir_base;
   p.range = d_range;
-  p.perm = d_perm;
+  p.src = d_src;
   uint64_t blocks;
   int threads = cfg.threads;
   size_t smem = cfg.smem_bytes;

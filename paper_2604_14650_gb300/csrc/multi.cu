@@ -3,7 +3,9 @@
 // A batch whose addresses carry a u8 table id is grouped by table with a two-pass counting sort
 // over fixed chunks of the batch: each chunk's histogram (shared-memory counters), one scan that
 // turns the (table, chunk) counts into output offsets in table-major order, and a scatter that
-// copies each address to its table's segment and records, in input order, where it went. Each
+// copies each address's high half to its table's segment, beside its input position (the lookup
+// reads the low half from the input, through that position, only when a count needs it), and
+// records, in input order, where it went. Each
 // table's lookup then reads its segment contiguously (its table stays L2-resident while it runs)
 // and writes its results contiguously in bucketed order; a final gather in input order reads each
 // address's result back through the recorded position. Both the scatter's and the gather's
@@ -132,21 +134,21 @@ constexpr int kScatterThreads = 256;
 constexpr int kScatterItems = 8;
 constexpr int kTile = kScatterThreads * kScatterItems;
 constexpr size_t kScatterSmem =
-    2 * 2 * kTile * sizeof(uint64_t) + kTile * sizeof(uint16_t) + kTile * sizeof(uint8_t);
+    2 * kTile * sizeof(uint64_t) + kTile * sizeof(uint16_t) + kTile * sizeof(uint8_t);
 
 __global__ void __launch_bounds__(kScatterThreads)
-    mt_scatter_kernel(const uint64_t* __restrict__ hi, const uint64_t* __restrict__ lo,
-                      const uint8_t* __restrict__ tid, uint64_t n, uint32_t T, uint64_t chunk,
+    mt_scatter_kernel(const uint64_t* __restrict__ hi, const uint8_t* __restrict__ tid,
+                      uint64_t n, uint32_t T, uint64_t chunk,
                       const uint32_t* __restrict__ offsets, const uint64_t* __restrict__ range,
-                      uint64_t* __restrict__ bhi, uint64_t* __restrict__ blo,
+                      uint64_t* __restrict__ bhi, uint32_t* __restrict__ bsrc,
                       uint16_t* __restrict__ where, uint32_t* __restrict__ tile_start,
                       uint16_t* __restrict__ tile_base, const uint64_t* __restrict__ d_n) {
   typedef cub::BlockScan<uint32_t, kScatterThreads> Scan;
   __shared__ typename Scan::TempStorage scan_tmp;
   __shared__ uint32_t cur[256], cnt[256], base[256];
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* s_in = reinterpret_cast<uint64_t*>(smem_raw);   // [buffer][high, low][kTile]
-  uint16_t* s_src = reinterpret_cast<uint16_t*>(s_in + 4 * kTile);   // input index per slot
+  uint64_t* s_in = reinterpret_cast<uint64_t*>(smem_raw);   // [buffer][kTile] high halves
+  uint16_t* s_src = reinterpret_cast<uint16_t*>(s_in + 2 * kTile);   // input index per slot
   uint8_t* s_t = reinterpret_cast<uint8_t*>(s_src + kTile);           // table per slot
   batch_shape(d_n, n, chunk);
   for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x)
@@ -159,12 +161,8 @@ __global__ void __launch_bounds__(kScatterThreads)
   auto issue = [&](uint64_t tb, uint32_t b) {
     if (tb < b1) {
       const uint64_t m = b1 - tb < static_cast<uint64_t>(kTile) ? b1 - tb : kTile;
-      uint64_t* dh = s_in + (2u * b) * kTile;
-      uint64_t* dl = dh + kTile;
-      for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
-        cp_async8(dh + k, hi + tb + k);
-        cp_async8(dl + k, lo + tb + k);
-      }
+      uint64_t* dh = s_in + b * kTile;
+      for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) cp_async8(dh + k, hi + tb + k);
     }
     cp_async_commit();
   };
@@ -221,14 +219,13 @@ __global__ void __launch_bounds__(kScatterThreads)
     cp_async_wait<1>();   // this tile's copies (all groups but the newest) have landed
     __syncthreads();
     const uint32_t m = static_cast<uint32_t>(b1 - tb < kTile ? b1 - tb : kTile);
-    const uint64_t* sh = s_in + (2u * buf) * kTile;
-    const uint64_t* sl = sh + kTile;
+    const uint64_t* sh = s_in + buf * kTile;
     for (uint32_t slot = threadIdx.x; slot < m; slot += blockDim.x) {
       const uint32_t t = s_t[slot];
       const uint32_t pos = cur[t] + (slot - base[t]);
       const uint32_t src = s_src[slot];
       bhi[pos] = sh[src];
-      blo[pos] = sl[src];
+      bsrc[pos] = static_cast<uint32_t>(tb) + src;   // n < 2^32
     }
     __syncthreads();
     for (uint32_t t = threadIdx.x; t <= T; t += blockDim.x) cur[t] += cnt[t];
@@ -302,9 +299,9 @@ size_t bucketing_tiles(size_t cap, uint32_t G) {
   return static_cast<size_t>(G) * ((chunk + kTile - 1) / kTile);
 }
 
-int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
+int launch_bucketing(const uint64_t* d_hi, const uint8_t* d_tid, size_t n,
                      uint32_t T, uint32_t G, uint32_t* d_counts, uint64_t* d_range,
-                     uint64_t* d_bhi, uint64_t* d_blo, uint16_t* d_where,
+                     uint64_t* d_bhi, uint32_t* d_bsrc, uint16_t* d_where,
                      uint32_t* d_tile_start, uint16_t* d_tile_base, void* stream,
                      const uint64_t* d_n) {
   if (T == 0 || T > 255 || G == 0 || n >= (uint64_t(1) << 32)) return PLANB_EINVAL;
@@ -318,7 +315,7 @@ int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* 
   mt_tablescan_kernel<<<1, 256, 0, st>>>(
       totals, T, d_range, reinterpret_cast<unsigned long long*>(d_range + 2 * T + 3));
   mt_scatter_kernel<<<G, kScatterThreads, kScatterSmem, st>>>(
-      d_hi, d_lo, d_tid, n, T, chunk, d_counts, d_range, d_bhi, d_blo, d_where, d_tile_start,
+      d_hi, d_tid, n, T, chunk, d_counts, d_range, d_bhi, d_bsrc, d_where, d_tile_start,
       d_tile_base, d_n);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }

@@ -29,6 +29,7 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
                                          const uint16_t* Dir, uint64_t s0, uint64_t s1,
                                          const uint64_t* __restrict__ xhi,
                                          const uint64_t* __restrict__ xlo,
+                                         const uint32_t* __restrict__ src,
                                          uint16_t* __restrict__ out, uint32_t* status) {
   const ulonglong2* nodes = static_cast<const ulonglong2*>(d.nodes);
   const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
@@ -45,13 +46,14 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
     const bool ok = mine < s1;
     const uint64_t my_hi = ok ? xhi[mine] : 0ull;
     LazyLo my_lo(ok);   // read on a high-half tie only
+    const LoRef lo_src{xlo, src, mine};
     uint32_t cnt = 0;
     if (N && d.staged)
       cnt = index_count(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, sidx, my_hi, my_lo,
-                        xlo + mine);
+                        lo_src);
     else if (N)
       cnt = index_count_global(sidx, N, d.dir, d.dir_bits, d.dir_shift, d.dir_base, my_hi, my_lo,
-                               xlo + mine);
+                               lo_src);
     uint32_t result = 0;
     if (db == 0) {
       uint32_t rank = cnt;
@@ -95,7 +97,7 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
 #pragma unroll
             for (int i = 0; i < kRounds; i++) {
               const uint32_t need = __ballot_sync(kFull, eq[i]) & gmask;
-              if (need && j == r0 + i) my_lo.get(xlo + mine);
+              if (need && j == r0 + i) my_lo.get(lo_src);
               const uint64_t ql = __shfl_sync(kFull, my_lo.v, gshift + r0 + i);
               lt[i] = lt[i] | (eq[i] & (key[i].y < ql));
             }
@@ -146,6 +148,7 @@ __device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* U
                                            const uint16_t* Dir, uint64_t s0, uint64_t s1,
                                            const uint64_t* __restrict__ xhi,
                                            const uint64_t* __restrict__ xlo,
+                                           const uint32_t* __restrict__ src,
                                            uint16_t* __restrict__ out, uint32_t* status) {
   const uint64_t leaf_key0 = static_cast<uint64_t>(d.internal_nodes) * 16u;
   const uint64_t* keys_hi = static_cast<const uint64_t*>(d.nodes) + leaf_key0;
@@ -215,9 +218,9 @@ __device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* U
     }
 #endif
     uint32_t w = __ldg(words + rank);
-    const uint64_t* lo_src = xlo + mine;
+    const LoRef lo_src{xlo, src, mine};
     w = settle_tie(keys_hi, keys_lo, nk, words, rank, w, my_hi,
-                   [lo_src, ok] { return ok ? *lo_src : 0ull; });
+                   [&lo_src, ok] { return ok ? *lo_src.ptr() : 0ull; });
     if (ok) out[mine] = static_cast<uint16_t>(w);
   }
 }
@@ -225,7 +228,8 @@ __device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* U
 __global__ void __launch_bounds__(512, 2)
     lookup_multi_persistent(const MultiDesc* __restrict__ desc, uint32_t T,
                             const uint64_t* __restrict__ range, const uint64_t* __restrict__ xhi,
-                            const uint64_t* __restrict__ xlo, uint16_t* __restrict__ out,
+                            const uint64_t* __restrict__ xlo, const uint32_t* __restrict__ src,
+                            uint16_t* __restrict__ out,
                             unsigned long long* __restrict__ next_item,
                             uint32_t* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -274,30 +278,30 @@ __global__ void __launch_bounds__(512, 2)
       const uint32_t sel = d.db <= static_cast<uint32_t>(kMultiMaxDb) ? d.db : 15u;
       if (d.f16) {
         switch (sel) {
-          case 0: multi_tiles16<0>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 1: multi_tiles16<1>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 2: multi_tiles16<2>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 3: multi_tiles16<3>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 4: multi_tiles16<4>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          default: multi_tiles16<-1>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 0: multi_tiles16<0>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 1: multi_tiles16<1>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 2: multi_tiles16<2>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 3: multi_tiles16<3>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 4: multi_tiles16<4>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          default: multi_tiles16<-1>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
         }
       } else if (d.packed) {
         switch (sel) {
-          case 0: multi_tiles<0, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 1: multi_tiles<1, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 2: multi_tiles<2, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 3: multi_tiles<3, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 4: multi_tiles<4, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          default: multi_tiles<-1, true>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 0: multi_tiles<0, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 1: multi_tiles<1, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 2: multi_tiles<2, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 3: multi_tiles<3, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 4: multi_tiles<4, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          default: multi_tiles<-1, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
         }
       } else {
         switch (sel) {
-          case 0: multi_tiles<0, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 1: multi_tiles<1, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 2: multi_tiles<2, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 3: multi_tiles<3, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          case 4: multi_tiles<4, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
-          default: multi_tiles<-1, false>(d, Uh, Dir, s0, s1, xhi, xlo, out, status); break;
+          case 0: multi_tiles<0, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 1: multi_tiles<1, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 2: multi_tiles<2, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 3: multi_tiles<3, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 4: multi_tiles<4, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          default: multi_tiles<-1, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
         }
       }
     }
@@ -323,14 +327,16 @@ int multi_persistent_setup(int device, size_t smem_bytes, int* ctas) {
 }
 
 int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t* d_range,
-                            const uint64_t* d_hi, const uint64_t* d_lo, uint16_t* d_out,
+                            const uint64_t* d_hi, const uint64_t* d_lo, const uint32_t* d_src,
+                            uint16_t* d_out,
                             unsigned long long* d_next_item, uint32_t* d_status, int ctas,
                             size_t smem_bytes, void* stream) {
   if (T == 0 || T > 255 || ctas < 1) return PLANB_EINVAL;
   cudaGetLastError();
   lookup_multi_persistent<<<static_cast<unsigned>(ctas), 512, smem_bytes,
                             static_cast<cudaStream_t>(stream)>>>(d_desc, T, d_range, d_hi, d_lo,
-                                                                 d_out, d_next_item, d_status);
+                                                                 d_src, d_out, d_next_item,
+                                                                 d_status);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

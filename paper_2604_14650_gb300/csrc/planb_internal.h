@@ -224,13 +224,14 @@ struct LaunchCfg {
 
 // Launches the lookup kernel for one table on `stream`. d_status may be null. With d_range (device
 // [begin, end)) the launch handles addresses begin..end-1 of d_hi/d_lo instead of 0..n-1 (n then only
-// sizes the grid); with d_perm the result of address j is stored at d_out[d_perm[j]]. lazy_lo (hybrid
-// tables, single table): read an address's low half only on a high-half tie, for addresses that
-// live in host memory and cross the host link.
+// sizes the grid); with d_src as well, d_lo holds the batch's low halves in input order and the low
+// half of address j is d_lo[d_src[j]], read only when a count needs it. lazy_lo (hybrid tables,
+// single table): read an address's low half only on a high-half tie, for addresses that live in
+// host memory and cross the host link.
 int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
                   const uint64_t* d_lo, size_t n, uint16_t* d_out, uint32_t* d_status,
                   void* stream, const uint64_t* d_range = nullptr,
-                  const uint32_t* d_perm = nullptr, bool lazy_lo = false);
+                  const uint32_t* d_src = nullptr, bool lazy_lo = false);
 
 // One table of the single-launch multi-table kernel (F8X128, F8V7 or F16HI tables of the hybrid
 // kernel).
@@ -259,18 +260,22 @@ struct MultiDesc {
 // The single-launch multi-table kernel: raises its shared-memory limit to the device maximum and
 // returns the persistent grid size for smem_bytes of dynamic shared memory per CTA.
 int multi_persistent_setup(int device, size_t smem_bytes, int* ctas);
-// Looks up the bucketed addresses [0, range[T]) of d_hi/d_lo against table t of d_desc for the
-// addresses in [range[t], range[t+1]), writing each result at its bucketed position in d_out.
+// Looks up the bucketed addresses [0, range[T]) of d_hi against table t of d_desc for the
+// addresses in [range[t], range[t+1]), writing each result at its bucketed position in d_out; the
+// low half of bucketed address j, read only when a count needs it, is d_lo[d_src[j]] (d_lo in the
+// batch's input order).
 // Work items are claimed from *d_next_item, which must be 0 when the launch starts (the bucketing
 // resets it). smem_bytes: 8 * (T + 3 rounded to even) + the largest over the tables of 8 * sidx_n
 // rounded up to 16 bytes plus 2 * (2^dir_bits + 1), at most the device maximum.
 int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t* d_range,
-                            const uint64_t* d_hi, const uint64_t* d_lo, uint16_t* d_out,
+                            const uint64_t* d_hi, const uint64_t* d_lo, const uint32_t* d_src,
+                            uint16_t* d_out,
                             unsigned long long* d_next_item, uint32_t* d_status, int ctas,
                             size_t smem_bytes, void* stream);
 
 // Multi-table bucketing (multi.cu): groups n addresses by their u8 table id (ids >= T form one
-// extra segment) into d_bhi/d_blo, table-major; d_range[t] .. d_range[t+1] bound table t's
+// extra segment) into d_bhi (high halves), table-major, with d_bsrc[j] = the input position of
+// bucketed address j; d_range[t] .. d_range[t+1] bound table t's
 // segment; d_range has room for 2T + 4 words (then T + 1 words of scratch, then the persistent
 // lookup's work counter, which is reset to 0). d_counts holds (T+1) x G words. The batch is cut
 // into G chunks and each chunk into tiles of up to 2,048 addresses: d_where[i] is address i's slot
@@ -283,9 +288,9 @@ size_t bucketing_tiles(size_t cap, uint32_t G);
 // Raises the scatter kernel's dynamic shared-memory limit (once per device, before any launch or
 // capture of launch_bucketing).
 int bucketing_setup();
-int launch_bucketing(const uint64_t* d_hi, const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
+int launch_bucketing(const uint64_t* d_hi, const uint8_t* d_tid, size_t n,
                      uint32_t T, uint32_t G, uint32_t* d_counts, uint64_t* d_range,
-                     uint64_t* d_bhi, uint64_t* d_blo, uint16_t* d_where,
+                     uint64_t* d_bhi, uint32_t* d_bsrc, uint16_t* d_where,
                      uint32_t* d_tile_start, uint16_t* d_tile_base, void* stream,
                      const uint64_t* d_n = nullptr);
 // d_out[i] = the bucketed result of address i (d_bres in bucketed order), 0 for ids >= T, using
