@@ -20,12 +20,11 @@
 // The intervals, node arrays and index are identical to the host builder's, word for word.
 #include <cuda_runtime.h>
 
-#include <cub/cub.cuh>
-
 #include <algorithm>
 #include <vector>
 
 #include "planb_internal.h"
+#include "primitives.cuh"
 
 namespace planb {
 
@@ -304,37 +303,14 @@ __global__ void k_fill_sidx(uint64_t n, uint64_t span, const uint64_t* ihi, cons
 
 struct Ctx {
   cudaStream_t st;
-  DevBuf tmp;
-  int grow(size_t need) {
-    if (tmp.p && need <= tmp.bytes) return PLANB_OK;
-    return tmp.alloc(need, st) ? PLANB_OK : PLANB_ENOMEM;
-  }
   template <class K>
   int sort_pairs(const K* kin, K* kout, const uint32_t* vin, uint32_t* vout, uint64_t n,
                  int end_bit) {
-    size_t need = 0;
-    const int nn = static_cast<int>(n);
-    if (cub::DeviceRadixSort::SortPairs(nullptr, need, kin, kout, vin, vout, nn, 0, end_bit, st) !=
-        cudaSuccess)
-      return PLANB_ECUDA;
-    if (int rc = grow(need)) return rc;
-    need = tmp.bytes;
-    return cub::DeviceRadixSort::SortPairs(tmp.p, need, kin, kout, vin, vout, nn, 0, end_bit, st) ==
-                   cudaSuccess
-               ? PLANB_OK
-               : PLANB_ECUDA;
+    return prim::sort_pairs<K>(kin, kout, vin, vout, n, end_bit, st);
   }
   template <class T>
   int select(const T* in, const uint8_t* flags, T* out, uint64_t n, uint32_t* d_count) {
-    size_t need = 0;
-    const int nn = static_cast<int>(n);
-    if (cub::DeviceSelect::Flagged(nullptr, need, in, flags, out, d_count, nn, st) != cudaSuccess)
-      return PLANB_ECUDA;
-    if (int rc = grow(need)) return rc;
-    need = tmp.bytes;
-    return cub::DeviceSelect::Flagged(tmp.p, need, in, flags, out, d_count, nn, st) == cudaSuccess
-               ? PLANB_OK
-               : PLANB_ECUDA;
+    return prim::select_flagged<T>(in, flags, out, n, d_count, st);
   }
   int read_count(const uint32_t* d, uint32_t& h) {
     return cudaMemcpyAsync(&h, d, 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
@@ -465,15 +441,9 @@ int gpu_sweep(const Prefix* d_canon, uint64_t N, bool merge, void* stream, GpuIn
   if (E) {
     k_delta<<<blocks_for(E), 256, 0, cx.st>>>(eord.as<uint32_t>(), ekey.as<uint32_t>(), E,
                                               delta.as<int>());
-    size_t need = 0;
-    if (cub::DeviceScan::InclusiveSum(nullptr, need, delta.as<int>(), depth.as<int>(),
-                                      static_cast<int>(E), cx.st) != cudaSuccess)
-      return PLANB_ECUDA;
-    if ((rc = cx.grow(need))) return rc;
-    need = cx.tmp.bytes;
-    if (cub::DeviceScan::InclusiveSum(cx.tmp.p, need, delta.as<int>(), depth.as<int>(),
-                                      static_cast<int>(E), cx.st) != cudaSuccess)
-      return PLANB_ECUDA;
+    if ((rc = prim::scan_inclusive<int, prim::Sum>(delta.as<int>(), depth.as<int>(), E,
+                                                   prim::Sum(), 0, cx.st)))
+      return rc;
     // group by depth (at most 129 nested prefixes: 8 bits), keeping event order inside a group
     k_depth_key<<<blocks_for(E), 256, 0, cx.st>>>(depth.as<int>(), E, w32a.as<uint32_t>(),
                                                   w32b.as<uint32_t>());
@@ -483,17 +453,10 @@ int gpu_sweep(const Prefix* d_canon, uint64_t N, bool merge, void* stream, GpuIn
     k_seg_values<<<blocks_for(E), 256, 0, cx.st>>>(gpos.as<uint32_t>(), gkey.as<uint32_t>(),
                                                    eord.as<uint32_t>(), ekey.as<uint32_t>(), E,
                                                    segv.as<unsigned long long>());
-    need = 0;
-    if (cub::DeviceScan::InclusiveScan(nullptr, need, segv.as<unsigned long long>(),
-                                       segs.as<unsigned long long>(), SegMax(),
-                                       static_cast<int>(E), cx.st) != cudaSuccess)
-      return PLANB_ECUDA;
-    if ((rc = cx.grow(need))) return rc;
-    need = cx.tmp.bytes;
-    if (cub::DeviceScan::InclusiveScan(cx.tmp.p, need, segv.as<unsigned long long>(),
-                                       segs.as<unsigned long long>(), SegMax(),
-                                       static_cast<int>(E), cx.st) != cudaSuccess)
-      return PLANB_ECUDA;
+    if ((rc = prim::scan_inclusive<unsigned long long, SegMax>(
+             segv.as<unsigned long long>(), segs.as<unsigned long long>(), E, SegMax(), 0ull,
+             cx.st)))
+      return rc;
     k_top_back<<<blocks_for(E), 256, 0, cx.st>>>(gpos.as<uint32_t>(),
                                                  segs.as<unsigned long long>(), E,
                                                  top.as<uint32_t>());

@@ -13,9 +13,8 @@
 // Ids at or above the table count get next hop 0 from the gather.
 #include <cuda_runtime.h>
 
-#include <cub/cub.cuh>
-
 #include "planb_internal.h"
+#include "primitives.cuh"
 
 namespace planb {
 
@@ -65,24 +64,26 @@ constexpr int kScanItems = 8;
 __global__ void __launch_bounds__(kScanThreads) mt_rowscan_kernel(uint32_t* __restrict__ counts,
                                                                   uint32_t G,
                                                                   uint64_t* __restrict__ totals) {
-  typedef cub::BlockScan<uint32_t, kScanThreads> Scan;
-  __shared__ typename Scan::TempStorage tmp;
+  static_assert(kScanThreads == prim::kThreads, "block scan width");
+  __shared__ uint32_t warp_tot[kScanThreads / 32];
   uint32_t* row = counts + static_cast<uint64_t>(blockIdx.x) * G;
   uint32_t carry = 0;
   for (uint32_t base = 0; base < G; base += kScanThreads * kScanItems) {
     uint32_t v[kScanItems];
+    uint32_t own = 0;   // the thread's items, then their exclusive prefixes within the thread
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
       const uint32_t i = base + threadIdx.x * kScanItems + k;
-      v[k] = i < G ? row[i] : 0u;
+      const uint32_t c = i < G ? row[i] : 0u;
+      v[k] = own;
+      own += c;
     }
     uint32_t tile_total = 0;
-    Scan(tmp).ExclusiveSum(v, v, tile_total);
-    __syncthreads();   // tmp is reused by the next tile
+    const uint32_t before = prim::block_scan(own, prim::Sum(), warp_tot, &tile_total) - own;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
       const uint32_t i = base + threadIdx.x * kScanItems + k;
-      if (i < G) row[i] = v[k] + carry;
+      if (i < G) row[i] = v[k] + before + carry;
     }
     carry += tile_total;
   }
@@ -94,11 +95,10 @@ __global__ void __launch_bounds__(kScanThreads) mt_rowscan_kernel(uint32_t* __re
 __global__ void mt_tablescan_kernel(const uint64_t* __restrict__ totals, uint32_t T,
                                     uint64_t* __restrict__ range,
                                     unsigned long long* __restrict__ next_item) {
-  typedef cub::BlockScan<uint64_t, 256> Scan;
-  __shared__ typename Scan::TempStorage tmp;
+  __shared__ uint64_t warp_tot[256 / 32];
   const uint32_t t = threadIdx.x;
-  uint64_t v = t <= T ? totals[t] : 0ull, excl = 0, all = 0;
-  Scan(tmp).ExclusiveSum(v, excl, all);
+  uint64_t v = t <= T ? totals[t] : 0ull, all = 0;
+  const uint64_t excl = prim::block_scan(v, prim::Sum(), warp_tot, &all) - v;
   if (t <= T) range[t] = excl;
   if (t == 0) {
     range[T + 1] = all;
@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(kScatterThreads)
                       uint64_t* __restrict__ bhi, uint32_t* __restrict__ bsrc,
                       uint16_t* __restrict__ where, uint32_t* __restrict__ tile_start,
                       uint16_t* __restrict__ tile_base, const uint64_t* __restrict__ d_n) {
-  typedef cub::BlockScan<uint32_t, kScatterThreads> Scan;
-  __shared__ typename Scan::TempStorage scan_tmp;
+  static_assert(kScatterThreads == prim::kThreads, "block scan width");
+  __shared__ uint32_t scan_tot[kScatterThreads / 32];
   __shared__ uint32_t cur[256], cnt[256], base[256];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint64_t* s_in = reinterpret_cast<uint64_t*>(smem_raw);   // [buffer][kTile] high halves
@@ -196,8 +196,9 @@ __global__ void __launch_bounds__(kScatterThreads)
       rank[k] = tt[k] != 0xFFFFu ? atomicAdd(&cnt[tt[k]], 1u) : 0u;
     __syncthreads();
     {
-      uint32_t v = threadIdx.x <= T ? cnt[threadIdx.x] : 0u, excl = 0;
-      Scan(scan_tmp).ExclusiveSum(v, excl);
+      const uint32_t v = threadIdx.x <= T ? cnt[threadIdx.x] : 0u;
+      uint32_t all = 0;
+      const uint32_t excl = prim::block_scan(v, prim::Sum(), scan_tot, &all) - v;
       if (threadIdx.x <= T) {
         base[threadIdx.x] = excl;
         // for the gather: where each table's run of this tile starts, in the tile and globally

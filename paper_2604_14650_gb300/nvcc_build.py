@@ -49,6 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> dict:
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
     headers = [os.path.join(CSRC, "planb_internal.h"), os.path.join(CSRC, "learned.cuh"),
+               os.path.join(CSRC, "primitives.cuh"),
                os.path.join(CSRC, "descent.cuh"), os.path.join(INCLUDE, "planb.h")]
     jobs, links = [], {}
     for lib, defines in LIBS.items():
