@@ -259,10 +259,14 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
   __syncthreads();
 
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t g = lane >> 3;
-  const uint32_t j = lane & 7u;
-  const uint32_t gshift = g * 8u;
-  const uint32_t gmask = 0xFFu << gshift;
+  // 4-lane groups of phase B: group g, lane j within it; `sel` and `nib` gather the group's
+  // nibble of two ballots into one word
+  const uint32_t g = lane >> 2;
+  const uint32_t j = lane & 3u;
+  const uint32_t gmask = 0xFu << (g * 4u);
+  const uint32_t sel = (g >> 1) | ((4u + (g >> 1)) << 4);
+  const uint32_t nib = (g & 1u) ? 0xF0F0u : 0x0F0Fu;
+  const uint64_t* nodes64 = reinterpret_cast<const uint64_t*>(p.nodes);
   const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
 
@@ -346,63 +350,73 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
       const uint32_t my_node = p.sidx_node + cnt;
       uint32_t result = 0;
       uint64_t my_rank = 0;   // the interval index of this lane's own address
-      // phase B: the last DB levels from L2, 8-lane groups, kRounds addresses per group at once
+      // phase B: the last DB levels from L2 by 4-lane groups — lane j of group g holds keys 2j and
+      // 2j + 1 of a node (one 32-byte load of two (high, low) pairs), the group's four addresses
+      // are those of lanes 4g .. 4g + 3; one level left: all four in flight, else two at a time
+      // (and two when the low half is read lazily: the registers it needs)
+      constexpr int R = (DB == 1 && !LAZY) ? 4 : 2;
 #pragma unroll
-      for (uint32_t r0 = 0; r0 < 8; r0 += kRounds) {
-        uint64_t qh[kRounds];
-        uint32_t nd[kRounds], c[kRounds];
+      for (int r0 = 0; r0 < 4; r0 += R) {
+        uint64_t qh[R];
+        uint32_t nd[R], c[R];
+        Quad kq[R];
 #pragma unroll
-        for (int i = 0; i < kRounds; i++) {
-          const uint32_t src = gshift + r0 + i;
+        for (int i = 0; i < R; i++) {
+          const uint32_t src = g * 4u + r0 + i;
           qh[i] = __shfl_sync(kFull, my_hi, src);
           nd[i] = __shfl_sync(kFull, my_node, src);
         }
 #pragma unroll
         for (int l = 0; l < DB; l++) {
-          ulonglong2 key[kRounds];
 #pragma unroll
-          for (int i = 0; i < kRounds; i++)
-            key[i] = __ldg(p.nodes + static_cast<uint64_t>(nd[i]) * 8u + j);
-          // in a packed leaf, slot 7 holds next hops, not a key
-          const bool keylane = !PACKED || (l + 1 < DB) || (j < 7u);
+          for (int i = 0; i < R; i++)
+            kq[i] = ldg_quad(nodes64 + static_cast<uint64_t>(nd[i]) * 16u + j * 4u);
+          const bool last = l + 1 == DB;
+          // in a packed leaf, slot 7 (lane 3's second key) holds next hops, not a key
+          const bool key1 = !PACKED || !last || j < 3u;
           // (few predicates live at once: the equalities are recomputed on the tie path)
           bool anyeq = false;
 #pragma unroll
-          for (int i = 0; i < kRounds; i++) anyeq |= keylane & (key[i].x == qh[i]);
+          for (int i = 0; i < R; i++)
+            anyeq |= (kq[i].a == qh[i]) | (key1 & (kq[i].c == qh[i]));
           const bool tie = __any_sync(kFull, anyeq);
 #pragma unroll
-          for (int i = 0; i < kRounds; i++) {
-            bool lt = keylane & (key[i].x < qh[i]);
+          for (int i = 0; i < R; i++) {
+            bool lt0 = kq[i].a < qh[i];
+            bool lt1 = key1 & (kq[i].c < qh[i]);
             if (tie) {
-              const bool eq = keylane & (key[i].x == qh[i]);
+              const bool eq0 = kq[i].a == qh[i];
+              const bool eq1 = key1 & (kq[i].c == qh[i]);
               // the owner of address i of each group reads its low half if its group saw a tie
-              const uint32_t need = __ballot_sync(kFull, eq) & gmask;
-              if (need && j == r0 + i) my_lo.get(lo_src);
-              const uint64_t ql = __shfl_sync(kFull, my_lo.v, gshift + r0 + i);
-              lt = lt | (eq & (key[i].y < ql));
+              const uint32_t need = __ballot_sync(kFull, eq0 | eq1) & gmask;
+              if (need && j == static_cast<uint32_t>(r0 + i)) my_lo.get(lo_src);
+              const uint64_t ql = __shfl_sync(kFull, my_lo.v, g * 4u + r0 + i);
+              lt0 = lt0 | (eq0 & (kq[i].b < ql));
+              lt1 = lt1 | (eq1 & (kq[i].d < ql));
             }
-            c[i] = __popc(__ballot_sync(kFull, lt) & gmask);
-            if (l + 1 < DB) nd[i] = nd[i] * 9u + 1u + c[i];
+            c[i] = __popc(__byte_perm(__ballot_sync(kFull, lt0), __ballot_sync(kFull, lt1), sel) &
+                          nib);
+            if (!last) nd[i] = nd[i] * 9u + 1u + c[i];
           }
-          if (PACKED && l + 1 == DB) {
-            // the next hop of slot c sits in slot 7 of the same leaf line: lane 7 of the group
+          if (PACKED && last) {
+            // the next hop of slot c sits in slot 7 of the same leaf line: lane 3 of the group
             // picks its 16-bit field and broadcasts it
 #pragma unroll
-            for (int i = 0; i < kRounds; i++) {
+            for (int i = 0; i < R; i++) {
 #ifdef PLANB_BOUNDS_CHECK
               if (c[i] > 6u || nd[i] >= p.total_nodes) report(p.status, 4u);
 #endif
               const uint32_t ci = c[i] & 7u;
-              const uint64_t w = ci < 4u ? key[i].x : key[i].y;
+              const uint64_t w = ci < 4u ? kq[i].c : kq[i].d;
               const uint32_t f = static_cast<uint32_t>(w >> (16u * (ci & 3u))) & 0xFFFFu;
-              const uint32_t v = __shfl_sync(kFull, f, gshift + 7u);
-              if (j == r0 + i) result = v;
+              const uint32_t v = __shfl_sync(kFull, f, g * 4u + 3u);
+              if (j == static_cast<uint32_t>(r0 + i)) result = v;
             }
           }
         }
         if (!PACKED) {
 #pragma unroll
-          for (int i = 0; i < kRounds; i++) {
+          for (int i = 0; i < R; i++) {
             uint64_t rank = static_cast<uint64_t>(nd[i] - p.internal_nodes) * 8u + c[i];
 #ifdef PLANB_BOUNDS_CHECK
             if (rank >= p.n_intervals || nd[i] >= p.total_nodes) {
@@ -410,7 +424,7 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
               rank = 0;
             }
 #endif
-            if (j == r0 + i) my_rank = rank;
+            if (j == static_cast<uint32_t>(r0 + i)) my_rank = rank;
           }
         }
       }

@@ -273,11 +273,20 @@ __global__ void __launch_bounds__(kGatherThreads)
         if (sb[mid] <= s0) lo = mid; else hi = mid;
       }
       uint32_t t = lo;
-      const uint32_t s1 = s0 + kPer < m ? s0 + kPer : m;
-      for (uint32_t slot = s0; slot < s1; slot++) {
-        while (sb[t + 1] <= slot) t++;
-        res[slot] = t < T ? bres[st[t] + (slot - sb[t])] : static_cast<uint16_t>(0);
+      // the kPer source positions first (shared memory only), then their loads all in flight
+      uint32_t src[kPer];
+#pragma unroll
+      for (uint32_t k = 0; k < kPer; k++) {
+        const uint32_t slot = s0 + k;
+        while (t < T + 1 && sb[t + 1] <= slot) t++;
+        src[k] = (slot < m && t < T) ? st[t] + (slot - sb[t]) : 0xFFFFFFFFu;
       }
+      uint16_t v[kPer];
+#pragma unroll
+      for (uint32_t k = 0; k < kPer; k++) v[k] = src[k] != 0xFFFFFFFFu ? bres[src[k]] : uint16_t(0);
+#pragma unroll
+      for (uint32_t k = 0; k < kPer; k++)
+        if (s0 + k < m) res[s0 + k] = v[k];
     }
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) out[tb + k] = res[where[tb + k]];
