@@ -330,4 +330,33 @@ void fill_dir(const uint64_t* sidx, uint64_t n, const DirParams& p, uint16_t* di
   }
 }
 
+uint32_t bucket_dir_bits_for(uint64_t n) {
+  if (n == 0 || n >= (uint64_t(1) << 31)) return 0;
+  uint32_t lg = 0;
+  while ((uint64_t(1) << lg) < n) lg++;
+  return std::min<uint32_t>(20, std::max<uint32_t>(4, lg + 2));   // about four buckets per entry
+}
+
+BucketDir bucket_dir_params(const uint64_t* sidx, uint64_t n) {
+  BucketDir p;
+  p.bits = bucket_dir_bits_for(n);
+  if (!p.bits) return p;
+  const uint64_t lo = sidx[0], hi = sidx[2 * (n - 1)];
+  const uint64_t cap = uint64_t(1) << p.bits;
+  while (p.shift < 63 && (hi >> p.shift) - (lo >> p.shift) >= cap) p.shift++;
+  p.base = lo >> p.shift;
+  return p;
+}
+
+void fill_bucket_dir(const uint64_t* sidx, uint64_t n, const BucketDir& p, uint64_t* out) {
+  const uint64_t buckets = uint64_t(1) << p.bits;
+  uint64_t q = 0;
+  for (uint64_t b = 0; b < buckets; b++) {
+    const uint64_t first = q;
+    while (q < n && (sidx[2 * q] >> p.shift) - p.base <= b) q++;   // the entries of bucket b
+    out[2 * b] = first | ((q - first) << 32);
+    out[2 * b + 1] = first < n ? sidx[2 * first] : ~0ull;
+  }
+}
+
 }  // namespace planb

@@ -252,6 +252,11 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   planb::DirParams dp;
   if (kernel == planb::kHybrid) dp.bits = planb::dir_bits_for(sidx_n);
   const size_t dirb = planb::dir_bytes(dp);
+  // F16HI hybrid: the bucket directory of the in-place index search (small launches); its size
+  // follows from the entry count, its contents from the index
+  planb::BucketDir bdp;
+  if (kernel == planb::kHybrid && format == PLANB_FMT_F16HI) bdp.bits = planb::bucket_dir_bits_for(sidx_n);
+  const size_t bdb = planb::bucket_dir_bytes(bdp);
   // next hops: u16 per interval; F16HI: u32 words that also flag possible high-half ties
   const size_t vw = format == PLANB_FMT_F16HI ? 4 : 2;
   const size_t val_bytes = ((static_cast<size_t>(m) * vw + 255) / 256) * 256;
@@ -259,7 +264,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
       learned ? ((static_cast<size_t>(model_leaves) * 18 + 255) / 256) * 256 : 0;
   std::vector<uint64_t> host;
   if (!on_dev) {
-    host.resize((node_bytes + lo_bytes + sidx_bytes + dirb) / 8);
+    host.resize((node_bytes + lo_bytes + sidx_bytes + dirb + bdb) / 8);
     if (format == PLANB_FMT_F16HI)
       planb::fill_f16hi(iv, t->L, host.data(), host.data() + node_bytes / 8);
     else if (format == PLANB_FMT_F8V7)
@@ -274,6 +279,14 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
       if (dp.bits != bits) return fail_detail(PLANB_EINVAL, "radix directory size");
       planb::fill_dir(sx, sidx_n, dp, reinterpret_cast<uint16_t*>(
                                           host.data() + (node_bytes + lo_bytes + sidx_bytes) / 8));
+    }
+    if (bdp.bits) {
+      const uint64_t* sx = host.data() + (node_bytes + lo_bytes) / 8;
+      const uint32_t bits = bdp.bits;
+      bdp = planb::bucket_dir_params(sx, sidx_n);
+      if (bdp.bits != bits) return fail_detail(PLANB_EINVAL, "bucket directory size");
+      planb::fill_bucket_dir(sx, sidx_n, bdp,
+                             host.data() + (node_bytes + lo_bytes + sidx_bytes + dirb) / 8);
     }
   }
   t->build_ms = ms_since(t0);
@@ -293,7 +306,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                               model_leaves, iters, 0.01f, 64u, t->model);
     if (rc) return rc;
   }
-  t->bytes = node_bytes + lo_bytes + sidx_bytes + dirb + val_bytes + model_bytes;
+  t->bytes = node_bytes + lo_bytes + sidx_bytes + dirb + bdb + val_bytes + model_bytes;
   if (g_inject.load() == 2) {
     g_inject.store(0);
     return PLANB_ENOMEM;
@@ -304,7 +317,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
     return PLANB_ENOMEM;
   }
   char* base = static_cast<char*>(t->mem);
-  const size_t head = node_bytes + lo_bytes + sidx_bytes + dirb;
+  const size_t head = node_bytes + lo_bytes + sidx_bytes + dirb + bdb;
   t->dump_bytes = head + m * vw;
   if (on_dev) {
     // the index region's rounding tail is zero, as in the host-filled image
@@ -320,18 +333,31 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
     if (rc) return fail_detail(rc, "device layout fill", cudaGetLastError());
     if (cudaStreamSynchronize(bs->s) != cudaSuccess)
       return fail_detail(PLANB_ECUDA, "device layout fill", cudaGetLastError());
-    if (dp.bits) {   // the directory comes from the index the device just wrote
-      std::vector<uint64_t> sx(sidx_n * 2), dh(dirb / 8, 0);
+    if (dp.bits || bdp.bits) {   // the directories come from the index the device just wrote
+      std::vector<uint64_t> sx(sidx_n * 2);
       if (cudaMemcpy(sx.data(), base + node_bytes + lo_bytes, sidx_n * 16,
                      cudaMemcpyDeviceToHost) != cudaSuccess)
         return PLANB_ECUDA;
-      const uint32_t bits = dp.bits;
-      dp = planb::dir_params(sx.data(), sidx_n);
-      if (dp.bits != bits) return fail_detail(PLANB_EINVAL, "radix directory size");
-      planb::fill_dir(sx.data(), sidx_n, dp, reinterpret_cast<uint16_t*>(dh.data()));
-      if (cudaMemcpy(base + node_bytes + lo_bytes + sidx_bytes, dh.data(), dirb,
-                     cudaMemcpyHostToDevice) != cudaSuccess)
-        return PLANB_ECUDA;
+      if (dp.bits) {
+        std::vector<uint64_t> dh(dirb / 8, 0);
+        const uint32_t bits = dp.bits;
+        dp = planb::dir_params(sx.data(), sidx_n);
+        if (dp.bits != bits) return fail_detail(PLANB_EINVAL, "radix directory size");
+        planb::fill_dir(sx.data(), sidx_n, dp, reinterpret_cast<uint16_t*>(dh.data()));
+        if (cudaMemcpy(base + node_bytes + lo_bytes + sidx_bytes, dh.data(), dirb,
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+          return PLANB_ECUDA;
+      }
+      if (bdp.bits) {
+        std::vector<uint64_t> bh(bdb / 8, 0);
+        const uint32_t bits = bdp.bits;
+        bdp = planb::bucket_dir_params(sx.data(), sidx_n);
+        if (bdp.bits != bits) return fail_detail(PLANB_EINVAL, "bucket directory size");
+        planb::fill_bucket_dir(sx.data(), sidx_n, bdp, bh.data());
+        if (cudaMemcpy(base + node_bytes + lo_bytes + sidx_bytes + dirb, bh.data(), bdb,
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+          return PLANB_ECUDA;
+      }
     }
   } else {
     std::vector<uint32_t> words;
@@ -363,6 +389,10 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   t->dt.sidx_node = s < t->L.D ? t->L.level_node[s] : 0;
   t->dt.dir = dp.bits ? reinterpret_cast<const uint16_t*>(base + node_bytes + lo_bytes + sidx_bytes)
                       : nullptr;
+  t->dt.bdir = bdp.bits ? reinterpret_cast<const uint64_t*>(base + node_bytes + lo_bytes +
+                                                          sidx_bytes + dirb)
+                       : nullptr;
+  t->dt.bdp = bdp;
   t->dt.dir_bits = dp.bits;
   t->dt.dir_shift = dp.shift;
   t->dt.dir_base = dp.base;

@@ -211,6 +211,33 @@ __device__ __forceinline__ uint32_t quad_count(const Quad& k, uint64_t q, uint32
   return __popc(x & nib);
 }
 
+// The same count searched in place with the bucket directory (see BucketDir): one 16-byte read
+// of the address's bucket — its first entry's position, its entry count and that entry's high
+// half — settles a bucket of at most one entry; a fuller one is finished by a branch-free search
+// of its other entries in the global index. Buckets clamp at both ends: the entries of the first
+// and last buckets are compared with the address like any other.
+__device__ __forceinline__ uint32_t index_count_hi_bucket(const ulonglong2* sidx,
+                                                          const ulonglong2* bdir, uint32_t bits,
+                                                          uint32_t shift, uint64_t base,
+                                                          uint64_t my_hi) {
+  const uint64_t v = my_hi >> shift;
+  uint64_t bk = v > base ? v - base : 0ull;
+  const uint64_t last = (1ull << bits) - 1ull;
+  bk = bk < last ? bk : last;
+  const ulonglong2 w = __ldg(bdir + bk);
+  const uint32_t start = static_cast<uint32_t>(w.x);
+  const uint32_t n = static_cast<uint32_t>(w.x >> 32);
+  if (n == 0u || w.y >= my_hi) return start;   // no entry of the bucket is below the address
+  if (n == 1u) return start + 1u;
+  uint32_t b = start + 1u, m = n - 1u;          // the first is below: search the others
+  while (m > 1u) {
+    const uint32_t half = m >> 1;
+    b = __ldg(&sidx[b + half].x) < my_hi ? b + half : b;
+    m -= half;
+  }
+  return b + (__ldg(&sidx[b].x) < my_hi ? 1u : 0u);
+}
+
 // F16HI next-hop words: bits 0-15 the next hop of an interval, kTieBit set when the interval's key
 // (its inclusive end) has a low half other than all-ones. Only such a key can be below an address
 // whose high half it shares, so only there does a high-half-only count need a second look.

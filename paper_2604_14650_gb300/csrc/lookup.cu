@@ -70,6 +70,8 @@ struct KParams {
   uint32_t staged;            // hybrid: 1 = index and directory staged in shared memory, 0 =
                               // searched in place (small launches; no shared memory given)
   const uint16_t* dir;        // hybrid: radix directory over the index (dir_bits = 0: none)
+  const ulonglong2* bdir;     // F16HI hybrid: bucket directory of the in-place search, or null
+  BucketDir bdp;
   uint32_t dir_bits, dir_shift;
   uint64_t dir_base;
   const uint64_t* range;      // multi-table: device [begin, end) of this launch's addresses
@@ -497,6 +499,8 @@ __global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
     uint32_t cnt = 0;
     if (N && staged)
       cnt = index_count_hi(Uh, N, Dir, p.dir_bits, p.dir_shift, p.dir_base, my_hi);
+    else if (N && p.bdir)
+      cnt = index_count_hi_bucket(p.sidx, p.bdir, p.bdp.bits, p.bdp.shift, p.bdp.base, my_hi);
     else if (N)
       cnt = index_count_hi_global(p.sidx, N, p.dir, p.dir_bits, p.dir_shift, p.dir_base, my_hi);
     uint64_t rank = cnt;
@@ -763,6 +767,8 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   p.leaf_err = t.leaf_err;
   p.lp = t.lp;
   p.dir = t.dir;
+  p.bdir = reinterpret_cast<const ulonglong2*>(t.bdir);
+  p.bdp = t.bdp;
   p.dir_bits = t.dir_bits;
   p.dir_shift = t.dir_shift;
   p.dir_base = t.dir_base;

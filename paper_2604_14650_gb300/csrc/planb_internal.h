@@ -187,6 +187,21 @@ inline size_t dir_bytes(const DirParams& p) {
   return p.bits ? ((((size_t(1) << p.bits) + 1) * 2 + 127) / 128) * 128 : 0;
 }
 
+// Bucket directory for searching the index in place in global memory (launches too small to stage
+// it): about four buckets per entry, bucket b = (hi >> shift) - base as above, and each bucket one
+// 16-byte word — its first entry's position (low 32 bits) and entry count (high 32 bits), then the
+// high half of that first entry — so that one read settles a bucket of at most one entry.
+struct BucketDir {
+  uint32_t bits = 0, shift = 0;
+  uint64_t base = 0;
+};
+BucketDir bucket_dir_params(const uint64_t* sidx /* 2 per entry */, uint64_t n);
+inline size_t bucket_dir_bytes(const BucketDir& p) {
+  return p.bits ? (size_t(1) << p.bits) * 16 : 0;
+}
+void fill_bucket_dir(const uint64_t* sidx, uint64_t n, const BucketDir& p, uint64_t* out);
+uint32_t bucket_dir_bits_for(uint64_t n);
+
 // ------------------------------------------------------------------------- device side
 
 // Everything a lookup kernel needs about one table (device pointers).
@@ -198,6 +213,8 @@ struct DevTable {
   uint64_t sidx_n;          // entries in sidx
   uint64_t sidx_node;       // first node of level S (where the hybrid's per-group phase starts)
   const uint16_t* dir;      // hybrid: radix directory over the index (dir_bits = 0: none)
+  const uint64_t* bdir;     // F16HI hybrid: bucket directory of the in-place search, or null
+  BucketDir bdp;
   uint32_t dir_bits, dir_shift;
   uint64_t dir_base;
   uint32_t kernel;          // Kernel
