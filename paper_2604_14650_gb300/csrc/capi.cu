@@ -1275,6 +1275,8 @@ int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>
     x.f16 = d.format == PLANB_FMT_F16HI ? 1u : 0u;
     x.nodes_lo = d.nodes_lo;
     x.pad = 0;
+    x.bdir = d.bdir;
+    x.bdp = d.bdp;
     const uint64_t need = ((d.sidx_n + 1) & ~1ull) * 8u +
                           (d.dir_bits ? ((((1ull << d.dir_bits) + 1) + 7) & ~7ull) * 2u : 0u);
     x.staged = need <= kSmemBudget ? 1u : 0u;

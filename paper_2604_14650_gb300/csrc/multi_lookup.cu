@@ -17,7 +17,8 @@ namespace {
 // two or three tables are live in L2 at once. A CTA stages the top-of-tree index (high halves) and
 // radix directory of each table it meets in shared memory — keeping them while its next item is
 // in the same table; an index larger than the launch's share is searched in place in global
-// memory instead — and runs the hybrid descent of lookup_hybrid: phase A over the index, then
+// memory instead, through the table's bucket directory when it has one — and runs the hybrid
+// descent of lookup_hybrid: phase A over the index, then
 // the table's remaining DB levels from L2 by lane groups (8 lanes on F8 tables, 4 lanes with
 // 32-byte loads on F16HI tables), writing each result at its bucketed position. The tile code is instantiated per (DB, format) and picked per table; depths beyond
 // kMultiMaxDb take a run-time level loop. Addresses with an id beyond the tables (after range[T])
@@ -30,7 +31,8 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
                                          const uint64_t* __restrict__ xhi,
                                          const uint64_t* __restrict__ xlo,
                                          const uint32_t* __restrict__ src,
-                                         uint16_t* __restrict__ out, uint32_t* status) {
+                                         uint16_t* __restrict__ out, uint32_t* status,
+                                         bool staged) {
   const ulonglong2* nodes = static_cast<const ulonglong2*>(d.nodes);
   const ulonglong2* sidx = reinterpret_cast<const ulonglong2*>(d.sidx);
   const uint32_t N = d.sidx_n;
@@ -48,7 +50,7 @@ __device__ __noinline__ void multi_tiles(const MultiDesc& d, const uint64_t* Uh,
     LazyLo my_lo(ok);   // read on a high-half tie only
     const LoRef lo_src{xlo, src, mine};
     uint32_t cnt = 0;
-    if (N && d.staged)
+    if (N && staged)
       cnt = index_count(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, sidx, my_hi, my_lo,
                         lo_src);
     else if (N)
@@ -149,7 +151,8 @@ __device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* U
                                            const uint64_t* __restrict__ xhi,
                                            const uint64_t* __restrict__ xlo,
                                            const uint32_t* __restrict__ src,
-                                           uint16_t* __restrict__ out, uint32_t* status) {
+                                           uint16_t* __restrict__ out, uint32_t* status,
+                                           bool staged) {
   const uint64_t leaf_key0 = static_cast<uint64_t>(d.internal_nodes) * 16u;
   const uint64_t* keys_hi = static_cast<const uint64_t*>(d.nodes) + leaf_key0;
   const uint64_t* keys_lo = d.nodes_lo + leaf_key0;
@@ -170,8 +173,12 @@ __device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* U
     const bool ok = mine < s1;
     const uint64_t my_hi = ok ? xhi[mine] : 0ull;
     uint32_t cnt = 0;
-    if (N && d.staged)
+    if (N && staged)
       cnt = index_count_hi(Uh, N, Dir, d.dir_bits, d.dir_shift, d.dir_base, my_hi);
+    else if (N && d.bdir)
+      cnt = index_count_hi_bucket(reinterpret_cast<const ulonglong2*>(d.sidx),
+                                  reinterpret_cast<const ulonglong2*>(d.bdir), d.bdp.bits,
+                                  d.bdp.shift, d.bdp.base, my_hi);
     else if (N)
       cnt = index_count_hi_global(reinterpret_cast<const ulonglong2*>(d.sidx), N, d.dir,
                                   d.dir_bits, d.dir_shift, d.dir_base, my_hi);
@@ -276,32 +283,33 @@ __global__ void __launch_bounds__(512, 2)
         staged = t;
       }
       const uint32_t sel = d.db <= static_cast<uint32_t>(kMultiMaxDb) ? d.db : 15u;
+      const bool stage = d.staged != 0u;
       if (d.f16) {
         switch (sel) {
-          case 0: multi_tiles16<0>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 1: multi_tiles16<1>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 2: multi_tiles16<2>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 3: multi_tiles16<3>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 4: multi_tiles16<4>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          default: multi_tiles16<-1>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 0: multi_tiles16<0>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 1: multi_tiles16<1>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 2: multi_tiles16<2>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 3: multi_tiles16<3>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 4: multi_tiles16<4>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          default: multi_tiles16<-1>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
         }
       } else if (d.packed) {
         switch (sel) {
-          case 0: multi_tiles<0, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 1: multi_tiles<1, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 2: multi_tiles<2, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 3: multi_tiles<3, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 4: multi_tiles<4, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          default: multi_tiles<-1, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 0: multi_tiles<0, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 1: multi_tiles<1, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 2: multi_tiles<2, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 3: multi_tiles<3, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 4: multi_tiles<4, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          default: multi_tiles<-1, true>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
         }
       } else {
         switch (sel) {
-          case 0: multi_tiles<0, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 1: multi_tiles<1, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 2: multi_tiles<2, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 3: multi_tiles<3, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          case 4: multi_tiles<4, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
-          default: multi_tiles<-1, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status); break;
+          case 0: multi_tiles<0, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 1: multi_tiles<1, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 2: multi_tiles<2, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 3: multi_tiles<3, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          case 4: multi_tiles<4, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
+          default: multi_tiles<-1, false>(d, Uh, Dir, s0, s1, xhi, xlo, src, out, status, stage); break;
         }
       }
     }

@@ -272,6 +272,8 @@ struct MultiDesc {
                              // place in global memory (an index larger than the launch's share)
   uint32_t pad;
   const uint64_t* nodes_lo;  // F16HI low halves
+  const uint64_t* bdir;      // F16HI: bucket directory of the in-place search, or null
+  BucketDir bdp;
 };
 
 // The single-launch multi-table kernel: raises its shared-memory limit to the device maximum and
