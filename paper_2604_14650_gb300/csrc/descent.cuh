@@ -134,6 +134,20 @@ __device__ __forceinline__ uint32_t index_count_global(const ulonglong2* sidx, u
   return cnt;
 }
 
+// Entries of the ascending array a[lo, lo + n) below x, searched branch-free over the n + 1
+// possible answers lo .. lo + n: each read halves the candidates, ceil(log2(n + 1)) reads in all
+// (against ceil(log2 n) + 1 for a search of the n entries that compares the last one it keeps).
+template <class Load>
+__device__ __forceinline__ uint32_t count_hi_below(Load a, uint32_t lo, uint32_t n, uint64_t x) {
+  uint32_t b = lo, m = n + 1u;
+  while (m > 1u) {
+    const uint32_t half = m >> 1;
+    b = a(b + half - 1u) < x ? b + half : b;
+    m -= half;
+  }
+  return b;
+}
+
 // Entries of the staged high halves Uh[0..N) below the address's high half, started in the
 // address's bucket of the radix directory (the high-half-only count of the F16HI descent).
 __device__ __forceinline__ uint32_t index_count_hi(const uint64_t* Uh, uint32_t N,
@@ -149,14 +163,7 @@ __device__ __forceinline__ uint32_t index_count_hi(const uint64_t* Uh, uint32_t 
     lo = Dir[bk];
     n = Dir[bk + 1] - lo;
   }
-  if (!n) return lo;
-  uint32_t b = lo;
-  while (n > 1) {
-    const uint32_t half = n >> 1;
-    b = Uh[b + half] < my_hi ? b + half : b;
-    n -= half;
-  }
-  return b + (Uh[b] < my_hi ? 1u : 0u);
+  return count_hi_below([Uh](uint32_t i) { return Uh[i]; }, lo, n, my_hi);
 }
 
 // The same count read in place from the global index (entries of 16 bytes, high half first) and
@@ -174,14 +181,7 @@ __device__ __forceinline__ uint32_t index_count_hi_global(const ulonglong2* sidx
     lo = __ldg(dir + bk);
     n = __ldg(dir + bk + 1) - lo;
   }
-  if (!n) return lo;
-  uint32_t b = lo;
-  while (n > 1) {
-    const uint32_t half = n >> 1;
-    b = __ldg(&sidx[b + half].x) < my_hi ? b + half : b;
-    n -= half;
-  }
-  return b + (__ldg(&sidx[b].x) < my_hi ? 1u : 0u);
+  return count_hi_below([sidx](uint32_t i) { return __ldg(&sidx[i].x); }, lo, n, my_hi);
 }
 
 // Four consecutive high halves of a 128-byte F16HI node line (32 bytes, 32-byte aligned), read
@@ -228,14 +228,9 @@ __device__ __forceinline__ uint32_t index_count_hi_bucket(const ulonglong2* sidx
   const uint32_t start = static_cast<uint32_t>(w.x);
   const uint32_t n = static_cast<uint32_t>(w.x >> 32);
   if (n == 0u || w.y >= my_hi) return start;   // no entry of the bucket is below the address
-  if (n == 1u) return start + 1u;
-  uint32_t b = start + 1u, m = n - 1u;          // the first is below: search the others
-  while (m > 1u) {
-    const uint32_t half = m >> 1;
-    b = __ldg(&sidx[b + half].x) < my_hi ? b + half : b;
-    m -= half;
-  }
-  return b + (__ldg(&sidx[b].x) < my_hi ? 1u : 0u);
+  // the first is below: search the others
+  return count_hi_below([sidx](uint32_t i) { return __ldg(&sidx[i].x); }, start + 1u, n - 1u,
+                        my_hi);
 }
 
 // F16HI next-hop words: bits 0-15 the next hop of an interval, kTieBit set when the interval's key
