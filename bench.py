@@ -69,6 +69,8 @@ def parse():
                     help="serve: seconds of the same load before the measured phase")
     ap.add_argument("--per-table", action="store_true",
                     help="serve: one lookup launch per table instead of the single persistent one")
+    ap.add_argument("--bucketed", action="store_true",
+                    help="serve: group each batch by table even where the direct form applies")
     ap.add_argument("--builder", default="host", choices=["host", "device"],
                     help="where tables are built (and rebuilt by updates) in serve")
     ap.add_argument("--tables", type=int, default=64)
@@ -695,8 +697,9 @@ def run_vrf64(args):
     rng = np.random.default_rng(1)
     sample = rng.integers(0, n, 1 << 16)
 
-    def timed(per_table):
-        mt = pb.MultiFib(fibs, max_batch=n, per_table=per_table)
+    def timed(per_table, bucketed=False, direct=False):
+        mt = pb.MultiFib(fibs, max_batch=n, per_table=per_table, bucketed=bucketed,
+                         direct=direct)
         d_out.fill_(-1)
         mt.lookup_ptr(*args_ptr, stream)
         stream.synchronize()
@@ -715,13 +718,19 @@ def run_vrf64(args):
             mt.lookup_ptr(*args_ptr, stream)
         b.record(stream)
         stream.synchronize()
-        mode = mt.persistent
+        mode = mt.mode
         mt.close()
-        if mode == per_table:
-            raise SystemExit(f"multi-table launch mode is not the one asked for (per_table={per_table})")
+        if ((mode == "per_table") != per_table or (bucketed and mode != "bucketed") or
+                (direct and mode != "direct" and args.format == "f16hi" and args.no_tune)):
+            raise SystemExit(f"multi-table launch mode {mode} is not the one asked for")
+        timed.modes.append(mode)
         return a.elapsed_time(b) / args.steps
 
+    timed.modes = []
     ms = timed(False)
+    form = timed.modes[-1]
+    ms_direct = timed(False, direct=True)
+    ms_bucketed = timed(False, bucketed=True)
     ms_per_table = timed(True)
     kinds = {}
     for c in choices:
@@ -737,16 +746,23 @@ def run_vrf64(args):
                        "tables": args.tables, "prefixes_total": int(sizes.sum()),
                        "autotuned": not args.no_tune, "chosen": kinds,
                        "build_s": build_s,
-                       "graph": "bucketing (hist, scan, scatter) + one persistent lookup launch "
-                                "over all tables + gather, captured once, replayed per step",
+                       "form": form,
+                       "graph": ("one persistent launch in input order (no bucketing), captured "
+                                 "once, replayed per step" if form == "direct" else
+                                 "bucketing (hist, scan, scatter) + one persistent lookup launch "
+                                 "over all tables + gather, captured once, replayed per step"),
+                       "direct_B_lookups_per_s": n / ms_direct / 1e6,
+                       "direct_ms_per_step": ms_direct,
+                       "bucketed_B_lookups_per_s": n / ms_bucketed / 1e6,
+                       "bucketed_ms_per_step": ms_bucketed,
                        "per_table_launches_B_lookups_per_s": n / ms_per_table / 1e6,
                        "per_table_launches_ms_per_step": ms_per_table},
             "roofline": {"bound": "hbm", "achieved": 19 * n / (ms / 1e3) / 1e9,
                          "peak": measured_peaks()[0], "unit": "GB/s",
                          "frac": 19 * n / (ms / 1e3) / 1e9 / measured_peaks()[0],
                          "note": "19 B per lookup (16 B address + 1 B id + 2 B result) against the "
-                                 "measured copy bandwidth; bucketing adds ~40 B per lookup"},
-            "gpu_launches": args.steps * 5}
+                                 "measured copy bandwidth"},
+            "gpu_launches": args.steps * (1 if form == "direct" else 5)}
     print(json.dumps(line), flush=True)
     for f in fibs:
         f.close()
@@ -856,8 +872,10 @@ def block_zipf(args, stream, steps, warmup, fib_in=None, lookups=1 << 28):
 
 def block_vrf64(args, stream, steps, warmup, lookups=1 << 27, fmt="f16hi"):
     """64 VRF tables (sizes log-uniform over 1e3..3e5 prefixes) and 2^27 addresses tagged with a
-    table id drawn proportional to table size: the whole multi-table pipeline (one captured graph
-    per step) in the single persistent launch and with one launch per table."""
+    table id drawn proportional to table size: one captured graph per step, in each form of the
+    multi-table lookup — the library's own choice (auto), direct (one launch in input order),
+    bucketed (grouped by table, one persistent launch, gathered back) and one launch per
+    table."""
     import torch
     import paper_2604_14650_gb300 as pb
     import synth
@@ -877,8 +895,9 @@ def block_vrf64(args, stream, steps, warmup, lookups=1 << 27, fmt="f16hi"):
         want[sel] = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh[sample][sel], xl[sample][sel])
     res = {}
     try:
-        for mode, per_table in (("persistent", False), ("per_table", True)):
-            with pb.MultiFib(fibs, max_batch=n, per_table=per_table) as mt:
+        for mode in ("auto", "direct", "bucketed", "per_table"):
+            with pb.MultiFib(fibs, max_batch=n, per_table=mode == "per_table",
+                             bucketed=mode == "bucketed", direct=mode == "direct") as mt:
                 d_out.fill_(-1)
                 mt.lookup_ptr(*ptrs, stream)
                 stream.synchronize()
@@ -886,19 +905,21 @@ def block_vrf64(args, stream, steps, warmup, lookups=1 << 27, fmt="f16hi"):
                 ms = _timed_ms(lambda: mt.lookup_ptr(*ptrs, stream), stream, steps, warmup)
                 res[mode] = {"B_lookups_per_s": n / ms / 1e6, "ms_per_step": ms,
                              "sampled_parity_vs_oracle": bool(np.array_equal(got, want)),
-                             "single_launch": bool(mt.persistent)}
+                             "single_launch": bool(mt.persistent), "form": mt.mode}
     finally:
         for f in fibs:
             f.close()
     del d_hi, d_lo, d_t, d_out
-    p = res["persistent"]
+    p = res["auto"]
     return {"workload": f"64 VRF tables, {int(sizes.sum())} prefixes in all, {n} lookups "
                         "tagged with a u8 table id drawn proportional to table size",
             "value": p["B_lookups_per_s"], "unit": UNIT, "steps": steps, "warmup": warmup,
             "format": fmt,
-            "roofline": dict(_hbm_roofline(19, n, p["ms_per_step"], "multi-table pipeline"),
+            "form": p["form"],
+            "roofline": dict(_hbm_roofline(19, n, p["ms_per_step"],
+                                           f"multi-table lookup, {p['form']} form (whole step)"),
                              note="19 B per lookup (16 B address + 1 B table id + 2 B result) over "
-                                  "the whole captured pipeline of one step"),
+                                  "the whole captured step"),
             "modes": res,
             "sampled_parity_vs_oracle": all(r["sampled_parity_vs_oracle"] for r in res.values())}
 
@@ -943,7 +964,8 @@ def serve_line(args):
     offs = rng.integers(0, pool - 65536, nreq)
     gaps = rng.exponential(1.0 / args.rate, nreq)
     budget = int(sum(f.stats()["node_bytes"] + f.stats()["value_bytes"] for f in fibs) * 1.05)
-    srv = pb.Server(slots=4, max_batch=1 << 18, mem_budget=budget, per_table=args.per_table)
+    srv = pb.Server(slots=4, max_batch=1 << 18, mem_budget=budget, per_table=args.per_table,
+                    bucketed=args.bucketed)
     try:
         line = _serve_loop(args, srv, fibs, fibs_in, pools, nreq, tabs, lens, offs, gaps, rng,
                            budget)
@@ -962,6 +984,7 @@ def block_serve(args, rate=20000.0, duration=2.0, warmup=0.5):
     a = copy.copy(args)
     a.rate, a.duration, a.serve_warmup, a.update_rate = rate, duration, warmup, 1000.0
     a.builder, a.per_table, a.format, a.tables = "device", False, "f16hi", 64
+    a.bucketed = False
     line = serve_line(a)
     return {"workload": line["config"]["workload"], "value": line["value"], "unit": UNIT,
             "latency_us": line["latency_us"], "batch_us": line["batch_us"],

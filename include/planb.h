@@ -282,20 +282,31 @@ typedef struct planb_multi planb_multi; /* several tables (VRFs) served by one c
 #define PLANB_MULTI_NO_GRAPH 1u  /* flag: launch the pipeline directly instead of a captured graph */
 #define PLANB_MULTI_PER_TABLE 2u /* flag: one lookup launch per table even where every table could
                                     share the single persistent launch (for comparison)          */
+#define PLANB_MULTI_BUCKETED 4u  /* flag: group the batch by table even where every table could
+                                    take the direct launch (for comparison)                      */
+#define PLANB_MULTI_DIRECT 8u    /* flag: the direct launch at every batch size where the tables
+                                    allow it (for comparison)                                    */
 int planb_multi_create(planb_fib *const *fibs, uint32_t n_tables, size_t max_batch,
                        uint32_t flags, planb_multi **out);
 
 /*
  * planb_multi_lookup — next hop of n addresses, address i looked up in table d_table[i]
  * (ids >= n_tables give 0). d_addr_hi, d_addr_lo: device u64 arrays; d_table: device u8 array;
- * d_out: device u16 array; all of n entries. The batch is grouped by table (a counting sort on the
- * device); when every table uses the hybrid kernel (any format) and every index fits the shared
- * memory of a 512-thread CTA, one persistent launch looks up all groups — the CTAs claim pieces
- * of the grouped batch in order and stage the index of each table they meet — else each table's
- * group gets its own launch; results are gathered back into the input order. The whole
- * pipeline is captured once as a CUDA graph and replayed while the buffers and n stay the same;
- * in the single-launch form a table swapped by planb_update reaches the replays through its
- * descriptor (copied in stream order), while new buffers, a change of the launch's shape, or a
+ * d_out: device u16 array; all of n entries. Three forms (planb_multi_mode):
+ *  - direct: when every table is an F16HI table of the hybrid kernel (of fewer than 2^24 nodes,
+ *    about 268 million keys), one persistent launch looks up the batch in input order, each
+ *    address in its own table through that table's in-place index, and writes each result at its
+ *    input position. It reads every table's lines at once, so it is taken while those fit in L2
+ *    (at most 32 MB of leaf high halves, next-hop words and index) or the batch has at most 2^24
+ *    addresses (max_n for planb_multi_lookup_devn), and at every size with PLANB_MULTI_DIRECT;
+ *  - bucketed: else, the batch is grouped by table (a counting sort on the device). When every
+ *    table uses the hybrid kernel (any format), one persistent launch looks up all groups: the
+ *    CTAs claim pieces of the grouped batch in order and stage the index of each table they meet;
+ *    results are gathered back into the input order;
+ *  - per-table: else, each table's group gets its own launch.
+ * The whole pipeline is captured once as a CUDA graph and replayed while the buffers and n stay
+ * the same. In the single-launch forms, a table swapped by planb_update reaches the replays
+ * through its record (copied in stream order). New buffers, a change of the launch's shape, or a
  * swap under per-table launches cause one new capture. Enqueued on
  * `stream`; calls on one group are serialised on the host, and since the group's device scratch
  * is reused by every call, all calls on one group must use the same stream.
@@ -314,11 +325,19 @@ int planb_multi_lookup_devn(planb_multi *m, const uint64_t *d_addr_hi, const uin
                             const uint8_t *d_table, const uint64_t *d_n, size_t max_n,
                             uint16_t *d_out, planb_stream_t stream);
 
-/* planb_multi_persistent — 1 when the group's lookups run as the single persistent launch (every
- * table a hybrid F8X128/F8V7 table whose index fits one CTA's shared memory, and no
- * PLANB_MULTI_PER_TABLE flag), 0 when each table gets its own launch. Decided at the first lookup
- * and again whenever a table is swapped; 0 before the first lookup. Errors: PLANB_EINVAL. */
+/* planb_multi_persistent — 1 when the group's lookups run as a single persistent launch (the
+ * direct or the bucketed form of planb_multi_lookup), 0 when each table gets its own launch.
+ * Decided at the first lookup and again whenever a table is swapped; 0 before the first lookup.
+ * Errors: PLANB_EINVAL. */
 int planb_multi_persistent(const planb_multi *m);
+
+/* planb_multi_mode — the form of the group's last lookup: PLANB_MULTI_MODE_DIRECT,
+ * PLANB_MULTI_MODE_BUCKETED (grouped by table, one persistent launch) or
+ * PLANB_MULTI_MODE_PER_TABLE (also before the first lookup). Errors: PLANB_EINVAL. */
+#define PLANB_MULTI_MODE_PER_TABLE 0
+#define PLANB_MULTI_MODE_BUCKETED 1
+#define PLANB_MULTI_MODE_DIRECT 2
+int planb_multi_mode(const planb_multi *m);
 
 /* planb_multi_captures — how many times the group has captured its graph (the first lookup,
  * then once per table swap or buffer change seen by a lookup); 0 for NULL. */

@@ -110,6 +110,7 @@ _SIGS = {
     "planb_multi_lookup": (C.c_int, [_vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_multi_destroy": (None, [_vp]),
     "planb_multi_persistent": (C.c_int, [_vp]),
+    "planb_multi_mode": (C.c_int, [_vp]),
     "planb_multi_captures": (C.c_uint64, [_vp]),
     "planb_multi_lookup_devn": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "planb_server_opts_default": (None, [_vp]),
@@ -442,13 +443,17 @@ def _host_ptrs(hi, lo):
 class MultiFib:
     """Several tables (VRFs) looked up by one captured graph; each address carries a table id."""
 
-    def __init__(self, fibs, max_batch: int, graph: bool = True, per_table: bool = False):
+    MODES = ("per_table", "bucketed", "direct")   # planb_multi_mode's values, in order
+
+    def __init__(self, fibs, max_batch: int, graph: bool = True, per_table: bool = False,
+                 bucketed: bool = False, direct: bool = False):
         self._lib = fibs[0]._lib
         self._h = None
         self.fibs = list(fibs)                 # keep the tables alive while the group exists
         arr = (C.c_void_p * len(fibs))(*[f._h.value for f in fibs])
         h = C.c_void_p()
-        flags = (0 if graph else 1) | (2 if per_table else 0)
+        flags = ((0 if graph else 1) | (2 if per_table else 0) | (4 if bucketed else 0) |
+                 (8 if direct else 0))
         _check(self._lib.planb_multi_create(arr, len(fibs), max_batch, flags, C.byref(h)),
                "planb_multi_create")
         self._h = h
@@ -480,6 +485,15 @@ class MultiFib:
         if rc < 0:
             _check(rc, "planb_multi_persistent")
         return rc == 1
+
+    @property
+    def mode(self) -> str:
+        """The form of the last lookup: "direct" (input order, no bucketing), "bucketed" (grouped
+        by table, one persistent launch) or "per_table" (also before the first lookup)."""
+        rc = self._lib.planb_multi_mode(self._h)
+        if rc < 0:
+            _check(rc, "planb_multi_mode")
+        return self.MODES[rc]
 
     def lookup_ptr(self, hi_ptr: int, lo_ptr: int, tid_ptr: int, n: int, out_ptr: int, stream=None):
         _check(self._lib.planb_multi_lookup(self._h, C.c_void_p(hi_ptr), C.c_void_p(lo_ptr),
@@ -540,7 +554,7 @@ class Server:
 
     def __init__(self, slots: int = 4, max_batch: int = 1 << 18, max_request: int = 1 << 16,
                  mem_budget: int = 0, update_period_us: int = 10_000, device: int | None = None,
-                 per_table: bool = False):
+                 per_table: bool = False, bucketed: bool = False):
         self._lib = load()
         self._h = None
         o = ServerOpts()
@@ -548,7 +562,7 @@ class Server:
         o.slots, o.max_batch, o.max_request = slots, max_batch, max_request
         o.mem_budget, o.update_period_us = mem_budget, update_period_us
         o.device = -1 if device is None else device
-        o.multi_flags = 2 if per_table else 0
+        o.multi_flags = (2 if per_table else 0) | (4 if bucketed else 0)
         h = C.c_void_p()
         _check(self._lib.planb_server_create(C.byref(o), C.byref(h)), "planb_server_create")
         self._h = h

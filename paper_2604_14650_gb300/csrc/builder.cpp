@@ -330,16 +330,16 @@ void fill_dir(const uint64_t* sidx, uint64_t n, const DirParams& p, uint16_t* di
   }
 }
 
-uint32_t bucket_dir_bits_for(uint64_t n) {
+uint32_t bucket_dir_bits_for(uint64_t n, uint32_t extra) {
   if (n == 0 || n >= (uint64_t(1) << 31)) return 0;
   uint32_t lg = 0;
   while ((uint64_t(1) << lg) < n) lg++;
-  return std::min<uint32_t>(20, std::max<uint32_t>(4, lg + 2));   // about four buckets per entry
+  return std::min<uint32_t>(20, std::max<uint32_t>(4, lg + extra));   // 2^extra buckets per entry
 }
 
-BucketDir bucket_dir_params(const uint64_t* sidx, uint64_t n) {
+BucketDir bucket_dir_params(const uint64_t* sidx, uint64_t n, uint32_t extra) {
   BucketDir p;
-  p.bits = bucket_dir_bits_for(n);
+  p.bits = bucket_dir_bits_for(n, extra);
   if (!p.bits) return p;
   const uint64_t lo = sidx[0], hi = sidx[2 * (n - 1)];
   const uint64_t cap = uint64_t(1) << p.bits;

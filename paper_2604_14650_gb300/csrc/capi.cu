@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -257,6 +258,17 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
   planb::BucketDir bdp;
   if (kernel == planb::kHybrid && format == PLANB_FMT_F16HI) bdp.bits = planb::bucket_dir_bits_for(sidx_n);
   const size_t bdb = planb::bucket_dir_bytes(bdp);
+  // F16HI hybrid with two or more levels below its index: an index of the leaf level too, with a
+  // bucket directory of about two buckets per entry, for the direct multi-table launch's in-place
+  // search (one L2 level below it instead of two or more)
+  const bool f16hyb = kernel == planb::kHybrid && format == PLANB_FMT_F16HI;
+  const uint64_t lidx_n =
+      (f16hyb && s + 1 < t->L.D) ? planb::sidx_entries(t->L, t->L.D - 1) : 0;
+  const size_t lidx_bytes = ((lidx_n * 16 + 127) / 128) * 128;
+  planb::BucketDir lbp;
+  if (lidx_n) lbp.bits = planb::bucket_dir_bits_for(lidx_n, 1);
+  const size_t lbdb = planb::bucket_dir_bytes(lbp);
+  const size_t lidx_off = node_bytes + lo_bytes + sidx_bytes + dirb + bdb;
   // next hops: u16 per interval; F16HI: u32 words that also flag possible high-half ties
   const size_t vw = format == PLANB_FMT_F16HI ? 4 : 2;
   const size_t val_bytes = ((static_cast<size_t>(m) * vw + 255) / 256) * 256;
@@ -264,7 +276,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
       learned ? ((static_cast<size_t>(model_leaves) * 18 + 255) / 256) * 256 : 0;
   std::vector<uint64_t> host;
   if (!on_dev) {
-    host.resize((node_bytes + lo_bytes + sidx_bytes + dirb + bdb) / 8);
+    host.resize((lidx_off + lidx_bytes + lbdb) / 8);
     if (format == PLANB_FMT_F16HI)
       planb::fill_f16hi(iv, t->L, host.data(), host.data() + node_bytes / 8);
     else if (format == PLANB_FMT_F8V7)
@@ -288,6 +300,14 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
       planb::fill_bucket_dir(sx, sidx_n, bdp,
                              host.data() + (node_bytes + lo_bytes + sidx_bytes + dirb) / 8);
     }
+    if (lidx_n) {
+      uint64_t* lx = host.data() + lidx_off / 8;
+      planb::fill_sidx(iv, t->L, t->L.D - 1, lx);
+      const uint32_t bits = lbp.bits;
+      lbp = planb::bucket_dir_params(lx, lidx_n, 1);
+      if (lbp.bits != bits) return fail_detail(PLANB_EINVAL, "leaf bucket directory size");
+      planb::fill_bucket_dir(lx, lidx_n, lbp, host.data() + (lidx_off + lidx_bytes) / 8);
+    }
   }
   t->build_ms = ms_since(t0);
 
@@ -306,7 +326,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                               model_leaves, iters, 0.01f, 64u, t->model);
     if (rc) return rc;
   }
-  t->bytes = node_bytes + lo_bytes + sidx_bytes + dirb + bdb + val_bytes + model_bytes;
+  t->bytes = lidx_off + lidx_bytes + lbdb + val_bytes + model_bytes;
   if (g_inject.load() == 2) {
     g_inject.store(0);
     return PLANB_ENOMEM;
@@ -317,7 +337,7 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
     return PLANB_ENOMEM;
   }
   char* base = static_cast<char*>(t->mem);
-  const size_t head = node_bytes + lo_bytes + sidx_bytes + dirb + bdb;
+  const size_t head = lidx_off + lidx_bytes + lbdb;
   t->dump_bytes = head + m * vw;
   if (on_dev) {
     // the index region's rounding tail is zero, as in the host-filled image
@@ -331,6 +351,15 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                          reinterpret_cast<uint64_t*>(base + node_bytes + lo_bytes),
                          base + head, bs->s);
     if (rc) return fail_detail(rc, "device layout fill", cudaGetLastError());
+    if (lidx_n) {
+      const size_t used = static_cast<size_t>(lidx_n) * 16;
+      if (lidx_bytes > used &&
+          cudaMemsetAsync(base + lidx_off + used, 0, lidx_bytes - used, bs->s) != cudaSuccess)
+        return PLANB_ECUDA;
+      rc = planb::gpu_fill_index(giv, t->L, t->L.D - 1, lidx_n,
+                                 reinterpret_cast<uint64_t*>(base + lidx_off), bs->s);
+      if (rc) return fail_detail(rc, "device leaf index fill", cudaGetLastError());
+    }
     if (cudaStreamSynchronize(bs->s) != cudaSuccess)
       return fail_detail(PLANB_ECUDA, "device layout fill", cudaGetLastError());
     if (dp.bits || bdp.bits) {   // the directories come from the index the device just wrote
@@ -358,6 +387,19 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                        cudaMemcpyHostToDevice) != cudaSuccess)
           return PLANB_ECUDA;
       }
+    }
+    if (lidx_n) {   // the leaf index's directory likewise
+      std::vector<uint64_t> lx(lidx_n * 2), bh(lbdb / 8, 0);
+      if (cudaMemcpy(lx.data(), base + lidx_off, lidx_n * 16, cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+        return PLANB_ECUDA;
+      const uint32_t bits = lbp.bits;
+      lbp = planb::bucket_dir_params(lx.data(), lidx_n, 1);
+      if (lbp.bits != bits) return fail_detail(PLANB_EINVAL, "leaf bucket directory size");
+      planb::fill_bucket_dir(lx.data(), lidx_n, lbp, bh.data());
+      if (cudaMemcpy(base + lidx_off + lidx_bytes, bh.data(), lbdb, cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+        return PLANB_ECUDA;
     }
   } else {
     std::vector<uint32_t> words;
@@ -393,6 +435,22 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                                                           sidx_bytes + dirb)
                        : nullptr;
   t->dt.bdp = bdp;
+  if (f16hyb && lidx_n) {
+    t->dt.lidx = reinterpret_cast<const uint64_t*>(base + lidx_off);
+    t->dt.lidx_n = lidx_n;
+    t->dt.lidx_node = t->L.internal_nodes;   // the first leaf
+    t->dt.lidx_db = 1;
+    t->dt.lbdir = lbp.bits ? reinterpret_cast<const uint64_t*>(base + lidx_off + lidx_bytes)
+                           : nullptr;
+    t->dt.lbdp = lbp;
+  } else if (f16hyb) {   // at most one level below the top-of-tree index: it serves
+    t->dt.lidx = t->dt.sidx;
+    t->dt.lidx_n = sidx_n;
+    t->dt.lidx_node = t->dt.sidx_node;
+    t->dt.lidx_db = t->L.D - s;
+    t->dt.lbdir = t->dt.bdir;
+    t->dt.lbdp = bdp;
+  }
   t->dt.dir_bits = dp.bits;
   t->dt.dir_shift = dp.shift;
   t->dt.dir_base = dp.base;
@@ -1078,6 +1136,13 @@ struct planb_multi {
   bool persist = false;          // the current tables all fit the single persistent launch
   int persist_ctas = 0;
   size_t persist_smem = 0;
+  bool direct_ok = false;        // the current tables can all take the direct launch
+  bool direct = false;           // the direct launch is the form of the current graph
+  uint64_t direct_hot = 0;       // bytes of table lines the direct launch keeps reading
+  int direct_ctas = 0;
+  bool g_direct = false;         // the form the captured graph was made with
+  planb::DirectRec* drec = nullptr;     // per-table records of the direct launch
+  planb::DirectRec* hdrec = nullptr;    // page-locked staging of the records
   cudaStream_t cap_stream = nullptr;
   static constexpr int kBranches = 4;          // per-table lookups run on this many streams
   cudaStream_t side[kBranches] = {};
@@ -1102,6 +1167,12 @@ namespace {
 int multi_pipeline(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cur,
                    const uint64_t* d_addr_hi, const uint64_t* d_addr_lo, const uint8_t* d_table,
                    size_t n, uint16_t* d_out, cudaStream_t s, const uint64_t* d_n, bool fork) {
+  if (m->direct) {   // one launch, in input order: nothing to bucket or gather
+    const int rc = planb::launch_multi_direct(m->drec, m->T, d_addr_hi, d_addr_lo, d_table, n,
+                                              d_n, d_out, m->fibs[0]->d_status, m->direct_ctas,
+                                              s);
+    return rc ? fail_detail(rc, "multi: direct lookup", cudaGetLastError()) : PLANB_OK;
+  }
   int rc = planb::launch_bucketing(d_addr_hi, d_table, n, m->T, m->G, m->counts, m->range,
                                    m->bhi, m->bsrc, m->where, m->tile_start, m->tile_base, s,
                                    d_n);
@@ -1183,7 +1254,8 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     const size_t desc_off = range_off + up((2 * m->T + 4) * 8);
     const size_t tstart_off = desc_off + up(m->T * sizeof(planb::MultiDesc));
     const size_t tbase_off = tstart_off + up(tiles * 4);
-    const size_t bytes = tbase_off + up(tiles * 2);
+    const size_t drec_off = tbase_off + up(tiles * 2);
+    const size_t bytes = drec_off + up(m->T * sizeof(planb::DirectRec));
     if (cudaMalloc(&m->mem, bytes) != cudaSuccess) {
       m->mem = nullptr;
       cudaGetLastError();
@@ -1199,11 +1271,14 @@ int planb_multi_create(planb_fib* const* fibs, uint32_t n_tables, size_t max_bat
     m->counts = reinterpret_cast<uint32_t*>(b + counts_off);
     m->range = reinterpret_cast<uint64_t*>(b + range_off);
     m->desc = reinterpret_cast<planb::MultiDesc*>(b + desc_off);
+    m->drec = reinterpret_cast<planb::DirectRec*>(b + drec_off);
     bool ok = cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&m->desc_copied, cudaEventDisableTiming) == cudaSuccess &&
               cudaHostAlloc(reinterpret_cast<void**>(&m->hdesc),
-                            m->T * sizeof(planb::MultiDesc), cudaHostAllocDefault) == cudaSuccess;
+                            m->T * sizeof(planb::MultiDesc), cudaHostAllocDefault) == cudaSuccess &&
+              cudaHostAlloc(reinterpret_cast<void**>(&m->hdrec),
+                            m->T * sizeof(planb::DirectRec), cudaHostAllocDefault) == cudaSuccess;
     for (int k = 0; ok && k < planb_multi::kBranches; k++)
       ok = cudaStreamCreateWithFlags(&m->side[k], cudaStreamNonBlocking) == cudaSuccess &&
            cudaEventCreateWithFlags(&m->join[k], cudaEventDisableTiming) == cudaSuccess;
@@ -1249,10 +1324,51 @@ namespace {
 int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>>& cur,
                         cudaStream_t st) {
   m->persist = false;
+  m->direct_ok = false;
   if (m->flags & PLANB_MULTI_PER_TABLE) return PLANB_OK;
-  // the staging buffer is reused: its previous copy must have been made
+  // the staging buffers are reused: their previous copy must have been made
   const cudaError_t ew = cudaEventSynchronize(m->desc_copied);
   if (ew != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: descriptor staging", ew);
+  if (!(m->flags & PLANB_MULTI_BUCKETED)) {
+    // The direct launch: every table F16HI hybrid with at most one level below its in-place
+    // index, of fewer than 2^24 nodes (a node and its table share one 32-bit word in the group
+    // hand-off) and 2^32 intervals.
+    bool can = true;
+    for (uint32_t t = 0; can && t < m->T; t++) {
+      const planb::DevTable& d = cur[t]->dt;
+      can = d.format == PLANB_FMT_F16HI && d.kernel == planb::kHybrid && d.lidx_db <= 1 &&
+            (!d.lidx_n || d.lbdir) && d.total_nodes < (uint64_t(1) << 24) &&
+            d.n_intervals <= (uint64_t(1) << 32);
+    }
+    int ctas = 0;
+    if (can && planb::multi_direct_setup(m->device, m->T, &ctas) == PLANB_OK) {
+      m->direct_hot = 0;
+      for (uint32_t t = 0; t < m->T; t++) {
+        const planb::DevTable& d = cur[t]->dt;
+        // leaf high halves and next-hop words, 12 bytes per interval, the index and directory
+        m->direct_hot += d.n_intervals * 12u + d.lidx_n * 16u +
+                         (d.lbdir ? (uint64_t(16) << d.lbdp.bits) : 0u);
+        planb::DirectRec& r = m->hdrec[t];
+        r.idx = d.lidx_n ? d.lidx : nullptr;
+        r.bdir = d.lidx_n ? d.lbdir : nullptr;
+        r.bdir_base = d.lbdp.base;
+        r.packed = d.lbdp.bits | (d.lbdp.shift << 8) | (d.lidx_db << 16);
+        r.idx_node = static_cast<uint32_t>(d.lidx_node);
+        r.nodes = static_cast<const uint64_t*>(d.nodes);
+        r.words = reinterpret_cast<const uint32_t*>(d.values);
+        r.nodes_lo = d.nodes_lo;
+        r.nk = static_cast<uint32_t>(d.n_intervals - 1);
+        r.internal_nodes = static_cast<uint32_t>(d.internal_nodes);
+      }
+      cudaError_t e = cudaMemcpyAsync(m->drec, m->hdrec, m->T * sizeof(planb::DirectRec),
+                                      cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaEventRecord(m->desc_copied, st);
+      if (e != cudaSuccess) return fail_detail(PLANB_ECUDA, "multi: direct records", e);
+      m->direct_ok = true;
+      m->direct_ctas = ctas;
+    }
+    cudaGetLastError();
+  }
   planb::MultiDesc* hd = m->hdesc;
   uint64_t max_n = 0;
   for (uint32_t t = 0; t < m->T; t++) {
@@ -1333,19 +1449,33 @@ int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t*
   // carry the table pointers in their parameters and are captured again.
   bool reshape = false;
   if (changed) {
-    const bool was = m->persist;
-    const int ctas = m->persist_ctas;
+    const bool was = m->persist, was_direct = m->direct_ok;
+    const int ctas = m->persist_ctas, dctas = m->direct_ctas;
     const size_t smem = m->persist_smem;
     int rc = refresh_descriptors(m, cur, st);
     if (rc) return rc;
-    reshape = !m->persist || !was || ctas != m->persist_ctas || smem != m->persist_smem;
+    // per-table launches carry the tables in their parameters; the single launches read records
+    // copied in stream order, unless the launch's own parameters changed
+    reshape = (!m->persist && !m->direct_ok) || was != m->persist ||
+              was_direct != m->direct_ok ||
+              (m->persist && (ctas != m->persist_ctas || smem != m->persist_smem)) ||
+              (m->direct_ok && dctas != m->direct_ctas);
   }
+  // The direct form reads every table's lines at once: while they stay in L2 it beats grouping
+  // the batch by table at every size; past that, only up to a batch size where the grouping's
+  // passes cost more than the direct form's L2 misses (64 tables, 3.9 M prefixes, about 123 MB of
+  // table lines: the direct form is ahead up to 2^24 addresses, the grouping from 2^25).
+  constexpr uint64_t kDirectHotAll = uint64_t(32) << 20;
+  constexpr size_t kDirectMaxBatch = size_t(1) << 24;
+  m->direct = m->direct_ok && ((m->flags & PLANB_MULTI_DIRECT) || m->direct_hot <= kDirectHotAll ||
+                               n <= kDirectMaxBatch || !m->persist);
   if (m->flags & PLANB_MULTI_NO_GRAPH) {
     if (changed) m->snap = cur;
     return multi_pipeline(m, cur, d_addr_hi, d_addr_lo, d_table, n, d_out, st, d_n, false);
   }
   const bool same = !reshape && m->exec && m->g_hi == d_addr_hi && m->g_lo == d_addr_lo &&
-                    m->g_tid == d_table && m->g_out == d_out && m->g_n == n && m->g_dn == d_n;
+                    m->g_tid == d_table && m->g_out == d_out && m->g_n == n && m->g_dn == d_n &&
+                    m->g_direct == m->direct;
   if (same && changed) m->snap = cur;   // the replayed graph reads the new descriptors
   if (!same) {
     // a table was swapped by an update, or the buffers changed: capture the pipeline again
@@ -1380,6 +1510,7 @@ int multi_lookup_impl(planb_multi* m, const uint64_t* d_addr_hi, const uint64_t*
     m->g_out = d_out;
     m->g_n = n;
     m->g_dn = d_n;
+    m->g_direct = m->direct;
     m->snap = cur;
   }
   const cudaError_t eg = cudaGraphLaunch(m->exec, st);
@@ -1399,7 +1530,14 @@ uint64_t planb_multi_captures(const planb_multi* m) {
 int planb_multi_persistent(const planb_multi* m) {
   if (!m) return PLANB_EINVAL;
   std::lock_guard<std::mutex> lk(const_cast<planb_multi*>(m)->mu);
-  return m->persist ? 1 : 0;
+  return (m->persist || m->direct) ? 1 : 0;
+}
+
+int planb_multi_mode(const planb_multi* m) {
+  if (!m) return PLANB_EINVAL;
+  std::lock_guard<std::mutex> lk(const_cast<planb_multi*>(m)->mu);
+  return m->direct ? PLANB_MULTI_MODE_DIRECT
+                   : (m->persist ? PLANB_MULTI_MODE_BUCKETED : PLANB_MULTI_MODE_PER_TABLE);
 }
 
 void planb_multi_destroy(planb_multi* m) {
@@ -1416,6 +1554,7 @@ void planb_multi_destroy(planb_multi* m) {
     if (m->fork) cudaEventDestroy(m->fork);
     if (m->desc_copied) cudaEventDestroy(m->desc_copied);
     if (m->hdesc) cudaFreeHost(m->hdesc);
+    if (m->hdrec) cudaFreeHost(m->hdrec);
     if (m->mem) cudaFree(m->mem);
   }
   delete m;

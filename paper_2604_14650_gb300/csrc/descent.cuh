@@ -197,6 +197,46 @@ __device__ __forceinline__ Quad ldg_quad(const uint64_t* p) {
   return q;
 }
 
+// L2 eviction policies (sm_80+ createpolicy): evict-first for data streamed through once (a
+// batch's addresses and results), evict-last for table lines that later lookups read again, so a
+// large batch does not push a table set of L2's size out of it. (volatile: made where it is used,
+// one instruction, rather than held in two registers across a loop)
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t ldg_hint_u64(const uint64_t* p, uint64_t pol) {
+  uint64_t v;
+  asm("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ldg_hint_u8(const uint8_t* p, uint64_t pol) {
+  uint16_t v;
+  asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ uint32_t ldg_hint_u32(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void stg_hint_u16(uint16_t* p, uint16_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u16 [%0], %1, %2;" ::"l"(p), "h"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ Quad ldg_quad_hint(const uint64_t* p, uint64_t pol) {
+  Quad q;
+  asm("ld.global.nc.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%4], %5;"
+      : "=l"(q.a), "=l"(q.b), "=l"(q.c), "=l"(q.d)
+      : "l"(p), "l"(pol));
+  return q;
+}
+
 // Keys of a 16-key node below q for a 4-lane group (lane j of the group holds keys 4j .. 4j+3 in
 // k): one ballot per key slot; bit 4g + j of ballot s is key 4j + s of group g, so the group's
 // nibble of each of the four ballots, gathered into one word by byte permutes (`sel` picks byte

@@ -538,14 +538,7 @@ int gpu_fill(const GpuIntervals& iv, const Layout& L, uint32_t format, uint32_t 
     k_fill_nodes<2><<<blocks_for(slots), 256, 0, st>>>(g, ih, il, in, nd, nullptr);
   else
     k_fill_nodes<0><<<blocks_for(slots), 256, 0, st>>>(g, ih, il, in, nd, nullptr);
-  if (sidx_n) {
-    uint64_t span = 1;
-    if (S < L.D) {
-      span = L.kl;
-      for (uint32_t l = S; l + 1 < L.D; l++) span *= L.b;
-    }
-    k_fill_sidx<<<blocks_for(sidx_n), 256, 0, st>>>(sidx_n, span, ih, il, L.n_keys, iv.m, sidx);
-  }
+  if (sidx_n && gpu_fill_index(iv, L, S, sidx_n, sidx, stream)) return PLANB_ECUDA;
   if (format == PLANB_FMT_F16HI) {
     if (iv.m)
       k_nh_words<<<blocks_for(iv.m), 256, 0, st>>>(iv.m, il, in, static_cast<uint32_t*>(values));
@@ -553,6 +546,19 @@ int gpu_fill(const GpuIntervals& iv, const Layout& L, uint32_t format, uint32_t 
              cudaMemcpyAsync(values, in, iv.m * 2, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
     return PLANB_ECUDA;
   }
+  return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+int gpu_fill_index(const GpuIntervals& iv, const Layout& L, uint32_t S, uint64_t n,
+                   uint64_t* out, void* stream) {
+  if (!n) return PLANB_OK;
+  uint64_t span = 1;   // keys under one level-S node
+  if (S < L.D) {
+    span = L.kl;
+    for (uint32_t l = S; l + 1 < L.D; l++) span *= L.b;
+  }
+  k_fill_sidx<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      n, span, iv.hi.as<uint64_t>(), iv.lo.as<uint64_t>(), L.n_keys, iv.m, out);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

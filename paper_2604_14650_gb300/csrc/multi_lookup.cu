@@ -1,6 +1,8 @@
 // Multi-table lookups in one persistent launch (the lookup stage of planb_multi_lookup).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "descent.cuh"
 #include "planb_internal.h"
 
@@ -228,7 +230,7 @@ __device__ __noinline__ void multi_tiles16(const MultiDesc& d, const uint64_t* U
     const LoRef lo_src{xlo, src, mine};
     w = settle_tie(keys_hi, keys_lo, nk, words, rank, w, my_hi,
                    [&lo_src, ok] { return ok ? *lo_src.ptr() : 0ull; });
-    if (ok) out[mine] = static_cast<uint16_t>(w);
+    if (ok) stg_hint_u16(out + mine, static_cast<uint16_t>(w), l2_policy_evict_first());
   }
 }
 
@@ -316,6 +318,127 @@ __global__ void __launch_bounds__(512, 2)
   }
 }
 
+
+// The direct multi-table lookup of F16HI tables: the batch in input order, with no bucketing.
+// Each lane takes its own address and that address's table: the table's record from shared
+// memory, the in-place search of its index through the bucket directory, then the one level
+// below it by the 4-lane groups of lookup_hybrid16. A group's four addresses may belong to four
+// tables: each hands its group the table id and the node as one word, and the group's lanes read
+// that table's node array from its record. The lane then reads the next-hop word, settles a
+// flagged count, and stores the result at the address's input position. An address is read once
+// and its result written once, both coalesced; the tables' lines come from L2.
+__global__ void __launch_bounds__(512, 2)
+    lookup_multi_direct(const DirectRec* __restrict__ recs, uint32_t T,
+                        const uint64_t* __restrict__ xhi, const uint64_t* __restrict__ xlo,
+                        const uint8_t* __restrict__ tid, uint64_t n,
+                        const uint64_t* __restrict__ d_n, uint16_t* __restrict__ out,
+                        uint32_t* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ulonglong2* rw = reinterpret_cast<ulonglong2*>(smem_raw);   // record t: words 4t .. 4t + 3
+  for (uint32_t i = threadIdx.x; i < 4u * T; i += blockDim.x)
+    rw[i] = reinterpret_cast<const ulonglong2*>(recs)[i];
+  __syncthreads();
+  if (d_n) n = min(n, *d_n);
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t g = lane >> 2;
+  const uint32_t j = lane & 3u;
+  const uint32_t sel = (g >> 1) | ((4u + (g >> 1)) << 4);
+  const uint32_t nib = (g & 1u) ? 0xF0F0F0F0u : 0x0F0F0F0Fu;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t stride = gridDim.x * blockDim.x;   // whole warps of 32
+  uint64_t nx_hi = 0;
+  uint32_t nx_t = 0xFFu;
+  {
+    const uint64_t first = warp * 32 + lane;
+    if (first < n) {
+      nx_hi = xhi[first];
+      nx_t = tid[first];
+    }
+  }
+  for (uint64_t b0 = warp * 32; b0 < n; b0 += stride) {
+    const uint64_t mine = b0 + lane;
+    const bool ok = mine < n;
+    const uint64_t my_hi = nx_hi;
+    const uint32_t t = nx_t;
+    {
+      // the batch streams through L2 once: evict-first, so it does not displace table lines
+      const uint64_t next = mine + stride;
+      nx_hi = 0ull;
+      nx_t = 0xFFu;
+      if (next < n) {
+        nx_hi = ldg_hint_u64(xhi + next, l2_policy_evict_first());
+        nx_t = ldg_hint_u8(tid + next, l2_policy_evict_first());
+      }
+    }
+    const bool valid = ok && t < T;
+    // t << 24 | the node below the index when the table has a level there, else the index count
+    uint32_t tn = 0;
+    bool below = false;
+    if (valid) {
+      const ulonglong2 w0 = rw[4u * t], w1 = rw[4u * t + 1u];
+      const uint32_t packed = static_cast<uint32_t>(w1.y);
+      if (w0.y)
+        tn = index_count_hi_bucket(reinterpret_cast<const ulonglong2*>(w0.x),
+                                   reinterpret_cast<const ulonglong2*>(w0.y), packed & 0xFFu,
+                                   (packed >> 8) & 0xFFu, w1.x, my_hi);
+      below = (packed >> 16) != 0u;
+      if (below) tn = (t << 24) | (tn + static_cast<uint32_t>(w1.y >> 32));
+    }
+    uint32_t my_c = 0;
+    const uint32_t act = __ballot_sync(kFull, below);
+    if (act) {
+      // all four addresses of a group in flight; an address with no level below its index (or
+      // no table) takes no load and counts nothing
+      uint64_t qh[4];
+      uint32_t an[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        qh[i] = __shfl_sync(kFull, my_hi, g * 4u + i);
+        an[i] = __shfl_sync(kFull, tn, g * 4u + i);
+      }
+      Quad kq[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        if ((act >> (g * 4u + i)) & 1u) {
+          const uint64_t* nodes = reinterpret_cast<const uint64_t*>(rw[4u * (an[i] >> 24) + 2u].x);
+          kq[i] = ldg_quad_hint(nodes + static_cast<uint64_t>(an[i] & 0xFFFFFFu) * 16u + j * 4u,
+                                l2_policy_evict_last());
+        } else {
+          kq[i] = Quad{~0ull, ~0ull, ~0ull, ~0ull};
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        const uint32_t c = quad_count(kq[i], qh[i], sel, nib);
+        if (j == static_cast<uint32_t>(i)) my_c = c;
+      }
+    }
+    uint32_t w = 0;
+    if (valid) {
+      const ulonglong2 w2 = rw[4u * t + 2u], w3 = rw[4u * t + 3u];
+      const uint32_t* words = reinterpret_cast<const uint32_t*>(w2.y);
+      const uint32_t internal = static_cast<uint32_t>(w3.y >> 32);
+      uint64_t rank = below ? static_cast<uint64_t>((tn & 0xFFFFFFu) - internal) * 16u + my_c
+                            : static_cast<uint64_t>(tn);
+      const uint64_t nk = static_cast<uint32_t>(w3.y);
+#ifdef PLANB_BOUNDS_CHECK
+      if (rank > nk) {
+        report(status, 4u);
+        rank = 0;
+      }
+#endif
+      w = ldg_hint_u32(words + rank, l2_policy_evict_last());
+      if (w & kTieBit) {
+        const uint64_t leaf0 = static_cast<uint64_t>(internal) * 16u;
+        w = settle_tie(reinterpret_cast<const uint64_t*>(w2.x) + leaf0,
+                       reinterpret_cast<const uint64_t*>(w3.x) + leaf0, nk, words, rank, w, my_hi,
+                       [xlo, mine] { return xlo[mine]; });
+      }
+    }
+    if (ok) stg_hint_u16(out + mine, static_cast<uint16_t>(w), l2_policy_evict_first());
+  }
+}
+
 }  // namespace
 
 int multi_persistent_setup(int device, size_t smem_bytes, int* ctas) {
@@ -345,6 +468,36 @@ int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t*
                             static_cast<cudaStream_t>(stream)>>>(d_desc, T, d_range, d_hi, d_lo,
                                                                  d_src, d_out, d_next_item,
                                                                  d_status);
+  return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+
+int multi_direct_setup(int device, uint32_t T, int* ctas) {
+  if (T == 0 || T > 255) return PLANB_EINVAL;
+  int sms = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &per_sm, reinterpret_cast<const void*>(lookup_multi_direct), 512,
+          static_cast<size_t>(T) * sizeof(DirectRec)) != cudaSuccess)
+    return PLANB_ECUDA;
+  if (per_sm < 1) return PLANB_EINVAL;
+  *ctas = sms * per_sm;
+  return PLANB_OK;
+}
+
+int launch_multi_direct(const DirectRec* d_recs, uint32_t T, const uint64_t* d_hi,
+                        const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
+                        const uint64_t* d_n, uint16_t* d_out, uint32_t* d_status, int ctas,
+                        void* stream) {
+  if (T == 0 || T > 255 || ctas < 1) return PLANB_EINVAL;
+  if (n == 0) return PLANB_OK;
+  const uint64_t warps = (static_cast<uint64_t>(n) + 31) / 32;   // one tile per warp at least
+  const uint64_t blocks = std::min<uint64_t>(static_cast<uint64_t>(ctas), (warps + 15) / 16);
+  cudaGetLastError();
+  lookup_multi_direct<<<static_cast<unsigned>(blocks), 512,
+                        static_cast<size_t>(T) * sizeof(DirectRec),
+                        static_cast<cudaStream_t>(stream)>>>(d_recs, T, d_hi, d_lo, d_tid, n,
+                                                             d_n, d_out, d_status);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

@@ -127,6 +127,9 @@ int gpu_fill(const GpuIntervals& iv, const Layout& L, uint32_t format, uint32_t 
              uint64_t sidx_n, void* nodes, uint64_t* nodes_lo, uint64_t* sidx, void* values,
              void* stream);
 int gpu_download(const GpuIntervals& iv, void* stream, Intervals& out);
+// The index of level S alone (n entries, as fill_sidx) from the device intervals.
+int gpu_fill_index(const GpuIntervals& iv, const Layout& L, uint32_t S, uint64_t n,
+                   uint64_t* out, void* stream);
 
 // Linearized B+-tree arithmetic (Section 3.2).
 struct Layout {
@@ -195,12 +198,15 @@ struct BucketDir {
   uint32_t bits = 0, shift = 0;
   uint64_t base = 0;
 };
-BucketDir bucket_dir_params(const uint64_t* sidx /* 2 per entry */, uint64_t n);
+// extra: log2 of the buckets per entry, rounded up (2 for the index of the single-table in-place
+// search; 1 for the leaf-level index of a deeper table, which shares L2 with many other tables')
+BucketDir bucket_dir_params(const uint64_t* sidx /* 2 per entry */, uint64_t n,
+                            uint32_t extra = 2);
 inline size_t bucket_dir_bytes(const BucketDir& p) {
   return p.bits ? (size_t(1) << p.bits) * 16 : 0;
 }
 void fill_bucket_dir(const uint64_t* sidx, uint64_t n, const BucketDir& p, uint64_t* out);
-uint32_t bucket_dir_bits_for(uint64_t n);
+uint32_t bucket_dir_bits_for(uint64_t n, uint32_t extra = 2);
 
 // ------------------------------------------------------------------------- device side
 
@@ -231,6 +237,15 @@ struct DevTable {
   const LeafModel* leaves;  // learned: leaf models (device)
   const uint16_t* leaf_err; // learned: per-leaf window half-width (device)
   LearnedParams lp;         // learned: root weights and constants
+  // F16HI hybrid: the index searched in place by the direct multi-table launch, which leaves at
+  // most one level below it (the leaf level): the top-of-tree index itself when it does, else an
+  // index of the leaf level with its own bucket directory. lidx_db: levels below it (0 or 1).
+  const uint64_t* lidx = nullptr;
+  uint64_t lidx_n = 0;
+  uint64_t lidx_node = 0;
+  uint32_t lidx_db = 0;
+  const uint64_t* lbdir = nullptr;
+  BucketDir lbdp;
 };
 
 struct LaunchCfg {
@@ -291,6 +306,36 @@ int launch_multi_persistent(const MultiDesc* d_desc, uint32_t T, const uint64_t*
                             uint16_t* d_out,
                             unsigned long long* d_next_item, uint32_t* d_status, int ctas,
                             size_t smem_bytes, void* stream);
+
+// One F16HI table of the direct multi-table launch, 64 bytes (four 16-byte words, read from
+// shared memory by the lanes that need them):
+//   word 0: the in-place index (lidx) and its bucket directory (null: no index);
+//   word 1: the directory's base; bits | shift << 8 | db << 16; the first node below the index;
+//   word 2: the node array (high halves) and the next-hop words;
+//   word 3: the low halves; the key count and the internal node count (the tie path, the rank).
+struct DirectRec {
+  const uint64_t* idx;
+  const uint64_t* bdir;
+  uint64_t bdir_base;
+  uint32_t packed;
+  uint32_t idx_node;
+  const uint64_t* nodes;
+  const uint32_t* words;
+  const uint64_t* nodes_lo;
+  uint32_t nk;
+  uint32_t internal_nodes;
+};
+static_assert(sizeof(DirectRec) == 64, "direct record layout");
+
+// The direct multi-table kernel (multi_lookup.cu): every address of the batch looked up in input
+// order against table d_tid[i] of the T records (ids >= T give 0), the results written at their
+// input positions. Tables of fewer than 2^24 nodes and 2^32 intervals. n addresses, or
+// min(n, *d_n) when d_n is given. multi_direct_setup returns the persistent grid size.
+int multi_direct_setup(int device, uint32_t T, int* ctas);
+int launch_multi_direct(const DirectRec* d_recs, uint32_t T, const uint64_t* d_hi,
+                        const uint64_t* d_lo, const uint8_t* d_tid, size_t n,
+                        const uint64_t* d_n, uint16_t* d_out, uint32_t* d_status, int ctas,
+                        void* stream);
 
 // Multi-table bucketing (multi.cu): groups n addresses by their u8 table id (ids >= T form one
 // extra segment) into d_bhi (high halves), table-major, with d_bsrc[j] = the input position of

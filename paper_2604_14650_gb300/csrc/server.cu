@@ -344,7 +344,8 @@ int planb_server_create(const planb_server_opts* opts, planb_server** out) {
   }
   if (o.slots < 1 || o.slots > 64 || o.max_batch < 1 || o.max_request < 1 ||
       o.max_request > o.max_batch || o.update_period_us < 100 ||
-      (o.multi_flags & ~(PLANB_MULTI_NO_GRAPH | PLANB_MULTI_PER_TABLE)))
+      (o.multi_flags & ~(PLANB_MULTI_NO_GRAPH | PLANB_MULTI_PER_TABLE | PLANB_MULTI_BUCKETED |
+                          PLANB_MULTI_DIRECT)))
     return PLANB_EINVAL;
   try {
     std::unique_ptr<planb_server> m(new planb_server());

@@ -5,8 +5,9 @@ element by element, in the launch configurations the benchmark times:
   position model included): at this size the F16HI hybrid descends two levels from L2 below its
   shared-memory index and the learned F8 tables three;
 * 64 tables (VRFs) of log-uniform size between 1,000 and 300,000 prefixes and 2^27 addresses
-  tagged with a table id drawn proportional to table size, in the single persistent launch and
-  with one launch per table, for F16HI and F8X128 tables;
+  tagged with a table id drawn proportional to table size, in every form of the multi-table
+  lookup (direct, bucketed in one persistent launch, one launch per table), for F16HI and F8X128
+  tables;
 * the 200,000-prefix table under the locality-skewed trace (Zipf(1.1) over 10^5 hot /64 blocks).
 """
 import os
@@ -89,14 +90,17 @@ def vrf64():
     return sizes, fibs, tid, xh, xl, want
 
 
-@pytest.mark.parametrize("per_table", [False, True], ids=["persistent", "per_table"])
-@pytest.mark.parametrize("fmt", ["f16hi", "f8x128"])
-def test_vrf64_full_size_parity(vrf64, fmt, per_table):
+@pytest.mark.parametrize("fmt,mode", [("f16hi", "direct"), ("f16hi", "bucketed"),
+                                      ("f16hi", "per_table"), ("f8x128", "bucketed"),
+                                      ("f8x128", "per_table"), ("f16hi", "auto")])
+def test_vrf64_full_size_parity(vrf64, fmt, mode):
     sizes, fibs_in, tid, xh, xl, want = vrf64
     assert sizes.sum() > 2_000_000 and tid.size == 1 << 27
     fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) for f in fibs_in]
+    per_table = mode == "per_table"
     try:
-        with pb.MultiFib(fibs, max_batch=tid.size, per_table=per_table) as mt:
+        with pb.MultiFib(fibs, max_batch=tid.size, per_table=per_table,
+                         bucketed=mode == "bucketed", direct=mode == "direct") as mt:
             dh, dl, dt = dev(xh), dev(xl), dev(tid, np.uint8)
             out = torch.empty(tid.size, dtype=torch.int16, device="cuda")
             for _ in range(2):                 # the capture, then a replay of the graph
@@ -106,7 +110,9 @@ def test_vrf64_full_size_parity(vrf64, fmt, per_table):
                 got = out.cpu().numpy().view(np.uint16)
                 bad = int(np.count_nonzero(got != want))
                 assert bad == 0, f"{bad} of {want.size} differ"
+            # auto: 2^27 addresses over about 123 MB of table lines are grouped by table
             assert mt.persistent == (not per_table)
+            assert mt.mode == (mode if mode != "auto" else "bucketed")
             del dh, dl, dt, out
     finally:
         for f in fibs:

@@ -1,7 +1,9 @@
-"""Multi-table (VRF) lookups: each address carries a u8 table id; one captured graph buckets the
-batch by table, looks every group up — in one persistent launch when every table uses the hybrid
-kernel, else one launch per table — and gathers results back into input order. Checked bit-exactly
-against the oracle of each table, in both launch modes, captured and direct."""
+"""Multi-table (VRF) lookups: each address carries a u8 table id. When every table is an F16HI
+hybrid table, one persistent launch looks the batch up in input order (the direct form); else one
+captured graph buckets the batch by table, looks every group up — in one persistent launch when
+every table uses the hybrid kernel, else one launch per table — and gathers results back into
+input order. Checked bit-exactly against the oracle of each table, in every form, captured and
+launched directly."""
 import numpy as np
 import pytest
 
@@ -204,10 +206,53 @@ def test_large_index_is_searched_in_place():
     fibs_in, tid, xh, xl = workload(sizes, 400_000, seed=81)
     fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format="f16hi") for f in fibs_in]
     assert fibs[0].stats()["smem_bytes"] > 96 * 1024 > fibs[1].stats()["smem_bytes"]
-    with pb.MultiFib(fibs, max_batch=400_000) as mt:
+    with pb.MultiFib(fibs, max_batch=400_000, bucketed=True) as mt:
         out = mt.lookup(dev(xh), dev(xl), dev(tid, np.uint8))
         torch.cuda.synchronize()
-        assert mt.persistent
+        assert mt.persistent and mt.mode == "bucketed"
+        assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
+    for f in fibs:
+        f.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_direct_form_matches_oracle_and_bucketed(graph):
+    """The direct form over F16HI tables of every shape it meets: a table of the default route
+    alone (no index), tiny tables whose index holds every key (nothing below it), tables whose
+    top-of-tree index sits right above the leaves, and tables whose index sits two or more levels
+    higher (forced by smem_levels), which the direct form searches through their extra leaf-level
+    index. Ids beyond the tables give 0; batch sizes that end mid-warp; the bucketed form of the
+    same group gives the same results."""
+    sizes = [1, 7, 500, 3000, 20_000, 60_000, 160_000, 12_000, 2500]
+    smem = {4: 0, 5: 1, 7: 2}          # index levels forced shallow: leaf index built
+    fibs_in, tid, xh, xl = workload(sizes, 700_001, seed=91)
+    want = expected(fibs_in, tid, xh, xl)
+    fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format="f16hi", smem_levels=smem.get(t, -1))
+            for t, f in enumerate(fibs_in)]
+    assert any(f.stats()["depth"] - f.stats()["smem_levels"] >= 2 for f in fibs)
+    dh, dl, dt = dev(xh), dev(xl), dev(tid, np.uint8)
+    for bucketed in (False, True):
+        with pb.MultiFib(fibs, max_batch=1 << 20, graph=graph, bucketed=bucketed) as mt:
+            for k in (tid.size, 33, 1):
+                out = torch.full((k,), -1, dtype=torch.int16, device="cuda")
+                mt.lookup(dh[:k], dl[:k], dt[:k], out=out)
+                torch.cuda.synchronize()
+                assert np.array_equal(out.cpu().numpy().view(np.uint16), want[:k]), (bucketed, k)
+            assert mt.persistent and mt.mode == ("bucketed" if bucketed else "direct")
+    for f in fibs:
+        f.close()
+
+
+def test_direct_form_needs_every_table_f16hi():
+    """One F8X128 table in the group: the batch is bucketed (the direct form reads F16HI nodes)."""
+    sizes = [3000, 20_000]
+    fibs_in, tid, xh, xl = workload(sizes, 100_000, seed=93)
+    fibs = [pb.Fib(fibs_in[0].hi, fibs_in[0].lo, fibs_in[0].len, fibs_in[0].nh, format="f16hi"),
+            pb.Fib(fibs_in[1].hi, fibs_in[1].lo, fibs_in[1].len, fibs_in[1].nh, format="f8x128")]
+    with pb.MultiFib(fibs, max_batch=100_000) as mt:
+        out = mt.lookup(dev(xh), dev(xl), dev(tid, np.uint8))
+        torch.cuda.synchronize()
+        assert mt.mode == "bucketed"
         assert np.array_equal(out.cpu().numpy().view(np.uint16), expected(fibs_in, tid, xh, xl))
     for f in fibs:
         f.close()

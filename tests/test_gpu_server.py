@@ -25,8 +25,12 @@ def built():
     pb.build()
 
 
-@pytest.mark.parametrize("fmt", ["f8x128", "f16hi"])
-def test_requests_in_the_mix_equal_alone(fmt):
+@pytest.mark.parametrize("fmt,bucketed", [("f8x128", False), ("f16hi", False), ("f16hi", True)],
+                         ids=["f8x128", "f16hi-direct", "f16hi-bucketed"])
+def test_requests_in_the_mix_equal_alone(fmt, bucketed):
+    """Requests batched by the serving loop get the results they get alone and the oracle's; the
+    slots' batches of F16HI tables take the direct multi-table form (or, asked, the grouped one),
+    with the batch size read from device memory."""
     sizes = [3000, 40_000, 700, 12_000, 90_000, 5000]
     fibs_in = [synth.gen_fib(s, seed=600 + t, nh_max=4095) for t, s in enumerate(sizes)]
     fibs = [pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt) for f in fibs_in]
@@ -37,7 +41,7 @@ def test_requests_in_the_mix_equal_alone(fmt):
         n = int(np.exp(rng.uniform(np.log(32), np.log(65536))))
         xh, xl = synth.gen_trace(fibs_in[t], n, seed=10_000 + i)
         reqs.append((t, xh, xl, np.zeros(n, np.uint16)))
-    with pb.Server(slots=3, max_batch=1 << 18) as srv:
+    with pb.Server(slots=3, max_batch=1 << 18, bucketed=bucketed) as srv:
         ids = [srv.add_table(f) for f in fibs]
         assert ids == list(range(len(sizes)))
         tickets = [None] * len(reqs)
