@@ -563,7 +563,8 @@ def run_planb(args):
     kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
     # the kernel's name as ncu prints it
     if kname == "hybrid" and args.format == "f16hi":
-        kernel = f"lookup_hybrid16<{st['depth'] - st['smem_levels']}, 0>"
+        # (an F16HI table's launch searches its leaf-level index in place: one level below it)
+        kernel = f"lookup_hybrid16<{min(1, st['depth'] - st['smem_levels'])}, 0>"
     elif kname == "hybrid":
         kernel = (f"lookup_hybrid<{st['depth'] - st['smem_levels']}, "
                   f"{1 if args.format == 'f8v7' else 0}, 0, 0, 0>")
@@ -816,9 +817,11 @@ def block_learned1m(args, stream, steps, warmup, lookups=1 << 28):
             ms = _timed_ms(lambda: fib.lookup_ptr(d_hi.data_ptr(), d_lo.data_ptr(), n,
                                                   d_out.data_ptr(), stream), stream, steps, warmup)
             st = fib.stats()
+            # an F16HI table's launch searches its leaf-level index in place (one level below)
+            below = st["depth"] - st["smem_levels"]
             res[name] = {"B_lookups_per_s": n / ms / 1e6, "ms_per_launch": ms,
                          "depth": st["depth"], "smem_levels": st["smem_levels"],
-                         "levels_from_l2": st["depth"] - st["smem_levels"]}
+                         "levels_from_l2": min(1, below) if kw.get("format") == "f16hi" else below}
             if kw.get("kernel") == "learned":
                 res[name]["model"] = {k[6:]: st[k] for k in st if k.startswith("model_")}
             if ref is None:
@@ -863,7 +866,7 @@ def block_zipf(args, stream, steps, warmup, fib_in=None, lookups=1 << 28):
     want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh[idx], xl[idx])
     parity = bool(np.array_equal(d_out.cpu().numpy().view(np.uint16)[idx], want))
     del d_hi, d_lo, d_out
-    kernel = f"lookup_hybrid16<{st['depth'] - st['smem_levels']}, 0>"
+    kernel = f"lookup_hybrid16<{min(1, st['depth'] - st['smem_levels'])}, 0>"
     return {"workload": f"200,000-prefix FIB, {n} lookups, Zipf(1.1) over 1e5 hot /64 blocks",
             "value": n / ms / 1e6, "unit": UNIT, "steps": steps, "warmup": warmup,
             "ms_per_launch": ms, "roofline": _hbm_roofline(HBM_BYTES_PER_LOOKUP, n, ms, kernel),

@@ -2,8 +2,9 @@
 element by element, in the launch configurations the benchmark times:
 
 * 1,000,000 prefixes (+ ::/0) and 2^28 addresses, every node format and kernel (the learned
-  position model included): at this size the F16HI hybrid descends two levels from L2 below its
-  shared-memory index and the learned F8 tables three;
+  position model included): at this size the F16HI table's top-of-tree index sits two levels
+  above its leaves, so its launches search the leaf-level index in place, and the learned F8
+  tables descend three levels from L2;
 * 64 tables (VRFs) of log-uniform size between 1,000 and 300,000 prefixes and 2^27 addresses
   tagged with a table id drawn proportional to table size, in every form of the multi-table
   lookup (direct, bucketed in one persistent launch, one launch per table), for F16HI and F8X128
@@ -68,7 +69,8 @@ def test_million_prefix_full_size_parity(grown, variant):
     with pb.Fib(f.hi, f.lo, f.len, f.nh, format=fmt, kernel=kernel) as fib:
         st = fib.stats()
         if (fmt, kernel) == ("f16hi", "hybrid"):
-            assert st["depth"] - st["smem_levels"] == 2        # two L2 levels below the index
+            # two levels below the top-of-tree index: the leaf-level index serves the launches
+            assert st["depth"] - st["smem_levels"] == 2
         if kernel == "learned":
             assert st["model_iters"] > 0 and st["model_covered"] > 0.5
         got = lookup_all(fib, xh, xl)
