@@ -186,6 +186,14 @@ def measured_peaks_mhz() -> float:
         return 2070.0
 
 
+def f16_kernel_name(st) -> str:
+    """The name ncu prints for an F16HI hybrid table's single-table lookup kernel: the in-place
+    search of the index over the leaves (one level below it, four 256-thread CTAs per SM), or the
+    staged form when the index holds every key."""
+    return ("lookup_hybrid16<1, 0, 4>" if st["depth"] > st["smem_levels"]
+            else "lookup_hybrid16<0, 0, 0>")
+
+
 def recorded_counters(kernel: str):
     """Per-lookup counters of a kernel from the ncu capture summarised in profiles/traffic.json,
     if the kernel's source has not changed since the capture (else None)."""
@@ -563,8 +571,7 @@ def run_planb(args):
     kname = {1: "coop", 2: "hybrid", 3: "flat"}[st["kernel"]]
     # the kernel's name as ncu prints it
     if kname == "hybrid" and args.format == "f16hi":
-        # (an F16HI table's launch searches its leaf-level index in place: one level below it)
-        kernel = f"lookup_hybrid16<{min(1, st['depth'] - st['smem_levels'])}, 0>"
+        kernel = f16_kernel_name(st)
     elif kname == "hybrid":
         kernel = (f"lookup_hybrid<{st['depth'] - st['smem_levels']}, "
                   f"{1 if args.format == 'f8v7' else 0}, 0, 0, 0>")
@@ -866,7 +873,7 @@ def block_zipf(args, stream, steps, warmup, fib_in=None, lookups=1 << 28):
     want = oracle.Trie(f.hi, f.lo, f.len, f.nh).lookup(xh[idx], xl[idx])
     parity = bool(np.array_equal(d_out.cpu().numpy().view(np.uint16)[idx], want))
     del d_hi, d_lo, d_out
-    kernel = f"lookup_hybrid16<{min(1, st['depth'] - st['smem_levels'])}, 0>"
+    kernel = f16_kernel_name(st)
     return {"workload": f"200,000-prefix FIB, {n} lookups, Zipf(1.1) over 1e5 hot /64 blocks",
             "value": n / ms / 1e6, "unit": UNIT, "steps": steps, "warmup": warmup,
             "ms_per_launch": ms, "roofline": _hbm_roofline(HBM_BYTES_PER_LOOKUP, n, ms, kernel),

@@ -452,8 +452,9 @@ __global__ void __launch_bounds__(512, 2) lookup_hybrid(const KParams p) {
 // settle_tie finishes the count then. An address's low half is read only in that case.
 // MULTI: one table's launch within a multi-table batch (device-side address range, results through
 // the permutation when one is given).
-template <int DB, bool MULTI = false>
-__global__ void __launch_bounds__(1024, 1) lookup_hybrid16(const KParams p) {
+// IPB > 0: the in-place form's launch bounds, IPB 256-thread CTAs per SM (no shared memory).
+template <int DB, bool MULTI = false, int IPB = 0>
+__global__ void __launch_bounds__(IPB ? 256 : 1024, IPB ? IPB : 1) lookup_hybrid16(const KParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t N = p.sidx_n;
   uint64_t* Uh = reinterpret_cast<uint64_t*>(smem_raw);
@@ -579,6 +580,8 @@ __global__ void __launch_bounds__(256) lookup_flat(const KParams p) {
 
 typedef void (*KernelFn)(const KParams);
 
+constexpr int kInPlaceCtas = 4;   // 256-thread CTAs per SM of the in-place F16HI launch
+
 constexpr int kMaxDepth = 10;
 
 // db >= 0: the F16HI hybrid kernel for db levels below its index (an in-place search of another
@@ -661,10 +664,17 @@ KernelFn kernel_for(const DevTable& t, bool multi = false, bool lazy = false, in
   }
 }
 
+// Single-table launches on this table search its index over the leaves in place (see
+// launch_lookup).
+bool in_place(const DevTable& t) {
+  return t.kernel == kHybrid && t.format == PLANB_FMT_F16HI && t.lidx && t.lidx_db == 1;
+}
+
 }  // namespace
 
 int kernel_attributes(const DevTable& t, bool multi, int* out) {
   KernelFn fn = kernel_for(t, multi);
+  if (!multi && in_place(t)) fn = lookup_hybrid16<1, false, kInPlaceCtas>;   // what launches
   if (!fn) return PLANB_EINVAL;
   cudaFuncAttributes a;
   if (cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(fn)) != cudaSuccess) return PLANB_ECUDA;
@@ -790,11 +800,9 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
   // more). Four 256-thread CTAs per SM and no shared memory, so L1 keeps its full size for the
   // directory, index and leaf lines. Measured against the staged index: 79.5 against 79.0 B
   // lookups/s at 200 k prefixes, 77.4 against 61.8 at 1 M.
-  const bool leaf = !multi && t.kernel == kHybrid && t.format == PLANB_FMT_F16HI && t.lidx &&
-                    t.lidx_db == 1 && cfg.blocks > 0;
+  const bool leaf = !multi && in_place(t) && cfg.blocks > 0;
   if (leaf) {
-    fn = kernel_for(t, false, false, 1);
-    if (!fn) return PLANB_EINVAL;
+    fn = lookup_hybrid16<1, false, kInPlaceCtas>;
     p.sidx = reinterpret_cast<const ulonglong2*>(t.lidx);
     p.sidx_n = static_cast<uint32_t>(t.lidx_n);
     p.sidx_node = static_cast<uint32_t>(t.lidx_node);
@@ -806,7 +814,7 @@ int launch_lookup(const DevTable& t, const LaunchCfg& cfg, const uint64_t* d_hi,
     threads = 256;
     smem = 0;
     const uint64_t tiles = (n + 31) / 32;
-    blocks = std::min<uint64_t>((tiles + 7) / 8, static_cast<uint64_t>(cfg.blocks) * 4u);
+    blocks = std::min<uint64_t>((tiles + 7) / 8, static_cast<uint64_t>(cfg.blocks) * kInPlaceCtas);
   } else if (t.kernel == kFlat) {
     blocks = (n + cfg.threads - 1) / cfg.threads;
   } else {
