@@ -1396,6 +1396,19 @@ int refresh_descriptors(planb_multi* m, const std::vector<std::shared_ptr<Table>
     const uint64_t need = ((d.sidx_n + 1) & ~1ull) * 8u +
                           (d.dir_bits ? ((((1ull << d.dir_bits) + 1) + 7) & ~7ull) * 2u : 0u);
     x.staged = need <= kSmemBudget ? 1u : 0u;
+    if (d.lidx && d.lidx_db == 1 && d.lidx != d.sidx) {
+      // an F16HI index two or more levels above the leaves: search the leaf-level index in place
+      // instead (one level below the search, so a group keeps all four addresses in flight)
+      x.staged = 0;
+      x.sidx = d.lidx;
+      x.sidx_n = static_cast<uint32_t>(d.lidx_n);
+      x.sidx_node = static_cast<uint32_t>(d.lidx_node);
+      x.db = 1;
+      x.dir = nullptr;
+      x.dir_bits = 0;
+      x.bdir = d.lbdir;
+      x.bdp = d.lbdp;
+    }
     if (x.staged) max_n = std::max<uint64_t>(max_n, need);
   }
   // rounded up to 16 KB, so that a table growing a little keeps the captured launch's size,
