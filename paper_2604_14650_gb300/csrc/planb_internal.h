@@ -198,8 +198,7 @@ struct BucketDir {
   uint32_t bits = 0, shift = 0;
   uint64_t base = 0;
 };
-// extra: log2 of the buckets per entry, rounded up (2 for the index of the single-table in-place
-// search; 1 for the leaf-level index of a deeper table, which shares L2 with many other tables')
+// extra: log2 of the buckets per entry, rounded up (2: about four buckets per entry)
 BucketDir bucket_dir_params(const uint64_t* sidx /* 2 per entry */, uint64_t n,
                             uint32_t extra = 2);
 inline size_t bucket_dir_bytes(const BucketDir& p) {
