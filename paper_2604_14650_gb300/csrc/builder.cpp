@@ -310,15 +310,18 @@ uint32_t dir_bits_for(uint64_t n) {
   return std::min<uint32_t>(13, std::max<uint32_t>(4, lg + 1));   // about two buckets per entry
 }
 
-DirParams dir_params(const uint64_t* sidx, uint64_t n) {
+DirParams dir_params_ends(uint64_t lo, uint64_t hi, uint64_t n) {
   DirParams p;
   p.bits = dir_bits_for(n);
   if (!p.bits) return p;
-  const uint64_t lo = sidx[0], hi = sidx[2 * (n - 1)];
   const uint64_t cap = uint64_t(1) << p.bits;
   while (p.shift < 63 && (hi >> p.shift) - (lo >> p.shift) >= cap) p.shift++;
   p.base = lo >> p.shift;
   return p;
+}
+
+DirParams dir_params(const uint64_t* sidx, uint64_t n) {
+  return n ? dir_params_ends(sidx[0], sidx[2 * (n - 1)], n) : DirParams{};
 }
 
 void fill_dir(const uint64_t* sidx, uint64_t n, const DirParams& p, uint16_t* dir) {
@@ -337,15 +340,18 @@ uint32_t bucket_dir_bits_for(uint64_t n, uint32_t extra) {
   return std::min<uint32_t>(20, std::max<uint32_t>(4, lg + extra));   // 2^extra buckets per entry
 }
 
-BucketDir bucket_dir_params(const uint64_t* sidx, uint64_t n, uint32_t extra) {
+BucketDir bucket_dir_params_ends(uint64_t lo, uint64_t hi, uint64_t n, uint32_t extra) {
   BucketDir p;
   p.bits = bucket_dir_bits_for(n, extra);
   if (!p.bits) return p;
-  const uint64_t lo = sidx[0], hi = sidx[2 * (n - 1)];
   const uint64_t cap = uint64_t(1) << p.bits;
   while (p.shift < 63 && (hi >> p.shift) - (lo >> p.shift) >= cap) p.shift++;
   p.base = lo >> p.shift;
   return p;
+}
+
+BucketDir bucket_dir_params(const uint64_t* sidx, uint64_t n, uint32_t extra) {
+  return n ? bucket_dir_params_ends(sidx[0], sidx[2 * (n - 1)], n, extra) : BucketDir{};
 }
 
 void fill_bucket_dir(const uint64_t* sidx, uint64_t n, const BucketDir& p, uint64_t* out) {

@@ -361,47 +361,56 @@ int make_table(const std::vector<planb::Prefix>& canon, uint64_t n_input, const 
                                  reinterpret_cast<uint64_t*>(base + lidx_off), bs->s);
       if (rc) return fail_detail(rc, "device leaf index fill", cudaGetLastError());
     }
-    if (cudaStreamSynchronize(bs->s) != cudaSuccess)
-      return fail_detail(PLANB_ECUDA, "device layout fill", cudaGetLastError());
-    if (dp.bits || bdp.bits) {   // the directories come from the index the device just wrote
-      std::vector<uint64_t> sx(sidx_n * 2);
-      if (cudaMemcpy(sx.data(), base + node_bytes + lo_bytes, sidx_n * 16,
-                     cudaMemcpyDeviceToHost) != cudaSuccess)
-        return PLANB_ECUDA;
+    // The directories come from the indexes the device just wrote, filled on the device too; the
+    // host reads only each index's first and last high halves, which size them.
+    auto ends = [&](size_t off, uint64_t n, uint64_t& first, uint64_t& last) {
+      return cudaMemcpyAsync(&first, base + off, 8, cudaMemcpyDeviceToHost, bs->s) ==
+                 cudaSuccess &&
+             cudaMemcpyAsync(&last, base + off + (n - 1) * 16, 8, cudaMemcpyDeviceToHost,
+                             bs->s) == cudaSuccess &&
+             cudaStreamSynchronize(bs->s) == cudaSuccess;
+    };
+    const size_t sidx_off = node_bytes + lo_bytes;
+    if (dp.bits || bdp.bits) {
+      uint64_t first = 0, last = 0;
+      if (!ends(sidx_off, sidx_n, first, last))
+        return fail_detail(PLANB_ECUDA, "device index ends", cudaGetLastError());
+      const uint64_t* sx = reinterpret_cast<const uint64_t*>(base + sidx_off);
       if (dp.bits) {
-        std::vector<uint64_t> dh(dirb / 8, 0);
         const uint32_t bits = dp.bits;
-        dp = planb::dir_params(sx.data(), sidx_n);
+        dp = planb::dir_params_ends(first, last, sidx_n);
         if (dp.bits != bits) return fail_detail(PLANB_EINVAL, "radix directory size");
-        planb::fill_dir(sx.data(), sidx_n, dp, reinterpret_cast<uint16_t*>(dh.data()));
-        if (cudaMemcpy(base + node_bytes + lo_bytes + sidx_bytes, dh.data(), dirb,
-                       cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMemsetAsync(base + sidx_off + sidx_bytes, 0, dirb, bs->s) != cudaSuccess)
           return PLANB_ECUDA;
+        rc = planb::gpu_fill_dir(sx, sidx_n, dp,
+                                 reinterpret_cast<uint16_t*>(base + sidx_off + sidx_bytes), bs->s);
+        if (rc) return fail_detail(rc, "device radix directory", cudaGetLastError());
       }
       if (bdp.bits) {
-        std::vector<uint64_t> bh(bdb / 8, 0);
         const uint32_t bits = bdp.bits;
-        bdp = planb::bucket_dir_params(sx.data(), sidx_n);
+        bdp = planb::bucket_dir_params_ends(first, last, sidx_n);
         if (bdp.bits != bits) return fail_detail(PLANB_EINVAL, "bucket directory size");
-        planb::fill_bucket_dir(sx.data(), sidx_n, bdp, bh.data());
-        if (cudaMemcpy(base + node_bytes + lo_bytes + sidx_bytes + dirb, bh.data(), bdb,
-                       cudaMemcpyHostToDevice) != cudaSuccess)
-          return PLANB_ECUDA;
+        rc = planb::gpu_fill_bucket_dir(
+            sx, sidx_n, bdp, reinterpret_cast<uint64_t*>(base + sidx_off + sidx_bytes + dirb),
+            bs->s);
+        if (rc) return fail_detail(rc, "device bucket directory", cudaGetLastError());
       }
     }
     if (lidx_n) {   // the leaf index's directory likewise
-      std::vector<uint64_t> lx(lidx_n * 2), bh(lbdb / 8, 0);
-      if (cudaMemcpy(lx.data(), base + lidx_off, lidx_n * 16, cudaMemcpyDeviceToHost) !=
-          cudaSuccess)
-        return PLANB_ECUDA;
+      uint64_t first = 0, last = 0;
+      if (!ends(lidx_off, lidx_n, first, last))
+        return fail_detail(PLANB_ECUDA, "device leaf index ends", cudaGetLastError());
       const uint32_t bits = lbp.bits;
-      lbp = planb::bucket_dir_params(lx.data(), lidx_n, 2);
+      lbp = planb::bucket_dir_params_ends(first, last, lidx_n, 2);
       if (lbp.bits != bits) return fail_detail(PLANB_EINVAL, "leaf bucket directory size");
-      planb::fill_bucket_dir(lx.data(), lidx_n, lbp, bh.data());
-      if (cudaMemcpy(base + lidx_off + lidx_bytes, bh.data(), lbdb, cudaMemcpyHostToDevice) !=
-          cudaSuccess)
-        return PLANB_ECUDA;
+      rc = planb::gpu_fill_bucket_dir(reinterpret_cast<const uint64_t*>(base + lidx_off), lidx_n,
+                                      lbp,
+                                      reinterpret_cast<uint64_t*>(base + lidx_off + lidx_bytes),
+                                      bs->s);
+      if (rc) return fail_detail(rc, "device leaf bucket directory", cudaGetLastError());
     }
+    if (cudaStreamSynchronize(bs->s) != cudaSuccess)
+      return fail_detail(PLANB_ECUDA, "device directories", cudaGetLastError());
   } else {
     std::vector<uint32_t> words;
     const void* vals = iv.nh.data();

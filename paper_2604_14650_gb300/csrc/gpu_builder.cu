@@ -299,6 +299,36 @@ __global__ void k_fill_sidx(uint64_t n, uint64_t span, const uint64_t* ihi, cons
   }
 }
 
+// Entries of an ascending index (2 u64 per entry, high half first) whose bucket
+// (hi >> shift) - base is below b.
+__device__ __forceinline__ uint64_t entries_below(const uint64_t* idx, uint64_t n, uint32_t shift,
+                                                  uint64_t base, uint64_t b) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if ((idx[2 * mid] >> shift) - base < b)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_fill_dir(const uint64_t* idx, uint64_t n, uint32_t shift, uint64_t base,
+                           uint64_t buckets, uint16_t* out) {
+  GRID_LOOP(b, buckets + 1) out[b] = static_cast<uint16_t>(entries_below(idx, n, shift, base, b));
+}
+
+__global__ void k_fill_bucket_dir(const uint64_t* idx, uint64_t n, uint32_t shift, uint64_t base,
+                                  uint64_t buckets, uint64_t* out) {
+  GRID_LOOP(b, buckets) {
+    const uint64_t first = entries_below(idx, n, shift, base, b);
+    const uint64_t next = entries_below(idx, n, shift, base, b + 1);
+    out[2 * b] = first | ((next - first) << 32);
+    out[2 * b + 1] = first < n ? idx[2 * first] : ~0ull;
+  }
+}
+
 // ----------------------------------------------------------------------------- sorting helpers
 
 struct Ctx {
@@ -559,6 +589,24 @@ int gpu_fill_index(const GpuIntervals& iv, const Layout& L, uint32_t S, uint64_t
   }
   k_fill_sidx<<<blocks_for(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(
       n, span, iv.hi.as<uint64_t>(), iv.lo.as<uint64_t>(), L.n_keys, iv.m, out);
+  return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+int gpu_fill_dir(const uint64_t* idx, uint64_t n, const DirParams& p, uint16_t* out,
+                 void* stream) {
+  if (!p.bits) return PLANB_OK;
+  const uint64_t buckets = uint64_t(1) << p.bits;
+  k_fill_dir<<<blocks_for(buckets + 1), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      idx, n, p.shift, p.base, buckets, out);
+  return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
+}
+
+int gpu_fill_bucket_dir(const uint64_t* idx, uint64_t n, const BucketDir& p, uint64_t* out,
+                        void* stream) {
+  if (!p.bits) return PLANB_OK;
+  const uint64_t buckets = uint64_t(1) << p.bits;
+  k_fill_bucket_dir<<<blocks_for(buckets), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+      idx, n, p.shift, p.base, buckets, out);
   return cudaPeekAtLastError() == cudaSuccess ? PLANB_OK : PLANB_ECUDA;
 }
 

@@ -185,6 +185,8 @@ struct DirParams {
 };
 uint32_t dir_bits_for(uint64_t n);   // the directory size for an index of n entries
 DirParams dir_params(const uint64_t* sidx /* 2 per entry, ascending */, uint64_t n);
+// the same from the high halves of the index's first and last entries
+DirParams dir_params_ends(uint64_t first_hi, uint64_t last_hi, uint64_t n);
 void fill_dir(const uint64_t* sidx, uint64_t n, const DirParams& p, uint16_t* dir);
 inline size_t dir_bytes(const DirParams& p) {
   return p.bits ? ((((size_t(1) << p.bits) + 1) * 2 + 127) / 128) * 128 : 0;
@@ -201,11 +203,19 @@ struct BucketDir {
 // extra: log2 of the buckets per entry, rounded up (2: about four buckets per entry)
 BucketDir bucket_dir_params(const uint64_t* sidx /* 2 per entry */, uint64_t n,
                             uint32_t extra = 2);
+BucketDir bucket_dir_params_ends(uint64_t first_hi, uint64_t last_hi, uint64_t n,
+                                 uint32_t extra = 2);
 inline size_t bucket_dir_bytes(const BucketDir& p) {
   return p.bits ? (size_t(1) << p.bits) * 16 : 0;
 }
 void fill_bucket_dir(const uint64_t* sidx, uint64_t n, const BucketDir& p, uint64_t* out);
 uint32_t bucket_dir_bits_for(uint64_t n, uint32_t extra = 2);
+// The radix and bucket directories of a device index of n entries (fill_dir, fill_bucket_dir on
+// the device: each bucket's first entry by a lower bound over the ascending high halves).
+int gpu_fill_dir(const uint64_t* idx, uint64_t n, const DirParams& p, uint16_t* out,
+                 void* stream);
+int gpu_fill_bucket_dir(const uint64_t* idx, uint64_t n, const BucketDir& p, uint64_t* out,
+                        void* stream);
 
 // ------------------------------------------------------------------------- device side
 
