@@ -489,7 +489,8 @@ int planb_mlp_forward(const float *d_u, size_t n, const float *w, float *d_y,
 
 /*
  * planb_intervals — the elementary intervals of a prefix table (Section 3.1; Algorithm 2's event
- * sort and stack sweep, with the readings stated in the project's design notes): out_start_hi/lo
+ * sort and stack sweep, read as: exclusive range ends in 129-bit arithmetic, ends before starts at
+ * one address, starts by ascending length, one interval per distinct boundary): out_start_hi/lo
  * receive the first address of each interval, strictly increasing from 0, and out_nh its next hop.
  * `cap` is the room in the output arrays; *out_m receives the interval count m (<= 2N + 1). When
  * cap < m nothing is written, *out_m is set and PLANB_EINVAL is returned.

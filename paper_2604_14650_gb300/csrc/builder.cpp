@@ -8,7 +8,7 @@
 //   a4  layout              Section 3.2: internal levels in breadth-first order, then the leaves, in
 //                           one flat array; every node full, padded with all-ones keys.
 //
-// Readings taken where the paper is loose (each is listed in the design notes):
+// Readings taken where the paper is loose:
 //   * ranges use the exclusive end P + 2^(128-L) in 129-bit arithmetic; an end equal to 2^128 is not
 //     a boundary (Algorithm 2 writes 2^(64-L), undefined for L > 64, and does not treat overflow);
 //   * at one address, end events are applied before start events, and starts in ascending length, so
